@@ -1,0 +1,173 @@
+/*
+ * lt.h -- C ABI of the GB300 lens-transport library (liblt.so).
+ *
+ * What it computes (Precomputed Lens Transport Maps, Sec. 3):
+ *   the lens transport map T(p_in, w_in, I_in, lambda) -> {(p_out, w_out, I_out)}_k
+ *   of Eq. 1, one path k at a time (Sec. 4.2 path decomposition), for a
+ *   static, rotationally symmetric lens of spherical or planar surfaces under
+ *   geometric optics.  A path's operator is the composition of per-surface
+ *   operators S_{L,sigma} = (closest hit p_sigma, new direction d_{L,sigma},
+ *   Fresnel factor f_{L,sigma}) (Eq. 5-7).  A ray is valid iff the last
+ *   surface it reaches is the output (image) plane (Sec. 3).
+ *
+ * Conventions shared by every entry point:
+ *   - Units: mm; wavelengths in nm (glass formulas use micrometres).
+ *   - Frame: optical axis +z, light travels +z, entrance plane z = 0, surface
+ *     1's vertex at prescription.entrance_gap.  Entrance rays are given by
+ *     their point (x, y, 0) and direction (dx, dy, dz), dz > 0; the direction
+ *     need not be exactly unit (it is normalised on load).
+ *   - Ray arrays are structure-of-arrays FP32.  Unless an entry point says
+ *     "host", pointers are DEVICE pointers on the current CUDA device, each
+ *     array 16-byte aligned, and the call only enqueues work on `stream`:
+ *     the caller keeps the buffers alive until the stream has passed the
+ *     work.  The library never frees caller memory.
+ *   - Errors: every lt_status call returns LT_OK (0) or a negative code and
+ *     leaves a message for lt_last_error() in the calling thread.  Nothing
+ *     throws across this boundary.  Per-ray problems never fail a call: they
+ *     go into the ray's flags byte (LT_FLAG_*), and an invalid ray has all
+ *     six outputs set to 0.
+ *   - Paths: path_id 0 is the transmission path through surfaces 1..S;
+ *     path_id 1 .. S(S-1)/2 are the two-bounce ghosts (i, j), 1 <= i < j <= S,
+ *     numbered lexicographically ((1,2) = 1, (1,3) = 2, ...).  A ghost goes
+ *     forward 1..j reflecting at j, back j-1..i reflecting at i, then
+ *     forward i+1..S to the image plane (Sec. 4.2: paths with more than two
+ *     reflections are dropped).
+ */
+#ifndef LT_H
+#define LT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int lt_status;
+#define LT_OK          0
+#define LT_EINVAL     -1   /* bad argument (NULL, size, alignment, path id) */
+#define LT_ENOMEM     -2   /* device or host allocation failed */
+#define LT_ECUDA      -3   /* a CUDA runtime call failed */
+#define LT_EBUSY      -4   /* resource in use */
+#define LT_ETIMEOUT   -5   /* a bounded wait ran out */
+#define LT_ENOTREADY  -6   /* work not finished yet */
+#define LT_EBADLENS   -7   /* prescription rejected */
+#define LT_EIO        -8   /* file read/write failed */
+
+/* A cudaStream_t (same type, no CUDA header needed); NULL = legacy default stream. */
+typedef struct CUstream_st* lt_stream;
+
+/* ------------------------------------------------------------------ lenses */
+
+#define LT_MAX_SURFACES 32
+#define LT_MAX_GLASSES  32
+
+enum { LT_GLASS_AIR = 0, LT_GLASS_CAUCHY = 1, LT_GLASS_SELLMEIER = 2 };
+enum { LT_IMAGE_PARAXIAL = 0, LT_IMAGE_ABS = 1 };
+
+/* Dispersion (the paper takes lambda as an input everywhere, Eq. 1-2):
+ * Cauchy n = A + B / lam^2, Sellmeier n^2 = 1 + sum_i B3[i] lam^2 / (lam^2 - C3[i]),
+ * lam in micrometres. */
+typedef struct {
+    int kind;
+    double A, B;
+    double B3[3], C3[3];
+} lt_glass;
+
+typedef struct {
+    double curvature;    /* 1/R (1/mm); 0 = plane; > 0: centre of curvature on the +z side */
+    double thickness;    /* vertex to next vertex (mm); ignored for the last surface */
+    double aperture_r;   /* clear aperture radius (mm): a hit with x^2+y^2 > r^2 is absorbed */
+    int glass_after;     /* index into glasses[] of the medium after this surface; -1 = air */
+} lt_surface;
+
+typedef struct {
+    int n_surfaces;              /* 1 .. LT_MAX_SURFACES */
+    const lt_surface* surfaces;  /* host array, copied by lt_create_lens */
+    int n_glasses;               /* 0 .. LT_MAX_GLASSES */
+    const lt_glass* glasses;     /* host array, copied */
+    double entrance_gap;         /* entrance plane (z = 0) to the vertex of surface 1 */
+    int stop_after;              /* aperture stop in the gap after this surface (0: in front of 1) */
+    double stop_offset;          /* stop plane z relative to that gap's start (z = 0 or vertex) */
+    double stop_r;               /* stop radius; <= 0: no stop */
+    int image_mode;              /* LT_IMAGE_PARAXIAL: paraxial focus at lambda_ref_nm;
+                                    LT_IMAGE_ABS: the plane z = image_z */
+    double image_z;
+    double lambda_ref_nm;        /* reference wavelength of the paraxial focus (e.g. 587.6) */
+    double edge_eps_mm;          /* near-edge flag band; <= 0 selects 1e-6 mm */
+    double grazing_k;            /* ill-conditioning band on k = 1 - eta^2 sin^2 i; <= 0 selects 1e-2 */
+} lt_prescription;
+
+typedef struct lt_lens lt_lens;
+
+/* Validate and copy a prescription, compute the image plane (paraxial
+ * ABCD product in FP64 when image_mode is LT_IMAGE_PARAXIAL) and stage the
+ * lens for the kernels.  Medium after the last surface is forced to air.
+ * Errors: LT_EINVAL (NULL / counts out of range), LT_EBADLENS (glass index
+ * out of range, aperture larger than a sphere, back focal distance <= 0).
+ * The caller owns *out and releases it with lt_destroy_lens. */
+lt_status lt_create_lens(const lt_prescription* p, lt_lens** out);
+void lt_destroy_lens(lt_lens* lens);
+
+/* Paraxial data of a lens at lambda_nm (host, FP64): effective focal length,
+ * back focal distance, and the image-plane z in use.  Any output may be NULL. */
+lt_status lt_lens_paraxial(const lt_lens* lens, double lambda_nm, double* efl, double* bfd,
+                           double* z_image);
+
+/* Number of paths of the lens (1 + S(S-1)/2) and the (i, j) of a path id. */
+int32_t lt_lens_n_paths(const lt_lens* lens);
+lt_status lt_path_ij(int32_t n_surfaces, int32_t path_id, int32_t* i, int32_t* j);
+/* Path id of ghost (i, j) (0 for i = j = 0), or -1 if out of range. */
+int32_t lt_path_id(int32_t n_surfaces, int32_t i, int32_t j);
+/* Paper-style binary path code (Fig. 2 caption; values in Fig. 7): bit k-1 is
+ * set when interaction k reflects (first interaction = least significant
+ * bit), plus a leading 1 at bit K, K = number of interactions.  0 on error. */
+uint64_t lt_path_code(int32_t n_surfaces, int32_t i, int32_t j);
+
+/* ------------------------------------------------------------------ rays */
+
+/* Ray flags (one byte per ray). */
+#define LT_FLAG_VALID      0x01  /* reached the image plane */
+#define LT_FLAG_NEAR_EDGE  0x02  /* some aperture/stop test was within edge_eps_mm of its edge */
+#define LT_FLAG_NEAR_TIR   0x04  /* some interaction had |1 - eta^2 sin^2 i| < 1e-6 */
+#define LT_FLAG_BAD_INPUT  0x08  /* NaN/Inf input, dz <= 0 or lambda <= 0 */
+#define LT_FLAG_TRACED     0x10  /* a map query answered this ray with the exact tracer */
+#define LT_FLAG_OUTSIDE    0x20  /* a map query found the ray outside the map's lattice box */
+#define LT_FLAG_GRAZING    0x40  /* some interaction had 0 <= k < grazing_k: the ray left within
+                                    ~6 deg of grazing and its FP32 output error is amplified by
+                                    ~1/(2 sqrt k) (ill-conditioned, reported separately) */
+
+typedef struct {
+    const float *x, *y;          /* entrance point on z = 0 */
+    const float *dx, *dy, *dz;   /* entrance direction */
+} lt_rays_in;
+
+typedef struct {
+    float *x, *y;                /* exit point on the image plane */
+    float *dx, *dy, *dz;         /* exit direction (unit) */
+    float *I;                    /* Fresnel throughput I_out for I_in = 1 */
+    uint8_t* flags;              /* LT_FLAG_* */
+} lt_rays_out;
+
+/* Brute-force FP32 trace of n rays along one path (Sec. 3, Eq. 6-7):
+ * one GPU thread per ray.  in/out/lambda_nm: device arrays of n entries.
+ * Errors: LT_EINVAL (NULL pointer with n > 0, misaligned array, bad path id),
+ * LT_ECUDA (launch failed).  n = 0 is a no-op. */
+lt_status lt_trace(const lt_lens* lens, const lt_rays_in* in, const float* lambda_nm,
+                   int32_t path_id, const lt_rays_out* out, size_t n, lt_stream stream);
+
+/* Same, with HOST arrays (pageable or pinned): copies in, traces, copies out
+ * in pipelined chunks on library streams and returns when the outputs are in
+ * host memory.  Errors as lt_trace, plus LT_ENOMEM for staging buffers. */
+lt_status lt_trace_host(const lt_lens* lens, const lt_rays_in* in, const float* lambda_nm,
+                        int32_t path_id, const lt_rays_out* out, size_t n);
+
+/* Thread-local message of the last failed call in this thread ("" if none). */
+const char* lt_last_error(void);
+/* Library version string. */
+const char* lt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LT_H */

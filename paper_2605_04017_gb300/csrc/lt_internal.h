@@ -1,0 +1,72 @@
+// Internal declarations of liblt (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/lt.h"
+
+namespace lt {
+
+// Error reporting: a thread-local message per failing call.
+lt_status fail(lt_status code, const char* fmt, ...);
+lt_status cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+
+#define LT_CUDA_TRY(expr)                                       \
+    do {                                                        \
+        cudaError_t _e = (expr);                                \
+        if (_e != cudaSuccess) return ::lt::cuda_fail(_e, #expr); \
+    } while (0)
+
+constexpr int kMaxS = LT_MAX_SURFACES;
+constexpr int kMaxG = LT_MAX_GLASSES;
+
+// The lens as the kernels see it: FP32, passed by value as a __grid_constant__
+// kernel parameter (a few KB, read through the constant cache; every lane of a
+// warp reads the same surface at the same time).
+//
+// Axial positions are kept relative to the vertex the ray last met, so the
+// FP32 z of a ray stays within a few mm of zero: vertex 0 is the entrance
+// plane z = 0, vertex k (1..S) the vertex of surface k, and
+//   th[k] = z(vertex k+1) - z(vertex k)   (k = 0..S-1, th[0] = entrance gap).
+struct LensDev {
+    int S;                  // optical surfaces
+    int stop_gap;           // stop in gap g (between vertex g and g+1; g = S: behind the last surface); -1 none
+    float zs_lo, zs_hi;     // stop plane z relative to vertex g and to vertex g+1
+    float a_stop2;          // stop radius squared
+    float eps2a_stop;       // near-edge band on r^2: 2 * a * eps
+    float z_img_rel;        // image plane z relative to vertex S
+    float grazing_k;        // k below which a refraction is flagged ill-conditioned
+    float c[kMaxS + 1];     // curvature of surface k (index 1..S)
+    float th[kMaxS + 1];    // vertex gaps
+    float ap2[kMaxS + 1];   // clear aperture radius squared
+    float eps2a[kMaxS + 1]; // near-edge band on r^2
+    int8_t med[kMaxS + 2];  // glass of medium m (0..S); -1 = air
+    int8_t gkind[kMaxG];
+    float gA[kMaxG], gB[kMaxG];
+    float gSB[kMaxG][3], gSC[kMaxG][3];
+};
+
+}  // namespace lt
+
+struct lt_lens {
+    int S;
+    int n_glass;
+    lt_surface surf[LT_MAX_SURFACES];
+    lt_glass glass[LT_MAX_GLASSES];
+    lt_prescription presc;          // arrays pointing at surf/glass above
+    double zv[LT_MAX_SURFACES + 1]; // FP64 vertex z (index 0 = entrance plane)
+    double z_stop;
+    double z_image;
+    lt::LensDev dev;
+};
+
+namespace lt {
+// Host FP64 paraxial ABCD data of a lens (defined in lens.cpp).
+int paraxial(const lt_lens* L, double lambda_nm, double* efl, double* bfd);
+bool path_ij(int S, int path_id, int* i, int* j);
+bool aligned16(const void* p);
+}  // namespace lt

@@ -1,0 +1,239 @@
+"""Thin ctypes binding of liblt.so (the C ABI in include/lt.h).
+
+Argument marshalling only: every step of the lens-transport path runs in
+the library's CUDA kernels.  PyTorch tensors serve as device memory and
+their streams as cudaStream_t; nothing here computes optics.  If the
+library has not been built, importing works but every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+from . import build as _build
+
+LT_OK = 0
+LT_EINVAL = -1
+LT_ENOMEM = -2
+LT_ECUDA = -3
+LT_EBUSY = -4
+LT_ETIMEOUT = -5
+LT_ENOTREADY = -6
+LT_EBADLENS = -7
+LT_EIO = -8
+
+FLAG_VALID = 0x01
+FLAG_NEAR_EDGE = 0x02
+FLAG_NEAR_TIR = 0x04
+FLAG_BAD_INPUT = 0x08
+FLAG_TRACED = 0x10
+FLAG_OUTSIDE = 0x20
+FLAG_GRAZING = 0x40
+
+MAX_SURFACES = 32
+MAX_GLASSES = 32
+
+
+class LTError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"lt error {code}: {msg}")
+        self.code = code
+
+
+class c_glass(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("A", ctypes.c_double), ("B", ctypes.c_double),
+                ("B3", ctypes.c_double * 3), ("C3", ctypes.c_double * 3)]
+
+
+class c_surface(ctypes.Structure):
+    _fields_ = [("curvature", ctypes.c_double), ("thickness", ctypes.c_double),
+                ("aperture_r", ctypes.c_double), ("glass_after", ctypes.c_int)]
+
+
+class c_prescription(ctypes.Structure):
+    _fields_ = [("n_surfaces", ctypes.c_int), ("surfaces", ctypes.POINTER(c_surface)),
+                ("n_glasses", ctypes.c_int), ("glasses", ctypes.POINTER(c_glass)),
+                ("entrance_gap", ctypes.c_double), ("stop_after", ctypes.c_int),
+                ("stop_offset", ctypes.c_double), ("stop_r", ctypes.c_double),
+                ("image_mode", ctypes.c_int), ("image_z", ctypes.c_double),
+                ("lambda_ref_nm", ctypes.c_double), ("edge_eps_mm", ctypes.c_double),
+                ("grazing_k", ctypes.c_double)]
+
+
+_fptr = ctypes.c_void_p
+
+
+class c_rays_in(ctypes.Structure):
+    _fields_ = [("x", _fptr), ("y", _fptr), ("dx", _fptr), ("dy", _fptr), ("dz", _fptr)]
+
+
+class c_rays_out(ctypes.Structure):
+    _fields_ = [("x", _fptr), ("y", _fptr), ("dx", _fptr), ("dy", _fptr), ("dz", _fptr),
+                ("I", _fptr), ("flags", _fptr)]
+
+
+_LIB: Optional[ctypes.CDLL] = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded liblt.so.  Raises if it has not been built: there is no
+    fallback implementation."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"liblt.so is not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        _declare(L)
+        _LIB = L
+    return _LIB
+
+
+def _declare(L: ctypes.CDLL) -> None:
+    vp = ctypes.c_void_p
+    st = ctypes.c_int
+    L.lt_last_error.restype = ctypes.c_char_p
+    L.lt_version.restype = ctypes.c_char_p
+    L.lt_create_lens.restype = st
+    L.lt_create_lens.argtypes = [ctypes.POINTER(c_prescription), ctypes.POINTER(vp)]
+    L.lt_destroy_lens.restype = None
+    L.lt_destroy_lens.argtypes = [vp]
+    L.lt_lens_paraxial.restype = st
+    L.lt_lens_paraxial.argtypes = [vp, ctypes.c_double] + [ctypes.POINTER(ctypes.c_double)] * 3
+    L.lt_lens_n_paths.restype = ctypes.c_int32
+    L.lt_lens_n_paths.argtypes = [vp]
+    L.lt_path_ij.restype = st
+    L.lt_path_ij.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                             ctypes.POINTER(ctypes.c_int32)]
+    L.lt_path_id.restype = ctypes.c_int32
+    L.lt_path_id.argtypes = [ctypes.c_int32] * 3
+    L.lt_path_code.restype = ctypes.c_uint64
+    L.lt_path_code.argtypes = [ctypes.c_int32] * 3
+    L.lt_trace.restype = st
+    L.lt_trace.argtypes = [vp, ctypes.POINTER(c_rays_in), vp, ctypes.c_int32,
+                           ctypes.POINTER(c_rays_out), ctypes.c_size_t, vp]
+    L.lt_trace_host.restype = st
+    L.lt_trace_host.argtypes = [vp, ctypes.POINTER(c_rays_in), vp, ctypes.c_int32,
+                                ctypes.POINTER(c_rays_out), ctypes.c_size_t]
+
+
+def check(code: int) -> None:
+    if code != LT_OK:
+        raise LTError(code, lib().lt_last_error().decode())
+
+
+def last_error() -> str:
+    return lib().lt_last_error().decode()
+
+
+def version() -> str:
+    return lib().lt_version().decode()
+
+
+def path_id(S: int, i: int, j: int) -> int:
+    return int(lib().lt_path_id(S, i, j))
+
+
+def path_ij(S: int, pid: int):
+    i = ctypes.c_int32()
+    j = ctypes.c_int32()
+    check(lib().lt_path_ij(S, pid, ctypes.byref(i), ctypes.byref(j)))
+    return i.value, j.value
+
+
+def path_code(S: int, i: int, j: int) -> int:
+    return int(lib().lt_path_code(S, i, j))
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if hasattr(t, "ctypes"):
+        return t.ctypes.data
+    return int(t)
+
+
+class Lens:
+    """A lens resident in the library, created from a workloads.Prescription
+    (or anything with the same attributes)."""
+
+    def __init__(self, presc, edge_eps_mm: float = 0.0, grazing_k: float = 0.0):
+        S = len(presc.surfaces)
+        self._surfs = (c_surface * max(S, 1))()
+        for k, s in enumerate(presc.surfaces):
+            self._surfs[k] = c_surface(s.curvature, s.thickness, s.aperture_r, s.glass_after)
+        ng = len(presc.glasses)
+        self._glasses = (c_glass * max(ng, 1))()
+        for g, G in enumerate(presc.glasses):
+            self._glasses[g] = c_glass(G.kind, G.A, G.B, (ctypes.c_double * 3)(*G.B3),
+                                       (ctypes.c_double * 3)(*G.C3))
+        self._p = c_prescription(S, self._surfs, ng, self._glasses, presc.entrance_gap,
+                                 presc.stop_after, presc.stop_offset, presc.stop_r,
+                                 presc.image_mode, presc.image_z, presc.lambda_ref_nm, edge_eps_mm,
+                                 grazing_k)
+        h = ctypes.c_void_p()
+        check(lib().lt_create_lens(ctypes.byref(self._p), ctypes.byref(h)))
+        self.handle = h
+        self.S = S
+        self.presc = presc
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().lt_destroy_lens(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_paths(self) -> int:
+        return int(lib().lt_lens_n_paths(self.handle))
+
+    def paraxial(self, lam_nm: float):
+        e, b, z = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        check(lib().lt_lens_paraxial(self.handle, lam_nm, ctypes.byref(e), ctypes.byref(b),
+                                     ctypes.byref(z)))
+        return e.value, b.value, z.value
+
+
+def rays_in(x, y, dx, dy, dz) -> c_rays_in:
+    return c_rays_in(_ptr(x), _ptr(y), _ptr(dx), _ptr(dy), _ptr(dz))
+
+
+def rays_out(x, y, dx, dy, dz, I, flags) -> c_rays_out:
+    return c_rays_out(_ptr(x), _ptr(y), _ptr(dx), _ptr(dy), _ptr(dz), _ptr(I), _ptr(flags))
+
+
+def trace(lens: Lens, inp: Sequence, lam, path_id: int, out: Sequence, n: int, stream=None):
+    """lt_trace on device tensors: inp = (x, y, dx, dy, dz), out = (x, y, dx, dy, dz, I, flags)."""
+    ri = rays_in(*inp)
+    ro = rays_out(*out)
+    check(lib().lt_trace(lens.handle, ctypes.byref(ri), _ptr(lam), path_id, ctypes.byref(ro), n,
+                         _stream_handle(stream)))
+
+
+def trace_host(lens: Lens, inp: Sequence, lam, path_id: int, out: Sequence, n: int):
+    """lt_trace_host on host arrays (numpy or pinned CPU tensors)."""
+    ri = rays_in(*inp)
+    ro = rays_out(*out)
+    check(lib().lt_trace_host(lens.handle, ctypes.byref(ri), _ptr(lam), path_id, ctypes.byref(ro),
+                              n))

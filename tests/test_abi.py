@@ -1,0 +1,121 @@
+"""CPU checks of the C ABI: the library loads, exports every function the
+headers declare, validates arguments before touching the GPU, and its host
+logic (paraxial image plane, path numbering) agrees with the oracle."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_04017_gb300 import lt, workloads as w
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(lt_[a-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_function():
+    L = lt.lib()
+    names = declared_functions()
+    assert len(names) >= 10
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_built_for_sm103a_only():
+    from paper_2605_04017_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def oracle_accept(p):
+    try:
+        e, b = oracle.Lens(p).paraxial(w.LAMBDA_D_NM)
+        return e > 0 and b > 0
+    except ValueError:
+        return False
+
+
+@pytest.mark.parametrize("which", ["singlet", "eleven"])
+def test_paraxial_matches_oracle(which):
+    p = w.singlet_lens() if which == "singlet" else w.eleven_surface_lens(oracle_accept)
+    L = lt.Lens(p)
+    O = oracle.Lens(p)
+    for lam in (380.0, 587.6, 780.0):
+        efl, bfd, zi = L.paraxial(lam)
+        oe, ob = O.paraxial(lam)
+        assert efl == pytest.approx(oe, rel=1e-12)
+        assert bfd == pytest.approx(ob, rel=1e-12)
+    assert zi == pytest.approx(O.z_image(), rel=1e-13)
+
+
+def test_path_numbering_matches_oracle():
+    for S in (2, 5, 11, 22):
+        L_paths = 1 + S * (S - 1) // 2
+        for pid in range(L_paths):
+            ij = lt.path_ij(S, pid)
+            assert ij == oracle.path_ij(S, pid)
+            assert lt.path_id(S, *ij) == pid
+            assert lt.path_code(S, *ij) == oracle.path_code(S, *ij)
+    assert lt.path_code(13, 1, 3) == 131092
+    assert lt.path_code(12, 3, 5) == 65616
+    assert lt.path_id(5, 3, 2) == -1
+
+
+def test_lens_validation():
+    p = w.singlet_lens()
+    p.surfaces[0].aperture_r = 60.0        # larger than |R| = 50
+    with pytest.raises(lt.LTError) as e:
+        lt.Lens(p)
+    assert e.value.code == lt.LT_EBADLENS
+    p = w.singlet_lens()
+    p.surfaces[0].glass_after = 3
+    with pytest.raises(lt.LTError) as e:
+        lt.Lens(p)
+    assert e.value.code == lt.LT_EBADLENS
+    # a diverging lens has no real paraxial focus behind it
+    p = w.singlet_lens()
+    p.surfaces[0].curvature = -1 / 50.0
+    p.surfaces[1].curvature = 1 / 50.0
+    with pytest.raises(lt.LTError):
+        lt.Lens(p)
+    assert "back focal" in lt.last_error()
+    p = w.singlet_lens()
+    p.surfaces = p.surfaces * 20           # 40 surfaces > LT_MAX_SURFACES
+    with pytest.raises(lt.LTError) as e:
+        lt.Lens(p)
+    assert e.value.code == lt.LT_EINVAL
+
+
+def test_trace_argument_errors_without_gpu():
+    L = lt.Lens(w.singlet_lens())
+    ri = lt.c_rays_in()
+    ro = lt.c_rays_out()
+    # NULL arrays with n > 0
+    rc = lt.lib().lt_trace(L.handle, ctypes.byref(ri), None, 0, ctypes.byref(ro), 10, None)
+    assert rc == lt.LT_EINVAL
+    # bad path id
+    rc = lt.lib().lt_trace(L.handle, ctypes.byref(ri), None, 2, ctypes.byref(ro), 0, None)
+    assert rc == lt.LT_EINVAL and "path" in lt.last_error()
+    # misaligned arrays
+    buf = np.zeros(64, np.float32)
+    base = buf.ctypes.data
+    ri = lt.c_rays_in(base + 4, base, base, base, base)
+    ro = lt.c_rays_out(base, base, base, base, base, base, base)
+    rc = lt.lib().lt_trace(L.handle, ctypes.byref(ri), base, 0, ctypes.byref(ro), 4, None)
+    assert rc == lt.LT_EINVAL and "aligned" in lt.last_error()
+    # n = 0 is a no-op
+    rc = lt.lib().lt_trace(L.handle, ctypes.byref(lt.c_rays_in()), None, 0,
+                           ctypes.byref(lt.c_rays_out()), 0, None)
+    assert rc == lt.LT_OK
