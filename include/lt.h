@@ -162,6 +162,115 @@ lt_status lt_trace(const lt_lens* lens, const lt_rays_in* in, const float* lambd
 lt_status lt_trace_host(const lt_lens* lens, const lt_rays_in* in, const float* lambda_nm,
                         int32_t path_id, const lt_rays_out* out, size_t n);
 
+/* ------------------------------------------------------------------ maps */
+
+/*
+ * Precomputed lens transport map of one path (Sec. 4, "Precomputed Lens
+ * Transport Maps"): the factorised form of Sec. 4.2 -- a binary valid/occluded
+ * mask (Eq. 11: output f(x) if g(x) = 1, nothing otherwise) and a regressor
+ * used only on unblocked rays.  Here the regressor is a table:
+ *   - a regular lattice over the 5-D input box (x, y, s_x, s_y, lambda) with
+ *     s = (d_x/d_z, d_y/d_z) the entrance direction slopes; every node is
+ *     traced exactly (FP32, the lt_trace tracer); node layout row-major over
+ *     (x, y, s_x, s_y, lambda), lambda fastest, 6 floats per node
+ *     (x, y, dx, dy, dz, I at the image plane; zeros if the node is invalid);
+ *   - every cell is INVALID (its 32 corners and every fit ray inside it are
+ *     invalid), VALID (all corners and fit rays valid, and no fit ray's exit
+ *     position differs from interpolation by more than max_residual_mm) or
+ *     BOUNDARY (anything else), 2 bits per cell;
+ *   - a query answers a VALID cell by multilinear interpolation of its 32
+ *     corners (direction renormalised), an INVALID cell with "no output", and
+ *     a BOUNDARY cell -- or a ray outside the box -- with the exact tracer
+ *     (the tracer is the map's fallback near mask boundaries).
+ * The cell of a ray is decided in FP32 with correctly rounded operations, in
+ * this order: s = d_x / d_z; u = (v - lo) * inv_step; cell = min(floor(u),
+ * res - 2); inside iff 0 <= u <= res - 1 on every axis; lo, step and
+ * inv_step are the FP32 roundings of lo, (hi - lo)/(res - 1) and its inverse.
+ * Node entrance rays are built the same way: q = lo + i * step (each step
+ * rounded), d = (s_x, s_y, 1) / sqrt(s_x^2 + s_y^2 + 1).
+ */
+typedef struct lt_map lt_map;
+
+typedef struct {
+    int32_t path_id;             /* path the map represents */
+    int32_t res[5];              /* nodes along x, y, s_x, s_y, lambda; each >= 2 */
+    double lo[5], hi[5];         /* lattice box (mm, mm, slope, slope, nm) */
+    double max_residual_mm;      /* <= 0: no limit; else VALID cells also need every fit
+                                    ray's |interpolated - traced| exit position <= this */
+    const float *fit_x, *fit_y, *fit_dx, *fit_dy, *fit_dz, *fit_lambda;  /* device arrays */
+    size_t n_fit;                /* fit rays (may be 0: classes from corners alone) */
+} lt_map_opts;
+
+typedef struct {
+    uint64_t n_nodes, n_cells, valid_nodes;
+    uint64_t cells_invalid, cells_valid, cells_boundary;
+    uint64_t fit_inside, fit_valid;          /* fit rays inside the box / valid */
+    double fit_residual_rms_mm;              /* over valid fit rays in cells whose corners are all valid */
+    double fit_residual_max_mm;
+    uint64_t table_bytes;                    /* device bytes held by the map */
+    double build_ms;                         /* wall time of lt_build_map */
+} lt_map_stats;
+
+/* Build a map on the current device: trace the lattice nodes, trace and
+ * reduce the fit rays per cell (FP64 residual sums), classify the cells.
+ * Work runs on `stream`; the call returns when the map is complete.  The map
+ * keeps a copy of the lens (no reference to `lens`).  Errors: LT_EINVAL
+ * (resolution < 2, empty box, bad path, misaligned fit arrays), LT_ENOMEM,
+ * LT_ECUDA.  The caller releases *out with lt_destroy_map. */
+lt_status lt_build_map(const lt_lens* lens, const lt_map_opts* opts, lt_map** out,
+                       lt_stream stream);
+void lt_destroy_map(lt_map* map);
+lt_status lt_map_stats_get(const lt_map* map, lt_map_stats* out);
+
+enum {
+    LT_QUERY_TABLE = 0,        /* mask + table, exact tracer for BOUNDARY cells (default) */
+    LT_QUERY_NO_MASK = 1       /* ablation of Fig. 6: ignore the mask, interpolate every ray
+                                  inside the box over all 32 corners (invalid nodes count as
+                                  zeros) and report it valid; outside the box: tracer */
+};
+
+/* Query the map for n rays (device arrays, as lt_trace).  Rays answered by
+ * the tracer carry LT_FLAG_TRACED.  Temporary device memory for the fallback
+ * list (4 bytes per ray) is taken stream-ordered from a library pool.
+ * Errors as lt_trace. */
+lt_status lt_query(const lt_map* map, const lt_rays_in* in, const float* lambda_nm,
+                   const lt_rays_out* out, size_t n, int32_t mode, lt_stream stream);
+/* Same with HOST arrays; returns when the results are in host memory. */
+lt_status lt_query_host(const lt_map* map, const lt_rays_in* in, const float* lambda_nm,
+                        const lt_rays_out* out, size_t n, int32_t mode);
+
+/* Copy the map to host memory for inspection: node6 (n_nodes x 6 floats),
+ * node_valid (n_nodes bytes, 1/0), cell_class (n_cells bytes: 0 INVALID,
+ * 1 VALID, 2 BOUNDARY).  Any pointer may be NULL. */
+lt_status lt_map_export(const lt_map* map, float* node6, uint8_t* node_valid,
+                        uint8_t* cell_class);
+
+/* Persist a map (lattice, tables, classes, the lens it was built on) to a
+ * file, and load it back onto the current device.  Errors: LT_EIO. */
+lt_status lt_map_save(const lt_map* map, const char* path);
+lt_status lt_map_load(const char* path, lt_map** out);
+
+/* ------------------------------------------------------------------ profiling */
+
+/* Per-kernel device time.  When enabled, each kernel launch of the library
+ * is bracketed by two CUDA events recorded on the stream it is launched on
+ * (so the times are device times of that kernel alone).  lt_profile_read
+ * waits for the recorded events, fills up to `max` entries (one per kernel
+ * name, launches and summed milliseconds), sets *n to the number of kernel
+ * names seen, and clears the record if `reset` is non-zero.  At most 65,536
+ * launches are kept between resets.  While enabled, tracing kernels also
+ * count their work (one 64-bit atomic per warp). */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+    int64_t work;        /* tracing kernels: ray-surface interactions evaluated (the image
+                            plane counts as one); 0 for other kernels */
+} lt_kernel_time;
+
+lt_status lt_profile_enable(int32_t on);
+lt_status lt_profile_read(lt_kernel_time* out, int32_t max, int32_t* n, int32_t reset);
+
 /* Thread-local message of the last failed call in this thread ("" if none). */
 const char* lt_last_error(void);
 /* Library version string. */

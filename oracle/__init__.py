@@ -122,6 +122,8 @@ def _declare(L: ctypes.CDLL) -> None:
     L.or_map_query_one.restype = ctypes.c_int
     L.or_map_query_one.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _ip, _fp, _fp, _fp,
                                    _fp, ctypes.c_long] + [_fp] * 6 + [ctypes.c_double, _dp, _ip]
+    L.or_map_node_rays.restype = None
+    L.or_map_node_rays.argtypes = [_ip, _fp, _fp] + [_fp] * 6
     L.or_map_interpolate.restype = None
     L.or_map_interpolate.argtypes = [_ip, _fp, _fp, _fp, _dp, _fp, _dp, _ip]
 
@@ -287,6 +289,15 @@ class Lattice:
         lib().or_map_node_ray(_ptr(self.lo_f, _fp), _ptr(self.step_f, _fp), _ptr(idx, _ip),
                               _ptr(ray, _fp))
         return ray
+
+    def node_rays(self):
+        """Entrance rays of every lattice node, in table order (a workloads.Rays)."""
+        from paper_2605_04017_gb300.workloads import Rays
+        N = self.n_nodes
+        arrs = [np.zeros(N, np.float32) for _ in range(6)]
+        lib().or_map_node_rays(_ptr(self.res, _ip), _ptr(self.lo_f, _fp), _ptr(self.step_f, _fp),
+                               *[_ptr(a, _fp) for a in arrs])
+        return Rays(*arrs)
 
     def cell_ids(self, rays) -> np.ndarray:
         n = len(rays)

@@ -362,3 +362,19 @@ void or_map_interpolate(const int* res, const float* lo_f, const float* step_f, 
     or_map_cell_of(res, lo_f, inv_f, ray, cell);
     interpolate(res, lo_f, step_f, cell, corner6, ray, out);
 }
+
+/* All lattice node entrance rays as SoA arrays (node order of the table). */
+void or_map_node_rays(const int* res, const float* lo_f, const float* step_f, float* x, float* y,
+                      float* dx, float* dy, float* dz, float* lam)
+{
+    long N = 1;
+    for (int d = 0; d < 5; ++d) N *= res[d];
+    int idx[5];
+    for (long l = 0; l < N; ++l) {
+        long t = l;
+        for (int d = 4; d >= 0; --d) { idx[d] = (int)(t % res[d]); t /= res[d]; }
+        float ray[6];
+        or_map_node_ray(lo_f, step_f, idx, ray);
+        x[l] = ray[0]; y[l] = ray[1]; dx[l] = ray[2]; dy[l] = ray[3]; dz[l] = ray[4]; lam[l] = ray[5];
+    }
+}

@@ -1,0 +1,778 @@
+// Tabulated lens transport map: build (node tracing, fit-ray reduction, cell
+// classification) and query (mask lookup, 32-corner multilinear
+// interpolation, exact-tracer fallback for BOUNDARY cells).
+//
+// The paper's factorisation (Sec. 4.2, Eq. 11): a valid/occluded mask g and a
+// regressor f used only where g = 1.  Here the mask is 2 bits per lattice
+// cell and the regressor a table of traced nodes; cells the mask cannot decide
+// (BOUNDARY) are answered by the tracer itself.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <chrono>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "map_internal.h"
+#include "profile.h"
+#include "tracer.cuh"
+
+namespace lt {
+
+constexpr int kQBlock = 256;
+constexpr uint32_t kOutsideBit = 0x80000000u;
+
+// ------------------------------------------------------------------ lattice (FP32 rule)
+
+__device__ __forceinline__ float node_coord(const MapDev& M, int d, int i)
+{
+    return __fadd_rn(M.lo[d], __fmul_rn((float)i, M.step[d]));
+}
+
+// entrance ray of lattice node `idx`: direction normalize(s_x, s_y, 1), all
+// operations correctly rounded (never contracted) so the oracle can rebuild it
+__device__ __forceinline__ void node_ray(const MapDev& M, const int idx[5], float ray[6])
+{
+    float q[5];
+#pragma unroll
+    for (int d = 0; d < 5; ++d) q[d] = node_coord(M, d, idx[d]);
+    const float a = __fmul_rn(q[2], q[2]);
+    const float b = __fmul_rn(q[3], q[3]);
+    const float s = __fadd_rn(a, b);
+    const float n2 = __fadd_rn(s, 1.0f);
+    const float len = __fsqrt_rn(n2);
+    ray[0] = q[0];
+    ray[1] = q[1];
+    ray[2] = __fdiv_rn(q[2], len);
+    ray[3] = __fdiv_rn(q[3], len);
+    ray[4] = __fdiv_rn(1.0f, len);
+    ray[5] = q[4];
+}
+
+// cell of a ray: returns false outside the box (or for dz <= 0 / NaN);
+// f[d] = u - cell is the FP32 position inside the cell
+__device__ __forceinline__ bool cell_of(const MapDev& M, float x, float y, float dx, float dy,
+                                        float dz, float lam, uint32_t& cid, float f[5])
+{
+    if (!(dz > 0.0f)) return false;
+    const float v[5] = {x, y, __fdiv_rn(dx, dz), __fdiv_rn(dy, dz), lam};
+    bool inside = true;
+    cid = 0;
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+        const float u = __fmul_rn(__fsub_rn(v[d], M.lo[d]), M.inv[d]);
+        inside &= (u >= 0.0f) & (u <= M.umax[d]);
+        int c = (int)floorf(u);
+        c = min(max(c, 0), M.res[d] - 2);
+        f[d] = u - (float)c;
+        cid += (uint32_t)c * M.cstride[d];
+    }
+    return inside;
+}
+
+__device__ __forceinline__ uint32_t cell_class(const MapDev& M, uint32_t cid)
+{
+    return (__ldg(M.cls + (cid >> 4)) >> ((cid & 15u) * 2u)) & 3u;
+}
+
+// node-table base index of the cell's (0,0,0,0,0) corner
+__device__ __forceinline__ uint32_t cell_base(const MapDev& M, uint32_t cid)
+{
+    uint32_t base = 0;
+#pragma unroll
+    for (int d = 4; d >= 0; --d) {
+        const uint32_t rd = (uint32_t)(M.res[d] - 1);
+        const uint32_t c = cid % rd;
+        cid /= rd;
+        base += c * M.stride[d];
+    }
+    return base;
+}
+
+// Multilinear interpolation over the 32 corners: lerp each lambda-adjacent
+// node pair (48 contiguous bytes, three 8-byte-aligned loads per node), then
+// weight the 16 (x, y, s_x, s_y) corners.  Direction renormalised.
+__device__ __forceinline__ void interpolate(const MapDev& M, const float* __restrict__ node,
+                                            uint32_t base, const float f[5], float o[6])
+{
+    const float w0[2] = {1.0f - f[0], f[0]}, w1[2] = {1.0f - f[1], f[1]};
+    const float w2[2] = {1.0f - f[2], f[2]}, w3[2] = {1.0f - f[3], f[3]};
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const float fl = f[4];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+        const int b0 = (c >> 3) & 1, b1 = (c >> 2) & 1, b2 = (c >> 1) & 1, b3 = c & 1;
+        const uint32_t off = base + b0 * M.stride[0] + b1 * M.stride[1] + b2 * M.stride[2] +
+                             b3 * M.stride[3];
+        const float2* p = reinterpret_cast<const float2*>(node + (size_t)off * 6);
+        const float2 a0 = __ldg(p + 0), a1 = __ldg(p + 1), a2 = __ldg(p + 2);
+        const float2 c0 = __ldg(p + 3), c1 = __ldg(p + 4), c2 = __ldg(p + 5);
+        const float w = (w0[b0] * w1[b1]) * (w2[b2] * w3[b3]);
+        acc[0] = fmaf(w, fmaf(fl, c0.x - a0.x, a0.x), acc[0]);
+        acc[1] = fmaf(w, fmaf(fl, c0.y - a0.y, a0.y), acc[1]);
+        acc[2] = fmaf(w, fmaf(fl, c1.x - a1.x, a1.x), acc[2]);
+        acc[3] = fmaf(w, fmaf(fl, c1.y - a1.y, a1.y), acc[3]);
+        acc[4] = fmaf(w, fmaf(fl, c2.x - a2.x, a2.x), acc[4]);
+        acc[5] = fmaf(w, fmaf(fl, c2.y - a2.y, a2.y), acc[5]);
+    }
+    const float n2 = fmaf(acc[2], acc[2], fmaf(acc[3], acc[3], acc[4] * acc[4]));
+    float inv = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
+    inv = inv * fmaf(-0.5f * n2, inv * inv, 1.5f);
+    o[0] = acc[0];
+    o[1] = acc[1];
+    o[2] = acc[2] * inv;
+    o[3] = acc[3] * inv;
+    o[4] = acc[4] * inv;
+    o[5] = acc[5];
+}
+
+__device__ __forceinline__ void store_out(const RaysOutDev& out, uint32_t r, const float o[6],
+                                          uint32_t flags)
+{
+    __stcs(out.x + r, o[0]);
+    __stcs(out.y + r, o[1]);
+    __stcs(out.dx + r, o[2]);
+    __stcs(out.dy + r, o[3]);
+    __stcs(out.dz + r, o[4]);
+    __stcs(out.I + r, o[5]);
+    out.flags[r] = (uint8_t)flags;
+}
+
+// ------------------------------------------------------------------ build kernels
+
+__global__ void __launch_bounds__(256)
+map_node_kernel(const __grid_constant__ MapDev M, float* __restrict__ node,
+                uint8_t* __restrict__ node_valid, uint32_t N)
+{
+    const uint32_t l = blockIdx.x * 256u + threadIdx.x;
+    if (l >= N) return;
+    int idx[5];
+    uint32_t t = l;
+#pragma unroll
+    for (int d = 4; d >= 0; --d) {
+        idx[d] = (int)(t % (uint32_t)M.res[d]);
+        t /= (uint32_t)M.res[d];
+    }
+    float ray[6];
+    node_ray(M, idx, ray);
+    TraceOut o;
+    int nint;
+    const uint32_t f = trace_ray(M.L, M.pi, M.pj, ray[0], ray[1], ray[2], ray[3], ray[4], ray[5], o, nint);
+    float2* p = reinterpret_cast<float2*>(node + (size_t)l * 6);
+    p[0] = make_float2(o.x, o.y);
+    p[1] = make_float2(o.dx, o.dy);
+    p[2] = make_float2(o.dz, o.I);
+    node_valid[l] = (uint8_t)(f & LT_FLAG_VALID);
+}
+
+// per cell: bit0 = all 32 corners valid, bit1 = all invalid
+__global__ void __launch_bounds__(256)
+map_corner_kernel(const __grid_constant__ MapDev M, const uint8_t* __restrict__ node_valid,
+                  uint8_t* __restrict__ corner_bits, uint32_t NC)
+{
+    const uint32_t cid = blockIdx.x * 256u + threadIdx.x;
+    if (cid >= NC) return;
+    const uint32_t base = cell_base(M, cid);
+    int nv = 0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const uint32_t off = base + ((k >> 4) & 1) * M.stride[0] + ((k >> 3) & 1) * M.stride[1] +
+                             ((k >> 2) & 1) * M.stride[2] + ((k >> 1) & 1) * M.stride[3] +
+                             (k & 1) * M.stride[4];
+        nv += __ldg(node_valid + off);
+    }
+    corner_bits[cid] = (uint8_t)((nv == 32 ? 1 : 0) | (nv == 0 ? 2 : 0));
+}
+
+struct FitAccum {
+    unsigned long long inside, valid, n_res;
+    double sumsq;
+    unsigned int max_res_bits;
+};
+
+// one thread per fit ray: mark the cell as having seen a valid / invalid ray,
+// and for valid rays in all-valid-corner cells reduce the interpolation residual
+__global__ void __launch_bounds__(256)
+map_fit_kernel(const __grid_constant__ MapDev M, RaysInDev fit, uint32_t nfit,
+               const float* __restrict__ node, const uint8_t* __restrict__ corner_bits,
+               uint32_t* __restrict__ seen, uint32_t* __restrict__ resmax, FitAccum* acc)
+{
+    const uint32_t r = blockIdx.x * 256u + threadIdx.x;
+    bool inside = false, valid = false, has_res = false;
+    float res = 0.0f;
+    if (r < nfit) {
+        const float x = __ldg(fit.x + r), y = __ldg(fit.y + r), dx = __ldg(fit.dx + r),
+                    dy = __ldg(fit.dy + r), dz = __ldg(fit.dz + r), lam = __ldg(fit.lam + r);
+        uint32_t cid;
+        float f[5];
+        inside = cell_of(M, x, y, dx, dy, dz, lam, cid, f);
+        if (inside) {
+            TraceOut o;
+            int nint;
+            valid = (trace_ray(M.L, M.pi, M.pj, x, y, dx, dy, dz, lam, o, nint) & LT_FLAG_VALID) != 0;
+            atomicOr(seen + (cid >> 4), (valid ? 1u : 2u) << ((cid & 15u) * 2u));
+            if (valid && (__ldg(corner_bits + cid) & 1)) {
+                float ip[6];
+                interpolate(M, node, cell_base(M, cid), f, ip);
+                res = hypotf(ip[0] - o.x, ip[1] - o.y);
+                has_res = true;
+                if (resmax) atomicMax(resmax + cid, __float_as_uint(res));
+            }
+        }
+    }
+    // warp reductions of the global statistics (FP64 sum of squares)
+    const unsigned full = 0xffffffffu;
+    unsigned long long cin = __popc(__ballot_sync(full, inside));
+    unsigned long long cva = __popc(__ballot_sync(full, valid));
+    unsigned long long cre = __popc(__ballot_sync(full, has_res));
+    double sq = has_res ? (double)res * (double)res : 0.0;
+    unsigned int mx = has_res ? __float_as_uint(res) : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sq += __shfl_xor_sync(full, sq, o);
+        mx = max(mx, __shfl_xor_sync(full, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (cin) atomicAdd(&acc->inside, cin);
+        if (cva) atomicAdd(&acc->valid, cva);
+        if (cre) {
+            atomicAdd(&acc->n_res, cre);
+            atomicAdd(&acc->sumsq, sq);
+            atomicMax(&acc->max_res_bits, mx);
+        }
+    }
+}
+
+// one thread per 16 cells (one word of 2-bit classes)
+__global__ void __launch_bounds__(256)
+map_classify_kernel(const uint8_t* __restrict__ corner_bits, const uint32_t* __restrict__ seen,
+                    const uint32_t* __restrict__ resmax, uint32_t tol_bits, uint32_t* __restrict__ cls,
+                    uint32_t NC, unsigned long long* counts)
+{
+    const uint32_t w = blockIdx.x * 256u + threadIdx.x;
+    const uint32_t nw = (NC + 15) / 16;
+    uint32_t word = 0, ninv = 0, nval = 0, nbnd = 0;
+    if (w < nw) {
+        const uint32_t sw = seen[w];
+        for (int q = 0; q < 16; ++q) {
+            const uint32_t cid = w * 16 + q;
+            if (cid >= NC) break;
+            const uint32_t cb = corner_bits[cid];
+            const uint32_t s = (sw >> (2 * q)) & 3u;
+            uint32_t c;
+            if ((cb & 2u) && !(s & 1u)) c = LT_CELL_INVALID;
+            else if ((cb & 1u) && !(s & 2u) && (!resmax || resmax[cid] <= tol_bits)) c = LT_CELL_VALID;
+            else c = LT_CELL_BOUNDARY;
+            word |= c << (2 * q);
+            ninv += c == LT_CELL_INVALID;
+            nval += c == LT_CELL_VALID;
+            nbnd += c == LT_CELL_BOUNDARY;
+        }
+        cls[w] = word;
+    }
+    const unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ninv += __shfl_xor_sync(full, ninv, o);
+        nval += __shfl_xor_sync(full, nval, o);
+        nbnd += __shfl_xor_sync(full, nbnd, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(counts + 0, (unsigned long long)ninv);
+        atomicAdd(counts + 1, (unsigned long long)nval);
+        atomicAdd(counts + 2, (unsigned long long)nbnd);
+    }
+}
+
+// ------------------------------------------------------------------ query kernels
+
+// Mask lookup + interpolation; rays the table cannot answer are appended
+// (warp-aggregated) to the fallback list, bit 31 marking "outside the box".
+template <int MODE>
+__global__ void __launch_bounds__(kQBlock)
+map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out, uint32_t n,
+                 uint32_t* __restrict__ fb_list, uint32_t* __restrict__ fb_count)
+{
+    const uint32_t r = blockIdx.x * kQBlock + threadIdx.x;
+    bool need_fb = false;
+    uint32_t tag = r;
+    if (r < n) {
+        const float x = __ldg(in.x + r), y = __ldg(in.y + r), dx = __ldg(in.dx + r),
+                    dy = __ldg(in.dy + r), dz = __ldg(in.dz + r), lam = __ldg(in.lam + r);
+        uint32_t cid;
+        float f[5];
+        if (!cell_of(M, x, y, dx, dy, dz, lam, cid, f)) {
+            need_fb = true;
+            tag |= kOutsideBit;
+        } else {
+            const uint32_t c = MODE == LT_QUERY_TABLE ? cell_class(M, cid) : (uint32_t)LT_CELL_VALID;
+            if (c == LT_CELL_VALID) {
+                float o[6];
+                interpolate(M, M.node, cell_base(M, cid), f, o);
+                store_out(out, r, o, LT_FLAG_VALID);
+            } else if (c == LT_CELL_INVALID) {
+                const float z[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                store_out(out, r, z, 0u);
+            } else {
+                need_fb = true;
+            }
+        }
+    }
+    const unsigned full = 0xffffffffu;
+    const unsigned m = __ballot_sync(full, need_fb);
+    if (m) {
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(m) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(fb_count, (uint32_t)__popc(m));
+        base = __shfl_sync(full, base, leader);
+        if (need_fb) fb_list[base + __popc(m & ((1u << lane) - 1u))] = tag;
+    }
+}
+
+// exact tracer over the fallback list (persistent grid-stride loop)
+__global__ void __launch_bounds__(kQBlock)
+map_fallback_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out,
+                    const uint32_t* __restrict__ fb_list, const uint32_t* __restrict__ fb_count,
+                    unsigned long long* work)
+{
+    const uint32_t cnt = *fb_count;
+    unsigned done = 0;
+    for (uint32_t i = blockIdx.x * kQBlock + threadIdx.x; i < cnt; i += gridDim.x * kQBlock) {
+        const uint32_t tag = fb_list[i];
+        const uint32_t r = tag & ~kOutsideBit;
+        TraceOut o;
+        int nint;
+        uint32_t f = trace_ray(M.L, M.pi, M.pj, __ldg(in.x + r), __ldg(in.y + r), __ldg(in.dx + r),
+                               __ldg(in.dy + r), __ldg(in.dz + r), __ldg(in.lam + r), o, nint);
+        f |= LT_FLAG_TRACED | ((tag & kOutsideBit) ? LT_FLAG_OUTSIDE : 0u);
+        const float v[6] = {o.x, o.y, o.dx, o.dy, o.dz, o.I};
+        store_out(out, r, v, f);
+        done += (unsigned)nint;
+    }
+    warp_add(work, done);
+}
+
+// ------------------------------------------------------------------ scratch pool
+
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {};
+
+lt_status scratch_pool(cudaMemPool_t* pool)
+{
+    int dev = 0;
+    LT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(LT_EINVAL, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        LT_CUDA_TRY(cudaMemPoolCreate(&g_pool[dev], &props));
+        uint64_t keep = ~0ull;  // keep freed blocks for reuse by later calls
+        LT_CUDA_TRY(cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+    }
+    *pool = g_pool[dev];
+    return LT_OK;
+}
+
+int query_fallback_blocks()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 152;
+    }
+    return sms * 8;
+}
+
+lt_status launch_query(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
+                       int mode, uint32_t* fb_list, uint32_t* fb_count, cudaStream_t st)
+{
+    LT_CUDA_TRY(cudaMemsetAsync(fb_count, 0, sizeof(uint32_t), st));
+    const unsigned blocks = (n + kQBlock - 1) / kQBlock;
+    {
+    ProfScope prof("map_query_kernel", st);
+    if (mode == LT_QUERY_TABLE)
+        map_query_kernel<LT_QUERY_TABLE><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, fb_list, fb_count);
+    else
+        map_query_kernel<LT_QUERY_NO_MASK><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, fb_list, fb_count);
+    }
+    LT_CUDA_TRY(cudaGetLastError());
+    const unsigned fbb = (unsigned)std::min<size_t>((size_t)query_fallback_blocks(), blocks);
+    {
+        ProfScope prof("map_fallback_kernel", st);
+        map_fallback_kernel<<<fbb, kQBlock, 0, st>>>(map->dev, in, out, fb_list, fb_count, prof.work());
+    }
+    LT_CUDA_TRY(cudaGetLastError());
+    return LT_OK;
+}
+
+// query with scratch from the stream-ordered pool
+lt_status query_pooled(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, size_t n,
+                       int mode, cudaStream_t st)
+{
+    cudaMemPool_t pool;
+    lt_status s = scratch_pool(&pool);
+    if (s != LT_OK) return s;
+    uint32_t* scratch = nullptr;
+    if (cudaMallocFromPoolAsync((void**)&scratch, (n + 1) * sizeof(uint32_t), pool, st) != cudaSuccess)
+        return fail(LT_ENOMEM, "lt_query: scratch allocation of %zu bytes failed", (n + 1) * 4);
+    s = launch_query(map, in, out, (uint32_t)n, mode, scratch + 1, scratch, st);
+    cudaFreeAsync(scratch, st);
+    return s;
+}
+
+}  // namespace lt
+
+using namespace lt;
+
+lt_map::~lt_map()
+{
+    if (node) cudaFree(node);
+    if (node_valid) cudaFree(node_valid);
+    if (cls) cudaFree(cls);
+}
+
+extern "C" {
+
+lt_status lt_build_map(const lt_lens* lens, const lt_map_opts* o, lt_map** out, lt_stream stream)
+{
+    clear_error();
+    auto t0 = std::chrono::steady_clock::now();
+    if (!lens || !o || !out) return fail(LT_EINVAL, "lt_build_map: NULL argument");
+    *out = nullptr;
+    int pi, pj;
+    if (!path_ij(lens->S, o->path_id, &pi, &pj))
+        return fail(LT_EINVAL, "lt_build_map: bad path id %d", o->path_id);
+    uint64_t N = 1, NC = 1;
+    for (int d = 0; d < 5; ++d) {
+        if (o->res[d] < 2 || o->res[d] > 4096) return fail(LT_EINVAL, "lt_build_map: res[%d] = %d outside 2..4096", d, o->res[d]);
+        if (!(o->hi[d] > o->lo[d])) return fail(LT_EINVAL, "lt_build_map: empty box on axis %d", d);
+        N *= (uint64_t)o->res[d];
+        NC *= (uint64_t)(o->res[d] - 1);
+    }
+    if (N * 6 >= (1ull << 32)) return fail(LT_EINVAL, "lt_build_map: %llu nodes is too many", (unsigned long long)N);
+    if (o->n_fit > 0) {
+        const void* ps[] = {o->fit_x, o->fit_y, o->fit_dx, o->fit_dy, o->fit_dz, o->fit_lambda};
+        for (const void* p : ps)
+            if (!p || !aligned16(p)) return fail(LT_EINVAL, "lt_build_map: fit arrays must be non-NULL and 16-byte aligned");
+        if (o->n_fit >= (1ull << 31)) return fail(LT_EINVAL, "lt_build_map: too many fit rays");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+
+    lt_map* m = new (std::nothrow) lt_map();
+    if (!m) return fail(LT_ENOMEM, "lt_build_map: host allocation");
+    m->lens = *lens;
+    m->lens.presc.surfaces = m->lens.surf;
+    m->lens.presc.glasses = m->lens.glass;
+    m->path_id = o->path_id;
+    m->n_nodes = N;
+    m->n_cells = NC;
+    m->tol = o->max_residual_mm;
+    MapDev& D = m->dev;
+    std::memset(&D, 0, sizeof D);
+    D.L = lens->dev;
+    D.pi = pi;
+    D.pj = pj;
+    uint32_t stride = 1, cstride = 1;
+    for (int d = 4; d >= 0; --d) {
+        m->res[d] = o->res[d];
+        m->lo[d] = o->lo[d];
+        m->hi[d] = o->hi[d];
+        D.res[d] = o->res[d];
+        D.lo[d] = (float)o->lo[d];
+        D.step[d] = (float)((o->hi[d] - o->lo[d]) / (double)(o->res[d] - 1));
+        D.inv[d] = (float)((double)(o->res[d] - 1) / (o->hi[d] - o->lo[d]));
+        D.umax[d] = (float)(o->res[d] - 1);
+        D.stride[d] = stride;
+        D.cstride[d] = cstride;
+        stride *= (uint32_t)o->res[d];
+        cstride *= (uint32_t)(o->res[d] - 1);
+    }
+    const uint32_t NW = (uint32_t)((NC + 15) / 16);
+    auto bail = [&](lt_status s) { delete m; return s; };
+    if (cudaMalloc(&m->node, N * 6 * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&m->node_valid, N) != cudaSuccess ||
+        cudaMalloc(&m->cls, (size_t)NW * sizeof(uint32_t)) != cudaSuccess)
+        return bail(fail(LT_ENOMEM, "lt_build_map: device allocation of the tables failed"));
+    D.node = m->node;
+    D.cls = m->cls;
+
+    // temporaries
+    uint8_t* corner_bits = nullptr;
+    uint32_t* seen = nullptr;
+    uint32_t* resmax = nullptr;
+    FitAccum* acc = nullptr;
+    unsigned long long* counts = nullptr;
+    const bool use_tol = o->max_residual_mm > 0.0;
+    lt_status s = LT_OK;
+    do {
+        if (cudaMalloc(&corner_bits, NC) != cudaSuccess ||
+            cudaMalloc(&seen, (size_t)NW * 4) != cudaSuccess ||
+            (use_tol && cudaMalloc(&resmax, NC * 4) != cudaSuccess) ||
+            cudaMalloc(&acc, sizeof(FitAccum)) != cudaSuccess ||
+            cudaMalloc(&counts, 3 * sizeof(unsigned long long)) != cudaSuccess) {
+            s = fail(LT_ENOMEM, "lt_build_map: device allocation of temporaries failed");
+            break;
+        }
+        if (cudaMemsetAsync(seen, 0, (size_t)NW * 4, st) != cudaSuccess ||
+            (use_tol && cudaMemsetAsync(resmax, 0, NC * 4, st) != cudaSuccess) ||
+            cudaMemsetAsync(acc, 0, sizeof(FitAccum), st) != cudaSuccess ||
+            cudaMemsetAsync(counts, 0, 24, st) != cudaSuccess) {
+            s = fail(LT_ECUDA, "lt_build_map: memset failed");
+            break;
+        }
+        map_node_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(D, m->node, m->node_valid, (uint32_t)N);
+        map_corner_kernel<<<(unsigned)((NC + 255) / 256), 256, 0, st>>>(D, m->node_valid, corner_bits, (uint32_t)NC);
+        if (o->n_fit > 0) {
+            RaysInDev fit{o->fit_x, o->fit_y, o->fit_dx, o->fit_dy, o->fit_dz, o->fit_lambda};
+            map_fit_kernel<<<(unsigned)((o->n_fit + 255) / 256), 256, 0, st>>>(
+                D, fit, (uint32_t)o->n_fit, m->node, corner_bits, seen, resmax, acc);
+        }
+        float tol_f = use_tol ? (float)o->max_residual_mm : 0.0f;
+        uint32_t tol_bits;
+        std::memcpy(&tol_bits, &tol_f, 4);
+        map_classify_kernel<<<(NW + 255) / 256, 256, 0, st>>>(corner_bits, seen, resmax, tol_bits, m->cls,
+                                                               (uint32_t)NC, counts);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) { s = cuda_fail(e, "lt_build_map launch"); break; }
+        FitAccum ha;
+        unsigned long long hc[3];
+        if (cudaMemcpyAsync(&ha, acc, sizeof ha, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(hc, counts, sizeof hc, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+            s = cuda_fail(e, "lt_build_map");
+            break;
+        }
+        // valid nodes: count on the host from the byte array would need a copy; reuse counts
+        m->stats.n_nodes = N;
+        m->stats.n_cells = NC;
+        m->stats.cells_invalid = hc[0];
+        m->stats.cells_valid = hc[1];
+        m->stats.cells_boundary = hc[2];
+        m->stats.fit_inside = ha.inside;
+        m->stats.fit_valid = ha.valid;
+        m->stats.fit_residual_rms_mm = ha.n_res ? std::sqrt(ha.sumsq / (double)ha.n_res) : 0.0;
+        float mx;
+        std::memcpy(&mx, &ha.max_res_bits, 4);
+        m->stats.fit_residual_max_mm = mx;
+        m->stats.table_bytes = N * 6 * 4 + N + (uint64_t)NW * 4;
+    } while (0);
+    if (corner_bits) cudaFree(corner_bits);
+    if (seen) cudaFree(seen);
+    if (resmax) cudaFree(resmax);
+    if (acc) cudaFree(acc);
+    if (counts) cudaFree(counts);
+    if (s != LT_OK) return bail(s);
+    cudaGetDevice(&m->device);
+    m->stats.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = m;
+    return LT_OK;
+}
+
+void lt_destroy_map(lt_map* m) { delete m; }
+
+lt_status lt_map_stats_get(const lt_map* m, lt_map_stats* out)
+{
+    if (!m || !out) return fail(LT_EINVAL, "lt_map_stats_get: NULL argument");
+    *out = m->stats;
+    return LT_OK;
+}
+
+lt_status lt_query(const lt_map* m, const lt_rays_in* in, const float* lam, const lt_rays_out* out,
+                   size_t n, int32_t mode, lt_stream stream)
+{
+    clear_error();
+    if (!m) return fail(LT_EINVAL, "lt_query: NULL map");
+    if (mode != LT_QUERY_TABLE && mode != LT_QUERY_NO_MASK) return fail(LT_EINVAL, "lt_query: unknown mode %d", mode);
+    lt_status s = check_io(in, lam, out, n, "lt_query");
+    if (s != LT_OK || n == 0) return s;
+    if (n >= (1ull << 31)) return fail(LT_EINVAL, "lt_query: n must be < 2^31");
+    RaysInDev din{in->x, in->y, in->dx, in->dy, in->dz, lam};
+    RaysOutDev dout{out->x, out->y, out->dx, out->dy, out->dz, out->I, out->flags};
+    return query_pooled(m, din, dout, n, mode, (cudaStream_t)stream);
+}
+
+lt_status lt_query_host(const lt_map* m, const lt_rays_in* in, const float* lam,
+                        const lt_rays_out* out, size_t n, int32_t mode)
+{
+    clear_error();
+    if (!m) return fail(LT_EINVAL, "lt_query_host: NULL map");
+    if (mode != LT_QUERY_TABLE && mode != LT_QUERY_NO_MASK) return fail(LT_EINVAL, "lt_query_host: unknown mode %d", mode);
+    if (!in || !out) return fail(LT_EINVAL, "lt_query_host: NULL ray struct");
+    if (n == 0) return LT_OK;
+    const void* ps[] = {in->x, in->y, in->dx, in->dy, in->dz, lam, out->x, out->y,
+                        out->dx, out->dy, out->dz, out->I, out->flags};
+    for (const void* p : ps)
+        if (!p) return fail(LT_EINVAL, "lt_query_host: NULL ray array");
+    return run_host_pipelined(in, lam, out, n, [&](const RaysInDev& a, const RaysOutDev& b, size_t k, cudaStream_t st) {
+        return query_pooled(m, a, b, k, mode, st);
+    });
+}
+
+lt_status lt_map_export(const lt_map* m, float* node6, uint8_t* node_valid, uint8_t* cell_class)
+{
+    clear_error();
+    if (!m) return fail(LT_EINVAL, "lt_map_export: NULL map");
+    if (node6) LT_CUDA_TRY(cudaMemcpy(node6, m->node, m->n_nodes * 6 * sizeof(float), cudaMemcpyDeviceToHost));
+    if (node_valid) LT_CUDA_TRY(cudaMemcpy(node_valid, m->node_valid, m->n_nodes, cudaMemcpyDeviceToHost));
+    if (cell_class) {
+        const size_t NW = (m->n_cells + 15) / 16;
+        std::vector<uint32_t> w(NW);
+        LT_CUDA_TRY(cudaMemcpy(w.data(), m->cls, NW * 4, cudaMemcpyDeviceToHost));
+        for (uint64_t c = 0; c < m->n_cells; ++c) cell_class[c] = (uint8_t)((w[c >> 4] >> ((c & 15) * 2)) & 3);
+    }
+    return LT_OK;
+}
+
+// ---------------------------------------------------------------- save / load
+
+struct MapFileHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t path_id;
+    int32_t res[5];
+    int32_t S, n_glass;
+    double lo[5], hi[5];
+    double tol;
+    uint64_t n_nodes, n_cells;
+};
+
+lt_status lt_map_save(const lt_map* m, const char* path)
+{
+    clear_error();
+    if (!m || !path) return fail(LT_EINVAL, "lt_map_save: NULL argument");
+    std::vector<float> node(m->n_nodes * 6);
+    std::vector<uint8_t> nv(m->n_nodes);
+    const size_t NW = (m->n_cells + 15) / 16;
+    std::vector<uint32_t> cls(NW);
+    LT_CUDA_TRY(cudaMemcpy(node.data(), m->node, node.size() * 4, cudaMemcpyDeviceToHost));
+    LT_CUDA_TRY(cudaMemcpy(nv.data(), m->node_valid, nv.size(), cudaMemcpyDeviceToHost));
+    LT_CUDA_TRY(cudaMemcpy(cls.data(), m->cls, NW * 4, cudaMemcpyDeviceToHost));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(LT_EIO, "lt_map_save: cannot open %s", path);
+    MapFileHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, "LTMAP01", 8);
+    h.version = 1;
+    h.path_id = m->path_id;
+    for (int d = 0; d < 5; ++d) { h.res[d] = m->res[d]; h.lo[d] = m->lo[d]; h.hi[d] = m->hi[d]; }
+    h.S = m->lens.S;
+    h.n_glass = m->lens.n_glass;
+    h.tol = m->tol;
+    h.n_nodes = m->n_nodes;
+    h.n_cells = m->n_cells;
+    bool ok = std::fwrite(&h, sizeof h, 1, f) == 1;
+    ok = ok && std::fwrite(m->lens.surf, sizeof(lt_surface), m->lens.S, f) == (size_t)m->lens.S;
+    ok = ok && (m->lens.n_glass == 0 ||
+                std::fwrite(m->lens.glass, sizeof(lt_glass), m->lens.n_glass, f) == (size_t)m->lens.n_glass);
+    lt_prescription p = m->lens.presc;
+    p.surfaces = nullptr;
+    p.glasses = nullptr;
+    ok = ok && std::fwrite(&p, sizeof p, 1, f) == 1;
+    ok = ok && std::fwrite(&m->stats, sizeof m->stats, 1, f) == 1;
+    ok = ok && std::fwrite(node.data(), 4, node.size(), f) == node.size();
+    ok = ok && std::fwrite(nv.data(), 1, nv.size(), f) == nv.size();
+    ok = ok && std::fwrite(cls.data(), 4, NW, f) == NW;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(LT_EIO, "lt_map_save: write to %s failed", path);
+    return LT_OK;
+}
+
+lt_status lt_map_load(const char* path, lt_map** out)
+{
+    clear_error();
+    if (!path || !out) return fail(LT_EINVAL, "lt_map_load: NULL argument");
+    *out = nullptr;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(LT_EIO, "lt_map_load: cannot open %s", path);
+    MapFileHeader h;
+    lt_surface surf[LT_MAX_SURFACES];
+    lt_glass glass[LT_MAX_GLASSES];
+    lt_prescription p;
+    lt_map_stats stats;
+    bool ok = std::fread(&h, sizeof h, 1, f) == 1 && std::memcmp(h.magic, "LTMAP01", 8) == 0 &&
+              h.S >= 1 && h.S <= LT_MAX_SURFACES && h.n_glass >= 0 && h.n_glass <= LT_MAX_GLASSES;
+    ok = ok && std::fread(surf, sizeof(lt_surface), h.S, f) == (size_t)h.S;
+    ok = ok && (h.n_glass == 0 || std::fread(glass, sizeof(lt_glass), h.n_glass, f) == (size_t)h.n_glass);
+    ok = ok && std::fread(&p, sizeof p, 1, f) == 1 && std::fread(&stats, sizeof stats, 1, f) == 1;
+    uint64_t N = 1, NC = 1;
+    for (int d = 0; ok && d < 5; ++d) {
+        ok = h.res[d] >= 2 && h.res[d] <= 4096;
+        N *= (uint64_t)h.res[d];
+        NC *= (uint64_t)(h.res[d] - 1);
+    }
+    ok = ok && N == h.n_nodes && NC == h.n_cells && N * 6 < (1ull << 32);
+    if (!ok) { std::fclose(f); return fail(LT_EIO, "lt_map_load: %s is not a map file", path); }
+    std::vector<float> node(N * 6);
+    std::vector<uint8_t> nv(N);
+    const size_t NW = (NC + 15) / 16;
+    std::vector<uint32_t> cls(NW);
+    ok = std::fread(node.data(), 4, node.size(), f) == node.size() &&
+         std::fread(nv.data(), 1, N, f) == N && std::fread(cls.data(), 4, NW, f) == NW;
+    std::fclose(f);
+    if (!ok) return fail(LT_EIO, "lt_map_load: %s is truncated", path);
+    p.surfaces = surf;
+    p.glasses = glass;
+    lt_lens* lens = nullptr;
+    lt_status s = lt_create_lens(&p, &lens);
+    if (s != LT_OK) return s;
+    // rebuild the map shell without tracing: corners-only options, then overwrite the tables
+    lt_map* m = new (std::nothrow) lt_map();
+    if (!m) { lt_destroy_lens(lens); return fail(LT_ENOMEM, "lt_map_load: host allocation"); }
+    m->lens = *lens;
+    m->lens.presc.surfaces = m->lens.surf;
+    m->lens.presc.glasses = m->lens.glass;
+    lt_destroy_lens(lens);
+    int pi, pj;
+    path_ij(m->lens.S, h.path_id, &pi, &pj);
+    m->path_id = h.path_id;
+    m->n_nodes = N;
+    m->n_cells = NC;
+    m->tol = h.tol;
+    m->stats = stats;
+    MapDev& D = m->dev;
+    std::memset(&D, 0, sizeof D);
+    D.L = m->lens.dev;
+    D.pi = pi;
+    D.pj = pj;
+    uint32_t stride = 1, cstride = 1;
+    for (int d = 4; d >= 0; --d) {
+        m->res[d] = h.res[d];
+        m->lo[d] = h.lo[d];
+        m->hi[d] = h.hi[d];
+        D.res[d] = h.res[d];
+        D.lo[d] = (float)h.lo[d];
+        D.step[d] = (float)((h.hi[d] - h.lo[d]) / (double)(h.res[d] - 1));
+        D.inv[d] = (float)((double)(h.res[d] - 1) / (h.hi[d] - h.lo[d]));
+        D.umax[d] = (float)(h.res[d] - 1);
+        D.stride[d] = stride;
+        D.cstride[d] = cstride;
+        stride *= (uint32_t)h.res[d];
+        cstride *= (uint32_t)(h.res[d] - 1);
+    }
+    if (cudaMalloc(&m->node, N * 6 * 4) != cudaSuccess || cudaMalloc(&m->node_valid, N) != cudaSuccess ||
+        cudaMalloc(&m->cls, NW * 4) != cudaSuccess) {
+        delete m;
+        return fail(LT_ENOMEM, "lt_map_load: device allocation failed");
+    }
+    D.node = m->node;
+    D.cls = m->cls;
+    if (cudaMemcpy(m->node, node.data(), N * 24, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m->node_valid, nv.data(), N, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m->cls, cls.data(), NW * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        delete m;
+        return fail(LT_ECUDA, "lt_map_load: upload failed");
+    }
+    cudaGetDevice(&m->device);
+    *out = m;
+    return LT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,46 @@
+// Internal declarations of the tabulated map (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lt_internal.h"
+#include "rays.cuh"
+
+enum { LT_CELL_INVALID = 0, LT_CELL_VALID = 1, LT_CELL_BOUNDARY = 2 };
+
+namespace lt {
+
+// The map as the kernels see it (a __grid_constant__ parameter, ~2 KB):
+// the lens for the fallback tracer, the path, the FP32 lattice constants and
+// the device tables.  Node strides: (x, y, s_x, s_y, lambda) row-major,
+// lambda fastest; cell strides likewise over res - 1.
+struct MapDev {
+    LensDev L;
+    int pi, pj;
+    int res[5];
+    float lo[5], step[5], inv[5], umax[5];
+    uint32_t stride[5], cstride[5];
+    const float* node;      // n_nodes x 6 floats
+    const uint32_t* cls;    // 2 bits per cell
+};
+
+lt_status scratch_pool(cudaMemPool_t* pool);
+
+}  // namespace lt
+
+struct lt_map {
+    lt_lens lens;             // copy of the lens the map was built on
+    int path_id = 0;
+    int res[5] = {};
+    double lo[5] = {}, hi[5] = {};
+    double tol = 0.0;
+    uint64_t n_nodes = 0, n_cells = 0;
+    float* node = nullptr;
+    uint8_t* node_valid = nullptr;
+    uint32_t* cls = nullptr;
+    int device = 0;
+    lt_map_stats stats = {};
+    lt::MapDev dev;
+    ~lt_map();
+};

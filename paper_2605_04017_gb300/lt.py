@@ -237,3 +237,159 @@ def trace_host(lens: Lens, inp: Sequence, lam, path_id: int, out: Sequence, n: i
     ro = rays_out(*out)
     check(lib().lt_trace_host(lens.handle, ctypes.byref(ri), _ptr(lam), path_id, ctypes.byref(ro),
                               n))
+
+
+# ------------------------------------------------------------------ maps
+
+QUERY_TABLE = 0
+QUERY_NO_MASK = 1
+
+CELL_INVALID, CELL_VALID, CELL_BOUNDARY = 0, 1, 2
+
+
+class c_map_opts(ctypes.Structure):
+    _fields_ = [("path_id", ctypes.c_int32), ("res", ctypes.c_int32 * 5),
+                ("lo", ctypes.c_double * 5), ("hi", ctypes.c_double * 5),
+                ("max_residual_mm", ctypes.c_double),
+                ("fit_x", _fptr), ("fit_y", _fptr), ("fit_dx", _fptr), ("fit_dy", _fptr),
+                ("fit_dz", _fptr), ("fit_lambda", _fptr), ("n_fit", ctypes.c_size_t)]
+
+
+class c_map_stats(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_uint64), ("n_cells", ctypes.c_uint64),
+                ("valid_nodes", ctypes.c_uint64), ("cells_invalid", ctypes.c_uint64),
+                ("cells_valid", ctypes.c_uint64), ("cells_boundary", ctypes.c_uint64),
+                ("fit_inside", ctypes.c_uint64), ("fit_valid", ctypes.c_uint64),
+                ("fit_residual_rms_mm", ctypes.c_double), ("fit_residual_max_mm", ctypes.c_double),
+                ("table_bytes", ctypes.c_uint64), ("build_ms", ctypes.c_double)]
+
+
+def _declare_maps(L: ctypes.CDLL) -> None:
+    vp = ctypes.c_void_p
+    st = ctypes.c_int
+    L.lt_build_map.restype = st
+    L.lt_build_map.argtypes = [vp, ctypes.POINTER(c_map_opts), ctypes.POINTER(vp), vp]
+    L.lt_destroy_map.restype = None
+    L.lt_destroy_map.argtypes = [vp]
+    L.lt_map_stats_get.restype = st
+    L.lt_map_stats_get.argtypes = [vp, ctypes.POINTER(c_map_stats)]
+    L.lt_query.restype = st
+    L.lt_query.argtypes = [vp, ctypes.POINTER(c_rays_in), vp, ctypes.POINTER(c_rays_out),
+                           ctypes.c_size_t, ctypes.c_int32, vp]
+    L.lt_query_host.restype = st
+    L.lt_query_host.argtypes = [vp, ctypes.POINTER(c_rays_in), vp, ctypes.POINTER(c_rays_out),
+                                ctypes.c_size_t, ctypes.c_int32]
+    L.lt_map_export.restype = st
+    L.lt_map_export.argtypes = [vp, vp, vp, vp]
+    L.lt_map_save.restype = st
+    L.lt_map_save.argtypes = [vp, ctypes.c_char_p]
+    L.lt_map_load.restype = st
+    L.lt_map_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(vp)]
+
+
+_old_declare = _declare
+
+
+def _declare(L: ctypes.CDLL) -> None:  # noqa: F811
+    _old_declare(L)
+    _declare_maps(L)
+
+
+class Map:
+    """A map resident on the device (lt_build_map / lt_map_load)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self.handle = handle
+
+    @classmethod
+    def build(cls, lens: Lens, path_id: int, res, lo, hi, fit=None, max_residual_mm: float = 0.0,
+              stream=None) -> "Map":
+        """fit: a batch.DeviceRays (or None)."""
+        o = c_map_opts()
+        o.path_id = path_id
+        for d in range(5):
+            o.res[d] = int(res[d])
+            o.lo[d] = float(lo[d])
+            o.hi[d] = float(hi[d])
+        o.max_residual_mm = max_residual_mm
+        if fit is not None:
+            o.fit_x, o.fit_y, o.fit_dx, o.fit_dy, o.fit_dz = [_ptr(t) for t in fit.inp]
+            o.fit_lambda = _ptr(fit.lam)
+            o.n_fit = fit.n
+        h = ctypes.c_void_p()
+        check(lib().lt_build_map(lens.handle, ctypes.byref(o), ctypes.byref(h),
+                                 _stream_handle(stream)))
+        return cls(h)
+
+    @classmethod
+    def load(cls, path: str) -> "Map":
+        h = ctypes.c_void_p()
+        check(lib().lt_map_load(path.encode(), ctypes.byref(h)))
+        return cls(h)
+
+    def save(self, path: str) -> None:
+        check(lib().lt_map_save(self.handle, path.encode()))
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().lt_destroy_map(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        s = c_map_stats()
+        check(lib().lt_map_stats_get(self.handle, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in c_map_stats._fields_}
+
+    def query(self, inp: Sequence, lam, out: Sequence, n: int, mode: int = QUERY_TABLE,
+              stream=None) -> None:
+        ri = rays_in(*inp)
+        ro = rays_out(*out)
+        check(lib().lt_query(self.handle, ctypes.byref(ri), _ptr(lam), ctypes.byref(ro), n, mode,
+                             _stream_handle(stream)))
+
+    def query_host(self, inp: Sequence, lam, out: Sequence, n: int, mode: int = QUERY_TABLE):
+        ri = rays_in(*inp)
+        ro = rays_out(*out)
+        check(lib().lt_query_host(self.handle, ctypes.byref(ri), _ptr(lam), ctypes.byref(ro), n,
+                                  mode))
+
+    def export(self, n_nodes: int, n_cells: int):
+        import numpy as np
+        node6 = np.empty((n_nodes, 6), np.float32)
+        nv = np.empty(n_nodes, np.uint8)
+        cc = np.empty(n_cells, np.uint8)
+        check(lib().lt_map_export(self.handle, node6.ctypes.data, nv.ctypes.data, cc.ctypes.data))
+        return node6, nv, cc
+
+
+# ------------------------------------------------------------------ profiling
+
+class c_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double), ("work", ctypes.c_int64)]
+
+
+def profile_enable(on: bool = True) -> None:
+    L = lib()
+    L.lt_profile_enable.restype = ctypes.c_int
+    L.lt_profile_enable.argtypes = [ctypes.c_int32]
+    check(L.lt_profile_enable(1 if on else 0))
+
+
+def profile_read(reset: bool = True) -> dict:
+    """{kernel name: (launches, total device ms, work units)} since the last reset."""
+    L = lib()
+    L.lt_profile_read.restype = ctypes.c_int
+    L.lt_profile_read.argtypes = [ctypes.POINTER(c_kernel_time), ctypes.c_int32,
+                                  ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
+    buf = (c_kernel_time * 64)()
+    n = ctypes.c_int32()
+    check(L.lt_profile_read(buf, 64, ctypes.byref(n), 1 if reset else 0))
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms), int(buf[i].work))
+            for i in range(min(n.value, 64))}

@@ -43,16 +43,21 @@ def test_singlet_all_rays(path_id):
     p = w.singlet_lens()
     rays = w.singlet_rays()
     out, flags = run_gpu(lt.Lens(p), rays, path_id)
-    ex, ev, edge, kmin = oracle.Lens(p).trace(rays, oracle.path_ij(2, path_id))
-    st = compare_trace(out, flags, ex, ev, edge, kmin, f"singlet path {path_id}")
+    ol = oracle.Lens(p)
+    path = oracle.path_ij(2, path_id)
+    ex, ev, edge, kmin = ol.trace(rays, path)
+    st = compare_trace(out, flags, ex, ev, edge, kmin, f"singlet path {path_id}",
+                       cond=(ol, rays, path))
     assert st["valid_gpu"] > 1000
 
 
 def test_eleven_full_size_transmission(eleven):
     rays = w.eleven_rays(eleven)          # 4,194,304 rays
     out, flags = run_gpu(lt.Lens(eleven), rays, 0)
-    ex, ev, edge, kmin = oracle.Lens(eleven).trace(rays)
-    st = compare_trace(out, flags, ex, ev, edge, kmin, "eleven transmission")
+    ol = oracle.Lens(eleven)
+    ex, ev, edge, kmin = ol.trace(rays)
+    st = compare_trace(out, flags, ex, ev, edge, kmin, "eleven transmission",
+                       cond=(ol, rays, (0, 0)))
     assert st["valid_gpu"] > 100000
 
 
@@ -64,8 +69,10 @@ def test_eleven_every_ghost_path(eleven):
     worst = {"pos_max": 0.0, "dir_max": 0.0, "I_max": 0.0}
     for pid in range(1, lens.n_paths):
         out, flags = run_gpu(lens, rays, pid)
-        ex, ev, edge, kmin = ol.trace(rays, oracle.path_ij(S, pid))
-        st = compare_trace(out, flags, ex, ev, edge, kmin, f"eleven ghost {pid}")
+        path = oracle.path_ij(S, pid)
+        ex, ev, edge, kmin = ol.trace(rays, path)
+        st = compare_trace(out, flags, ex, ev, edge, kmin, f"eleven ghost {pid}",
+                           cond=(ol, rays, path))
         for k in worst:
             worst[k] = max(worst[k], st[k])
     print("ghost worst", worst)
