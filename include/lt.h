@@ -239,6 +239,27 @@ lt_status lt_query(const lt_map* map, const lt_rays_in* in, const float* lambda_
 lt_status lt_query_host(const lt_map* map, const lt_rays_in* in, const float* lambda_nm,
                         const lt_rays_out* out, size_t n, int32_t mode);
 
+/* Map query that allocates nothing.  The paper has no counterpart: this is a
+ * deployment aid.  Some callers cannot allocate GPU memory while they run --
+ * a renderer or serving process that reserves the whole device at start-up
+ * with its own allocator, or a loop where any cudaMalloc (and the implicit
+ * synchronisation it can bring) is not allowed.  lt_query takes a small
+ * fallback list from a stream-ordered pool; this variant instead uses one
+ * fixed array compiled into the library: LT_NOALLOC_MAX_RAYS + 64 uint32
+ * words (about 4 MiB), present on every GPU that loads the library and held
+ * until the process exits.
+ *   - Same arguments, results and errors as lt_query; n > LT_NOALLOC_MAX_RAYS
+ *     is rejected with LT_EINVAL (split larger batches).
+ *   - The first call on each device looks up the array's device address
+ *     (once per device, with that device current); make that first call
+ *     before any stream capture.
+ *   - All calls share the one array: calls whose work overlaps on the GPU
+ *     (other streams, other threads) race and must be serialised by the
+ *     caller.  Each call clears the part that must start at zero. */
+#define LT_NOALLOC_MAX_RAYS (1 << 20)
+lt_status lt_query_noalloc(const lt_map* map, const lt_rays_in* in, const float* lambda_nm,
+                           const lt_rays_out* out, size_t n, int32_t mode, lt_stream stream);
+
 /* Copy the map to host memory for inspection: node6 (n_nodes x 6 floats),
  * node_valid (n_nodes bytes, 1/0), cell_class (n_cells bytes: 0 INVALID,
  * 1 VALID, 2 BOUNDARY).  Any pointer may be NULL. */

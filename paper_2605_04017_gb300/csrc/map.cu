@@ -776,3 +776,50 @@ lt_status lt_map_load(const char* path, lt_map** out)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free query
+
+// The fallback-list scratch of lt_query_noalloc: word 0 is the list length,
+// the list starts at word 64 (256-byte aligned).  In host code the name of
+// this array is only a stand-in; the device address comes from
+// cudaGetSymbolAddress, looked up once per device below.
+static __device__ __align__(256) uint32_t g_noalloc_scratch[LT_NOALLOC_MAX_RAYS + 64];
+
+namespace {
+std::mutex g_noalloc_mu;
+uint32_t* g_noalloc_addr[64] = {};
+}  // namespace
+
+extern "C" lt_status lt_query_noalloc(const lt_map* m, const lt_rays_in* in, const float* lam,
+                                      const lt_rays_out* out, size_t n, int32_t mode,
+                                      lt_stream stream)
+{
+    clear_error();
+    if (!m) return fail(LT_EINVAL, "lt_query_noalloc: NULL map");
+    if (mode != LT_QUERY_TABLE && mode != LT_QUERY_NO_MASK)
+        return fail(LT_EINVAL, "lt_query_noalloc: unknown mode %d", mode);
+    if (n > (size_t)LT_NOALLOC_MAX_RAYS)
+        return fail(LT_EINVAL, "lt_query_noalloc: n = %zu exceeds LT_NOALLOC_MAX_RAYS (%d); split the batch",
+                    n, LT_NOALLOC_MAX_RAYS);
+    lt_status s = check_io(in, lam, out, n, "lt_query_noalloc");
+    if (s != LT_OK || n == 0) return s;
+    int dev = 0;
+    LT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(LT_EINVAL, "lt_query_noalloc: device index %d out of range", dev);
+    uint32_t* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "lt_query_noalloc: cudaGetSymbolAddress");
+            g_noalloc_addr[dev] = static_cast<uint32_t*>(p);
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    RaysInDev din{in->x, in->y, in->dx, in->dy, in->dz, lam};
+    RaysOutDev dout{out->x, out->y, out->dx, out->dy, out->dz, out->I, out->flags};
+    // launch_query clears the list length (word 0) on `stream` before the kernels
+    return launch_query(m, din, dout, (uint32_t)n, mode, scratch + 64, scratch,
+                        (cudaStream_t)stream);
+}

@@ -393,3 +393,23 @@ def profile_read(reset: bool = True) -> dict:
     check(L.lt_profile_read(buf, 64, ctypes.byref(n), 1 if reset else 0))
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms), int(buf[i].work))
             for i in range(min(n.value, 64))}
+
+
+# ------------------------------------------------------------------ allocation-free query
+
+NOALLOC_MAX_RAYS = 1 << 20
+
+
+def query_noalloc(gmap: "Map", inp: Sequence, lam, out: Sequence, n: int,
+                  mode: int = QUERY_TABLE, stream=None) -> None:
+    """lt_query_noalloc: the map query for callers that cannot allocate GPU
+    memory; its scratch is a fixed array inside the library (n <= 2^20)."""
+    L = lib()
+    L.lt_query_noalloc.restype = ctypes.c_int
+    L.lt_query_noalloc.argtypes = [ctypes.c_void_p, ctypes.POINTER(c_rays_in), ctypes.c_void_p,
+                                   ctypes.POINTER(c_rays_out), ctypes.c_size_t, ctypes.c_int32,
+                                   ctypes.c_void_p]
+    ri = rays_in(*inp)
+    ro = rays_out(*out)
+    check(L.lt_query_noalloc(gmap.handle, ctypes.byref(ri), _ptr(lam), ctypes.byref(ro), n, mode,
+                             _stream_handle(stream)))
