@@ -206,13 +206,6 @@ lt_status lt_create_lens(const lt_prescription* p, lt_lens** out)
     LensDev& D = L->dev;
     std::memset(&D, 0, sizeof D);
     D.S = S;
-    for (int k = 0; k < S; ++k) D.th[k] = (float)(L->zv[k + 1] - L->zv[k]);
-    for (int k = 1; k <= S; ++k) {
-        const double a = L->surf[k - 1].aperture_r;
-        D.c[k] = (float)L->surf[k - 1].curvature;
-        D.ap2[k] = (float)(a * a);
-        D.eps2a[k] = (float)(2.0 * a * eps);
-    }
     D.med[0] = -1;
     for (int k = 1; k <= S; ++k) D.med[k] = (int8_t)L->surf[k - 1].glass_after;
     D.med[S] = -1;
@@ -225,6 +218,22 @@ lt_status lt_create_lens(const lt_prescription* p, lt_lens** out)
             D.gSB[g][i] = (float)G.B3[i];
             D.gSC[g][i] = (float)G.C3[i];
         }
+    }
+    for (int k = 1; k <= S; ++k) {
+        const double a = L->surf[k - 1].aperture_r;
+        SurfRec& r = D.s[k];
+        r.c = (float)L->surf[k - 1].curvature;
+        r.th_before = (float)(L->zv[k] - L->zv[k - 1]);
+        r.th_after = k < S ? (float)(L->zv[k + 1] - L->zv[k]) : 0.0f;
+        r.ap2 = (float)(a * a);
+        r.eps2a = (float)(2.0 * a * eps);
+        const int gb = D.med[k - 1], ga = D.med[k];
+        r.A_before = gb < 0 ? 1.0f : D.gA[gb];
+        r.B_before = gb < 0 ? 0.0f : D.gB[gb];
+        r.A_after = ga < 0 ? 1.0f : D.gA[ga];
+        r.B_after = ga < 0 ? 0.0f : D.gB[ga];
+        r.g_before = (float)gb;
+        r.g_after = (float)ga;
     }
     if (p->stop_r > 0.0) {
         const int g = p->stop_after;

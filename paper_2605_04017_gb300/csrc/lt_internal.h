@@ -24,14 +24,22 @@ void clear_error();
 constexpr int kMaxS = LT_MAX_SURFACES;
 constexpr int kMaxG = LT_MAX_GLASSES;
 
+// One surface as the tracer reads it (48 bytes): both neighbouring media are
+// resolved, so an interaction evaluates one dispersion formula.
+struct __align__(16) SurfRec {
+    float c, th_before, th_after, ap2;          // curvature, vertex gaps to s-1 and s+1, aperture^2
+    float eps2a, A_before, B_before, A_after;   // near-edge band on r^2; Cauchy (A, B) of media s-1, s
+    float B_after, g_before, g_after, pad;      // glass ids of media s-1, s (as float; -1 air)
+};
+
 // The lens as the kernels see it: FP32, passed by value as a __grid_constant__
-// kernel parameter (a few KB, read through the constant cache; every lane of a
-// warp reads the same surface at the same time).
+// kernel parameter (about 2.7 KB, read through the constant cache; the lanes
+// of a warp read the same surface at the same time).
 //
 // Axial positions are kept relative to the vertex the ray last met, so the
 // FP32 z of a ray stays within a few mm of zero: vertex 0 is the entrance
-// plane z = 0, vertex k (1..S) the vertex of surface k, and
-//   th[k] = z(vertex k+1) - z(vertex k)   (k = 0..S-1, th[0] = entrance gap).
+// plane z = 0, vertex k (1..S) the vertex of surface k; s[k].th_before is the
+// gap from vertex k-1 to k and s[k].th_after the gap from k to k+1.
 struct LensDev {
     int S;                  // optical surfaces
     int stop_gap;           // stop in gap g (between vertex g and g+1; g = S: behind the last surface); -1 none
@@ -40,10 +48,7 @@ struct LensDev {
     float eps2a_stop;       // near-edge band on r^2: 2 * a * eps
     float z_img_rel;        // image plane z relative to vertex S
     float grazing_k;        // k below which a refraction is flagged ill-conditioned
-    float c[kMaxS + 1];     // curvature of surface k (index 1..S)
-    float th[kMaxS + 1];    // vertex gaps
-    float ap2[kMaxS + 1];   // clear aperture radius squared
-    float eps2a[kMaxS + 1]; // near-edge band on r^2
+    SurfRec s[kMaxS + 1];   // surfaces 1..S
     int8_t med[kMaxS + 2];  // glass of medium m (0..S); -1 = air
     int8_t gkind[kMaxG];
     float gA[kMaxG], gB[kMaxG];

@@ -90,9 +90,13 @@ __device__ __forceinline__ uint32_t cell_base(const MapDev& M, uint32_t cid)
     return base;
 }
 
-// Multilinear interpolation over the 32 corners: lerp each lambda-adjacent
-// node pair (48 contiguous bytes, three 8-byte-aligned loads per node), then
-// weight the 16 (x, y, s_x, s_y) corners.  Direction renormalised.
+// Node records are 8 floats (32 bytes): x, y, dx, dy, dz, I, 0, 0.  The two
+// lambda-adjacent nodes of a cell corner are then 64 contiguous, 64-byte
+// aligned bytes: one sector pair, fetched by four 16-byte loads.
+constexpr int kNodeFloats = 8;
+
+// Scalar multilinear interpolation (one thread, 16 corner pairs) -- used by the
+// map build; the query kernel uses the warp-cooperative form below.
 __device__ __forceinline__ void interpolate(const MapDev& M, const float* __restrict__ node,
                                             uint32_t base, const float f[5], float o[6])
 {
@@ -100,21 +104,20 @@ __device__ __forceinline__ void interpolate(const MapDev& M, const float* __rest
     const float w2[2] = {1.0f - f[2], f[2]}, w3[2] = {1.0f - f[3], f[3]};
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const float fl = f[4];
-#pragma unroll
+#pragma unroll 4
     for (int c = 0; c < 16; ++c) {
         const int b0 = (c >> 3) & 1, b1 = (c >> 2) & 1, b2 = (c >> 1) & 1, b3 = c & 1;
         const uint32_t off = base + b0 * M.stride[0] + b1 * M.stride[1] + b2 * M.stride[2] +
                              b3 * M.stride[3];
-        const float2* p = reinterpret_cast<const float2*>(node + (size_t)off * 6);
-        const float2 a0 = __ldg(p + 0), a1 = __ldg(p + 1), a2 = __ldg(p + 2);
-        const float2 c0 = __ldg(p + 3), c1 = __ldg(p + 4), c2 = __ldg(p + 5);
+        const float4* p = reinterpret_cast<const float4*>(node + (size_t)off * kNodeFloats);
+        const float4 a0 = __ldg(p + 0), a1 = __ldg(p + 1), c0 = __ldg(p + 2), c1 = __ldg(p + 3);
         const float w = (w0[b0] * w1[b1]) * (w2[b2] * w3[b3]);
         acc[0] = fmaf(w, fmaf(fl, c0.x - a0.x, a0.x), acc[0]);
         acc[1] = fmaf(w, fmaf(fl, c0.y - a0.y, a0.y), acc[1]);
-        acc[2] = fmaf(w, fmaf(fl, c1.x - a1.x, a1.x), acc[2]);
-        acc[3] = fmaf(w, fmaf(fl, c1.y - a1.y, a1.y), acc[3]);
-        acc[4] = fmaf(w, fmaf(fl, c2.x - a2.x, a2.x), acc[4]);
-        acc[5] = fmaf(w, fmaf(fl, c2.y - a2.y, a2.y), acc[5]);
+        acc[2] = fmaf(w, fmaf(fl, c0.z - a0.z, a0.z), acc[2]);
+        acc[3] = fmaf(w, fmaf(fl, c0.w - a0.w, a0.w), acc[3]);
+        acc[4] = fmaf(w, fmaf(fl, c1.x - a1.x, a1.x), acc[4]);
+        acc[5] = fmaf(w, fmaf(fl, c1.y - a1.y, a1.y), acc[5]);
     }
     const float n2 = fmaf(acc[2], acc[2], fmaf(acc[3], acc[3], acc[4] * acc[4]));
     float inv = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
@@ -141,6 +144,8 @@ __device__ __forceinline__ void store_out(const RaysOutDev& out, uint32_t r, con
 
 // ------------------------------------------------------------------ build kernels
 
+// every lattice node traced exactly (one thread per node)
+template <bool CAUCHY>
 __global__ void __launch_bounds__(256)
 map_node_kernel(const __grid_constant__ MapDev M, float* __restrict__ node,
                 uint8_t* __restrict__ node_valid, uint32_t N)
@@ -158,11 +163,11 @@ map_node_kernel(const __grid_constant__ MapDev M, float* __restrict__ node,
     node_ray(M, idx, ray);
     TraceOut o;
     int nint;
-    const uint32_t f = trace_ray(M.L, M.pi, M.pj, ray[0], ray[1], ray[2], ray[3], ray[4], ray[5], o, nint);
-    float2* p = reinterpret_cast<float2*>(node + (size_t)l * 6);
-    p[0] = make_float2(o.x, o.y);
-    p[1] = make_float2(o.dx, o.dy);
-    p[2] = make_float2(o.dz, o.I);
+    const uint32_t f = trace_ray<CAUCHY>(M.L, M.pi, M.pj, ray[0], ray[1], ray[2], ray[3], ray[4],
+                                         ray[5], o, nint);
+    float4* p = reinterpret_cast<float4*>(node + (size_t)l * kNodeFloats);
+    p[0] = make_float4(o.x, o.y, o.dx, o.dy);
+    p[1] = make_float4(o.dz, o.I, 0.0f, 0.0f);
     node_valid[l] = (uint8_t)(f & LT_FLAG_VALID);
 }
 
@@ -193,6 +198,7 @@ struct FitAccum {
 
 // one thread per fit ray: mark the cell as having seen a valid / invalid ray,
 // and for valid rays in all-valid-corner cells reduce the interpolation residual
+template <bool CAUCHY>
 __global__ void __launch_bounds__(256)
 map_fit_kernel(const __grid_constant__ MapDev M, RaysInDev fit, uint32_t nfit,
                const float* __restrict__ node, const uint8_t* __restrict__ corner_bits,
@@ -210,7 +216,8 @@ map_fit_kernel(const __grid_constant__ MapDev M, RaysInDev fit, uint32_t nfit,
         if (inside) {
             TraceOut o;
             int nint;
-            valid = (trace_ray(M.L, M.pi, M.pj, x, y, dx, dy, dz, lam, o, nint) & LT_FLAG_VALID) != 0;
+            valid = (trace_ray<CAUCHY>(M.L, M.pi, M.pj, x, y, dx, dy, dz, lam, o, nint) &
+                     LT_FLAG_VALID) != 0;
             atomicOr(seen + (cid >> 4), (valid ? 1u : 2u) << ((cid & 15u) * 2u));
             if (valid && (__ldg(corner_bits + cid) & 1)) {
                 float ip[6];
@@ -287,30 +294,55 @@ map_classify_kernel(const uint8_t* __restrict__ corner_bits, const uint32_t* __r
 
 // ------------------------------------------------------------------ query kernels
 
-// Mask lookup + interpolation; rays the table cannot answer are appended
-// (warp-aggregated) to the fallback list, bit 31 marking "outside the box".
+// A ray of the block waiting for interpolation: its index, the node index of
+// its cell's first corner and its FP32 position inside the cell.
+struct __align__(16) InterpItem {
+    uint32_t r, base;
+    float f[5];
+    float pad;
+};
+
+__device__ __forceinline__ float4 shfl_xor4(float4 v, int m)
+{
+    const unsigned full = 0xffffffffu;
+    v.x = __shfl_xor_sync(full, v.x, m);
+    v.y = __shfl_xor_sync(full, v.y, m);
+    v.z = __shfl_xor_sync(full, v.z, m);
+    v.w = __shfl_xor_sync(full, v.w, m);
+    return v;
+}
+
+// Mask lookup for a block of 256 rays, then warp-cooperative interpolation.
+// INVALID cells are answered at once; rays the table cannot answer are
+// appended (warp-aggregated) to the fallback list, bit 31 marking "outside
+// the box"; VALID cells are queued in shared memory.  Each warp then takes
+// one queued ray at a time: lane l loads 16 bytes (part l & 3) of the corner
+// pair 8h + (l >> 2) in round h = 0, 1, so a warp instruction fetches eight
+// whole 64-byte pairs (one L1 wavefront each) instead of 32 scattered words;
+// shuffles pair the two lambda nodes and sum the 16 weighted corners.
 template <int MODE>
 __global__ void __launch_bounds__(kQBlock)
 map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out, uint32_t n,
                  uint32_t* __restrict__ fb_list, uint32_t* __restrict__ fb_count)
 {
+    __shared__ InterpItem q[kQBlock];
+    __shared__ uint32_t qn;
+    if (threadIdx.x == 0) qn = 0;
+    __syncthreads();
     const uint32_t r = blockIdx.x * kQBlock + threadIdx.x;
-    bool need_fb = false;
-    uint32_t tag = r;
+    bool need_fb = false, need_ip = false;
+    uint32_t tag = r, cid = 0;
+    float f[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     if (r < n) {
         const float x = __ldg(in.x + r), y = __ldg(in.y + r), dx = __ldg(in.dx + r),
                     dy = __ldg(in.dy + r), dz = __ldg(in.dz + r), lam = __ldg(in.lam + r);
-        uint32_t cid;
-        float f[5];
         if (!cell_of(M, x, y, dx, dy, dz, lam, cid, f)) {
             need_fb = true;
             tag |= kOutsideBit;
         } else {
             const uint32_t c = MODE == LT_QUERY_TABLE ? cell_class(M, cid) : (uint32_t)LT_CELL_VALID;
             if (c == LT_CELL_VALID) {
-                float o[6];
-                interpolate(M, M.node, cell_base(M, cid), f, o);
-                store_out(out, r, o, LT_FLAG_VALID);
+                need_ip = true;
             } else if (c == LT_CELL_INVALID) {
                 const float z[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 store_out(out, r, z, 0u);
@@ -320,18 +352,77 @@ map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out,
         }
     }
     const unsigned full = 0xffffffffu;
-    const unsigned m = __ballot_sync(full, need_fb);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    unsigned m = __ballot_sync(full, need_ip);
     if (m) {
-        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(m) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(&qn, (uint32_t)__popc(m));
+        base = __shfl_sync(full, base, leader);
+        if (need_ip) {
+            InterpItem e;
+            e.r = r;
+            e.base = cell_base(M, cid);
+#pragma unroll
+            for (int d = 0; d < 5; ++d) e.f[d] = f[d];
+            e.pad = 0.0f;
+            q[base + __popc(m & lt_mask)] = e;
+        }
+    }
+    m = __ballot_sync(full, need_fb);
+    if (m) {
         const int leader = __ffs(m) - 1;
         uint32_t base = 0;
         if (lane == leader) base = atomicAdd(fb_count, (uint32_t)__popc(m));
         base = __shfl_sync(full, base, leader);
-        if (need_fb) fb_list[base + __popc(m & ((1u << lane) - 1u))] = tag;
+        if (need_fb) fb_list[base + __popc(m & lt_mask)] = tag;
+    }
+    __syncthreads();
+    const uint32_t nq = qn;
+    const int part = lane & 3, p8 = lane >> 2;
+    for (uint32_t it = threadIdx.x >> 5; it < nq; it += kQBlock / 32) {
+        const InterpItem e = q[it];
+        const float fl = e.f[4];
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int p = 8 * h + p8;
+            const int b0 = (p >> 3) & 1, b1 = (p >> 2) & 1, b2 = (p >> 1) & 1, b3 = p & 1;
+            const uint32_t nd = e.base + b0 * M.stride[0] + b1 * M.stride[1] + b2 * M.stride[2] +
+                                b3 * M.stride[3];
+            // part 0: (x, y, dx, dy) of node m; 1: (dz, I, 0, 0) of m; 2, 3: the same of m + 1
+            const float4 v = __ldg(reinterpret_cast<const float4*>(M.node + (size_t)nd * kNodeFloats) + part);
+            const float4 u = shfl_xor4(v, 2);
+            const float w = ((b0 ? e.f[0] : 1.0f - e.f[0]) * (b1 ? e.f[1] : 1.0f - e.f[1])) *
+                            ((b2 ? e.f[2] : 1.0f - e.f[2]) * (b3 ? e.f[3] : 1.0f - e.f[3]));
+            // lanes with part 0 / 1 hold node m in v and node m + 1 in u
+            acc.x = fmaf(w, fmaf(fl, u.x - v.x, v.x), acc.x);
+            acc.y = fmaf(w, fmaf(fl, u.y - v.y, v.y), acc.y);
+            acc.z = fmaf(w, fmaf(fl, u.z - v.z, v.z), acc.z);
+            acc.w = fmaf(w, fmaf(fl, u.w - v.w, v.w), acc.w);
+        }
+        // sum the 8 pairs of each round over lanes with the same part
+        float4 t = shfl_xor4(acc, 4);
+        acc.x += t.x; acc.y += t.y; acc.z += t.z; acc.w += t.w;
+        t = shfl_xor4(acc, 8);
+        acc.x += t.x; acc.y += t.y; acc.z += t.z; acc.w += t.w;
+        t = shfl_xor4(acc, 16);
+        acc.x += t.x; acc.y += t.y; acc.z += t.z; acc.w += t.w;
+        const float dz = __shfl_sync(full, acc.x, 1);
+        const float I = __shfl_sync(full, acc.y, 1);
+        if (lane == 0) {
+            const float n2 = fmaf(acc.z, acc.z, fmaf(acc.w, acc.w, dz * dz));
+            float inv = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
+            inv = inv * fmaf(-0.5f * n2, inv * inv, 1.5f);
+            const float o[6] = {acc.x, acc.y, acc.z * inv, acc.w * inv, dz * inv, I};
+            store_out(out, e.r, o, LT_FLAG_VALID);
+        }
     }
 }
 
-// exact tracer over the fallback list (persistent grid-stride loop)
+// exact tracer over the fallback list (one thread per entry, grid-stride)
+template <bool CAUCHY>
 __global__ void __launch_bounds__(kQBlock)
 map_fallback_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out,
                     const uint32_t* __restrict__ fb_list, const uint32_t* __restrict__ fb_count,
@@ -344,8 +435,9 @@ map_fallback_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev o
         const uint32_t r = tag & ~kOutsideBit;
         TraceOut o;
         int nint;
-        uint32_t f = trace_ray(M.L, M.pi, M.pj, __ldg(in.x + r), __ldg(in.y + r), __ldg(in.dx + r),
-                               __ldg(in.dy + r), __ldg(in.dz + r), __ldg(in.lam + r), o, nint);
+        uint32_t f = trace_ray<CAUCHY>(M.L, M.pi, M.pj, __ldg(in.x + r), __ldg(in.y + r),
+                                       __ldg(in.dx + r), __ldg(in.dy + r), __ldg(in.dz + r),
+                                       __ldg(in.lam + r), o, nint);
         f |= LT_FLAG_TRACED | ((tag & kOutsideBit) ? LT_FLAG_OUTSIDE : 0u);
         const float v[6] = {o.x, o.y, o.dx, o.dy, o.dz, o.I};
         store_out(out, r, v, f);
@@ -379,18 +471,6 @@ lt_status scratch_pool(cudaMemPool_t* pool)
     return LT_OK;
 }
 
-int query_fallback_blocks()
-{
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 152;
-    }
-    return sms * 8;
-}
-
 lt_status launch_query(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
                        int mode, uint32_t* fb_list, uint32_t* fb_count, cudaStream_t st)
 {
@@ -404,10 +484,17 @@ lt_status launch_query(const lt_map* map, const RaysInDev& in, const RaysOutDev&
         map_query_kernel<LT_QUERY_NO_MASK><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, fb_list, fb_count);
     }
     LT_CUDA_TRY(cudaGetLastError());
-    const unsigned fbb = (unsigned)std::min<size_t>((size_t)query_fallback_blocks(), blocks);
     {
+        // the list length is only known on the device: a grid of resident
+        // blocks walks it (at most one block per 256 rays of the batch)
         ProfScope prof("map_fallback_kernel", st);
-        map_fallback_kernel<<<fbb, kQBlock, 0, st>>>(map->dev, in, out, fb_list, fb_count, prof.work());
+        if (map->cauchy) {
+            const unsigned g = persistent_blocks((const void*)map_fallback_kernel<true>, kQBlock, n, 8);
+            map_fallback_kernel<true><<<g, kQBlock, 0, st>>>(map->dev, in, out, fb_list, fb_count, prof.work());
+        } else {
+            const unsigned g = persistent_blocks((const void*)map_fallback_kernel<false>, kQBlock, n, 8);
+            map_fallback_kernel<false><<<g, kQBlock, 0, st>>>(map->dev, in, out, fb_list, fb_count, prof.work());
+        }
     }
     LT_CUDA_TRY(cudaGetLastError());
     return LT_OK;
@@ -457,7 +544,7 @@ lt_status lt_build_map(const lt_lens* lens, const lt_map_opts* o, lt_map** out, 
         N *= (uint64_t)o->res[d];
         NC *= (uint64_t)(o->res[d] - 1);
     }
-    if (N * 6 >= (1ull << 32)) return fail(LT_EINVAL, "lt_build_map: %llu nodes is too many", (unsigned long long)N);
+    if (N * kNodeFloats >= (1ull << 32)) return fail(LT_EINVAL, "lt_build_map: %llu nodes is too many", (unsigned long long)N);
     if (o->n_fit > 0) {
         const void* ps[] = {o->fit_x, o->fit_y, o->fit_dx, o->fit_dy, o->fit_dz, o->fit_lambda};
         for (const void* p : ps)
@@ -478,6 +565,7 @@ lt_status lt_build_map(const lt_lens* lens, const lt_map_opts* o, lt_map** out, 
     MapDev& D = m->dev;
     std::memset(&D, 0, sizeof D);
     D.L = lens->dev;
+    m->cauchy = lens_all_cauchy(lens->dev);
     D.pi = pi;
     D.pj = pj;
     uint32_t stride = 1, cstride = 1;
@@ -497,7 +585,7 @@ lt_status lt_build_map(const lt_lens* lens, const lt_map_opts* o, lt_map** out, 
     }
     const uint32_t NW = (uint32_t)((NC + 15) / 16);
     auto bail = [&](lt_status s) { delete m; return s; };
-    if (cudaMalloc(&m->node, N * 6 * sizeof(float)) != cudaSuccess ||
+    if (cudaMalloc(&m->node, N * kNodeFloats * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&m->node_valid, N) != cudaSuccess ||
         cudaMalloc(&m->cls, (size_t)NW * sizeof(uint32_t)) != cudaSuccess)
         return bail(fail(LT_ENOMEM, "lt_build_map: device allocation of the tables failed"));
@@ -528,12 +616,20 @@ lt_status lt_build_map(const lt_lens* lens, const lt_map_opts* o, lt_map** out, 
             s = fail(LT_ECUDA, "lt_build_map: memset failed");
             break;
         }
-        map_node_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(D, m->node, m->node_valid, (uint32_t)N);
+        if (m->cauchy)
+            map_node_kernel<true><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(D, m->node, m->node_valid, (uint32_t)N);
+        else
+            map_node_kernel<false><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(D, m->node, m->node_valid, (uint32_t)N);
         map_corner_kernel<<<(unsigned)((NC + 255) / 256), 256, 0, st>>>(D, m->node_valid, corner_bits, (uint32_t)NC);
         if (o->n_fit > 0) {
             RaysInDev fit{o->fit_x, o->fit_y, o->fit_dx, o->fit_dy, o->fit_dz, o->fit_lambda};
-            map_fit_kernel<<<(unsigned)((o->n_fit + 255) / 256), 256, 0, st>>>(
-                D, fit, (uint32_t)o->n_fit, m->node, corner_bits, seen, resmax, acc);
+            const unsigned fb = (unsigned)((o->n_fit + 255) / 256);
+            if (m->cauchy)
+                map_fit_kernel<true><<<fb, 256, 0, st>>>(D, fit, (uint32_t)o->n_fit, m->node, corner_bits,
+                                                          seen, resmax, acc);
+            else
+                map_fit_kernel<false><<<fb, 256, 0, st>>>(D, fit, (uint32_t)o->n_fit, m->node, corner_bits,
+                                                           seen, resmax, acc);
         }
         float tol_f = use_tol ? (float)o->max_residual_mm : 0.0f;
         uint32_t tol_bits;
@@ -562,7 +658,7 @@ lt_status lt_build_map(const lt_lens* lens, const lt_map_opts* o, lt_map** out, 
         float mx;
         std::memcpy(&mx, &ha.max_res_bits, 4);
         m->stats.fit_residual_max_mm = mx;
-        m->stats.table_bytes = N * 6 * 4 + N + (uint64_t)NW * 4;
+        m->stats.table_bytes = N * kNodeFloats * 4 + N + (uint64_t)NW * 4;
     } while (0);
     if (corner_bits) cudaFree(corner_bits);
     if (seen) cudaFree(seen);
@@ -620,7 +716,9 @@ lt_status lt_map_export(const lt_map* m, float* node6, uint8_t* node_valid, uint
 {
     clear_error();
     if (!m) return fail(LT_EINVAL, "lt_map_export: NULL map");
-    if (node6) LT_CUDA_TRY(cudaMemcpy(node6, m->node, m->n_nodes * 6 * sizeof(float), cudaMemcpyDeviceToHost));
+    if (node6)
+        LT_CUDA_TRY(cudaMemcpy2D(node6, 6 * sizeof(float), m->node, kNodeFloats * sizeof(float),
+                                 6 * sizeof(float), m->n_nodes, cudaMemcpyDeviceToHost));
     if (node_valid) LT_CUDA_TRY(cudaMemcpy(node_valid, m->node_valid, m->n_nodes, cudaMemcpyDeviceToHost));
     if (cell_class) {
         const size_t NW = (m->n_cells + 15) / 16;
@@ -652,7 +750,8 @@ lt_status lt_map_save(const lt_map* m, const char* path)
     std::vector<uint8_t> nv(m->n_nodes);
     const size_t NW = (m->n_cells + 15) / 16;
     std::vector<uint32_t> cls(NW);
-    LT_CUDA_TRY(cudaMemcpy(node.data(), m->node, node.size() * 4, cudaMemcpyDeviceToHost));
+    LT_CUDA_TRY(cudaMemcpy2D(node.data(), 6 * sizeof(float), m->node, kNodeFloats * sizeof(float),
+                             6 * sizeof(float), m->n_nodes, cudaMemcpyDeviceToHost));
     LT_CUDA_TRY(cudaMemcpy(nv.data(), m->node_valid, nv.size(), cudaMemcpyDeviceToHost));
     LT_CUDA_TRY(cudaMemcpy(cls.data(), m->cls, NW * 4, cudaMemcpyDeviceToHost));
     FILE* f = std::fopen(path, "wb");
@@ -708,7 +807,7 @@ lt_status lt_map_load(const char* path, lt_map** out)
         N *= (uint64_t)h.res[d];
         NC *= (uint64_t)(h.res[d] - 1);
     }
-    ok = ok && N == h.n_nodes && NC == h.n_cells && N * 6 < (1ull << 32);
+    ok = ok && N == h.n_nodes && NC == h.n_cells && N * kNodeFloats < (1ull << 32);
     if (!ok) { std::fclose(f); return fail(LT_EIO, "lt_map_load: %s is not a map file", path); }
     std::vector<float> node(N * 6);
     std::vector<uint8_t> nv(N);
@@ -740,6 +839,7 @@ lt_status lt_map_load(const char* path, lt_map** out)
     MapDev& D = m->dev;
     std::memset(&D, 0, sizeof D);
     D.L = m->lens.dev;
+    m->cauchy = lens_all_cauchy(m->lens.dev);
     D.pi = pi;
     D.pj = pj;
     uint32_t stride = 1, cstride = 1;
@@ -757,14 +857,16 @@ lt_status lt_map_load(const char* path, lt_map** out)
         stride *= (uint32_t)h.res[d];
         cstride *= (uint32_t)(h.res[d] - 1);
     }
-    if (cudaMalloc(&m->node, N * 6 * 4) != cudaSuccess || cudaMalloc(&m->node_valid, N) != cudaSuccess ||
+    if (cudaMalloc(&m->node, N * kNodeFloats * 4) != cudaSuccess || cudaMalloc(&m->node_valid, N) != cudaSuccess ||
         cudaMalloc(&m->cls, NW * 4) != cudaSuccess) {
         delete m;
         return fail(LT_ENOMEM, "lt_map_load: device allocation failed");
     }
     D.node = m->node;
     D.cls = m->cls;
-    if (cudaMemcpy(m->node, node.data(), N * 24, cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (cudaMemset(m->node, 0, N * kNodeFloats * 4) != cudaSuccess ||
+        cudaMemcpy2D(m->node, kNodeFloats * sizeof(float), node.data(), 6 * sizeof(float),
+                     6 * sizeof(float), N, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(m->node_valid, nv.data(), N, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(m->cls, cls.data(), NW * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
         delete m;

@@ -40,6 +40,7 @@ struct lt_map {
     uint8_t* node_valid = nullptr;
     uint32_t* cls = nullptr;
     int device = 0;
+    bool cauchy = true;       // every glass of the lens is Cauchy (single-FMA dispersion)
     lt_map_stats stats = {};
     lt::MapDev dev;
     ~lt_map();

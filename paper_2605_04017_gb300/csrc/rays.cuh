@@ -26,6 +26,8 @@ lt_status check_io(const lt_rays_in* in, const float* lam, const lt_rays_out* ou
                    const char* who);
 lt_status launch_trace(const lt_lens* L, int pi, int pj, const RaysInDev& in,
                        const RaysOutDev& out, size_t n, cudaStream_t st);
+// blocks for a persistent kernel: resident blocks per SM x SMs, capped by the work
+unsigned persistent_blocks(const void* kernel, int block, size_t items, size_t per_warp);
 
 // ---------------------------------------------------------------- host staging
 

@@ -11,18 +11,19 @@ namespace lt {
 constexpr int kTraceBlock = 256;
 
 // One thread per ray.  Inputs are read once through the non-coherent path,
-// outputs are written with an evict-first hint (nothing re-reads them here).
+// outputs written with an evict-first hint (nothing here re-reads them).
+template <bool CAUCHY>
 __global__ void __launch_bounds__(kTraceBlock)
 trace_kernel(const __grid_constant__ LensDev L, int pi, int pj, RaysInDev in, RaysOutDev out,
-             size_t n, unsigned long long* work)
+             uint32_t n, unsigned long long* work)
 {
-    const size_t r = (size_t)blockIdx.x * kTraceBlock + threadIdx.x;
+    const uint32_t r = blockIdx.x * kTraceBlock + threadIdx.x;
     int nint = 0;
     if (r < n) {
         TraceOut o;
-        const uint32_t f = trace_ray(L, pi, pj, __ldg(in.x + r), __ldg(in.y + r),
-                                     __ldg(in.dx + r), __ldg(in.dy + r), __ldg(in.dz + r),
-                                     __ldg(in.lam + r), o, nint);
+        const uint32_t f = trace_ray<CAUCHY>(L, pi, pj, __ldg(in.x + r), __ldg(in.y + r),
+                                             __ldg(in.dx + r), __ldg(in.dy + r), __ldg(in.dz + r),
+                                             __ldg(in.lam + r), o, nint);
         __stcs(out.x + r, o.x);
         __stcs(out.y + r, o.y);
         __stcs(out.dx + r, o.dx);
@@ -34,14 +35,39 @@ trace_kernel(const __grid_constant__ LensDev L, int pi, int pj, RaysInDev in, Ra
     warp_add(work, (unsigned)nint);
 }
 
+// Grid of a persistent kernel: resident blocks per SM x SMs, but no more warps
+// than there are chunks of work.
+unsigned persistent_blocks(const void* kernel, int block, size_t items, size_t per_warp)
+{
+    int dev = 0, sms = 152, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0);
+    if (per_sm < 1) per_sm = 1;
+    const size_t warps_needed = (items + per_warp - 1) / per_warp;
+    const size_t blocks_needed = (warps_needed * 32 + block - 1) / block;
+    size_t g = (size_t)sms * per_sm;
+    if (blocks_needed < g) g = blocks_needed;
+    return (unsigned)(g ? g : 1);
+}
+
 lt_status launch_trace(const lt_lens* L, int pi, int pj, const RaysInDev& in,
                        const RaysOutDev& out, size_t n, cudaStream_t st)
 {
-    if (n == 0) return LT_OK;
-    const size_t blocks = (n + kTraceBlock - 1) / kTraceBlock;
-    ProfScope prof("trace_kernel", st);
-    trace_kernel<<<(unsigned)blocks, kTraceBlock, 0, st>>>(L->dev, pi, pj, in, out, n, prof.work());
-    LT_CUDA_TRY(cudaGetLastError());
+    const bool cauchy = lens_all_cauchy(L->dev);
+    for (size_t off = 0; off < n; off += ((size_t)1 << 30)) {
+        const uint32_t m = (uint32_t)std::min<size_t>(n - off, (size_t)1 << 30);
+        RaysInDev a{in.x + off, in.y + off, in.dx + off, in.dy + off, in.dz + off, in.lam + off};
+        RaysOutDev b{out.x + off, out.y + off, out.dx + off, out.dy + off, out.dz + off,
+                     out.I + off, out.flags + off};
+        ProfScope prof("trace_kernel", st);
+        const unsigned g = (m + kTraceBlock - 1) / kTraceBlock;
+        if (cauchy)
+            trace_kernel<true><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, prof.work());
+        else
+            trace_kernel<false><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, prof.work());
+        LT_CUDA_TRY(cudaGetLastError());
+    }
     return LT_OK;
 }
 
