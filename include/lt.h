@@ -271,6 +271,95 @@ lt_status lt_map_export(const lt_map* map, float* node6, uint8_t* node_valid,
 lt_status lt_map_save(const lt_map* map, const char* path);
 lt_status lt_map_load(const char* path, lt_map** out);
 
+/* ------------------------------------------------------------------ learned maps */
+
+/*
+ * The paper's learned form of a path's map (Sec. 4.2, Sec. 5.1): a binary
+ * classifier g (4 -> 32 -> 32 -> 1, tanh hidden, logit out) and a regressor f
+ * (4 -> 32 x 5 -> 6, tanh hidden, linear out); a ray gets f(x) iff g(x) > 0
+ * (Eq. 11).  Inputs are the symmetry-reduced entrance ray of Sec. 4.1 (Eq. 10):
+ * rotate about the axis so the point is (r, 0), mirror y if the rotated d_y < 0;
+ * x = (2 r / rho - 1, d_x' / wmax, 2 d_y' / wmax - 1, 2 (lam - lam_lo) /
+ * (lam_hi - lam_lo) - 1).  Regressor outputs are the exit (x', y'), direction
+ * and throughput in the same reduced frame, standardised by the training set's
+ * mean and standard deviation; a query mirrors and rotates them back.
+ *
+ * Parameter layout (FP32, flat, per network): for each layer in order the
+ * weight matrix W (out x in, row-major) then the bias (out).
+ * LT_MLP_REG_PARAMS = 4582, LT_MLP_CLS_PARAMS = 1249.
+ */
+#define LT_MLP_REG_PARAMS 4582
+#define LT_MLP_CLS_PARAMS 1249
+
+typedef struct lt_mlp lt_mlp;
+
+typedef struct {
+    int32_t path_id;
+    double rho, wmax;               /* input box: r in [0, rho], |d_xy| <= wmax */
+    double lam_lo, lam_hi;          /* wavelength range (nm) */
+} lt_mlp_frame;
+
+typedef struct {
+    lt_mlp_frame frame;
+    const float *fit_x, *fit_y, *fit_dx, *fit_dy, *fit_dz, *fit_lambda;  /* device training rays */
+    size_t n_fit;
+    const float* init_reg;          /* host: initial regressor parameters (the random draw is an input) */
+    const float* init_cls;          /* host: initial classifier parameters */
+    int32_t reg_steps, reg_batch;   /* regressor: Adam steps and rays per batch (valid rays only) */
+    int32_t cls_steps, cls_batch;   /* classifier: steps and batch (all rays) */
+    double lr, lr_decay;            /* schedule lr * lr_decay^(step / decay_every) (Sec. 5.1) */
+    int32_t decay_every;
+    int32_t ft_steps, ft_batch;     /* optional regressor fine-tune phase (0 steps: none) */
+    double ft_lr;
+    uint64_t seed;                  /* batch draws: SplitMix64(seed + step * batch + i) mod n */
+} lt_mlp_opts;
+
+typedef struct {
+    uint64_t n_train, n_valid;      /* training rays traced, of which valid */
+    double reg_loss, cls_loss;      /* mean training loss of the last 100 steps */
+    double t_mean[6], t_std[6];     /* target standardisation */
+    double train_ms;
+} lt_mlp_stats;
+
+enum {
+    LT_MLP_F32 = 0,      /* FP32 SIMT, rational tanh (Lambert continued fraction, 9/10) */
+    LT_MLP_BF16 = 1,     /* BF16 tensor-core MMA, FP32 accumulation, tanh.approx.bf16x2 */
+    LT_MLP_F16 = 2,      /* FP16 tensor-core MMA, FP32 accumulation, tanh.approx.f16x2 */
+    LT_MLP_F32_NOCLS = 3 /* ablation of Fig. 6: FP32 regressor for every ray, classifier off */
+};
+
+/* Trace the training rays (path frame.path_id), standardise the targets and
+ * train both networks with Adam on the GPU (forward, backward and update are
+ * this library's kernels; gradients are summed per block in FP32 and across
+ * blocks in FP64).  Returns when training is done. */
+lt_status lt_mlp_train(const lt_lens* lens, const lt_mlp_opts* opts, lt_mlp** out, lt_stream stream);
+
+/* A learned map from given parameters (host FP32 arrays) and target
+ * standardisation (6 means, 6 standard deviations). */
+lt_status lt_mlp_create(const lt_lens* lens, const lt_mlp_frame* frame, const float* reg,
+                        const float* cls, const double* t_mean, const double* t_std, lt_mlp** out);
+void lt_destroy_mlp(lt_mlp* mlp);
+lt_status lt_mlp_stats_get(const lt_mlp* mlp, lt_mlp_stats* out);
+/* Copy the current parameters to host arrays (either may be NULL). */
+lt_status lt_mlp_get_params(const lt_mlp* mlp, float* reg, float* cls);
+
+/* Query n rays (device arrays as lt_trace) with LT_MLP_* arithmetic. */
+lt_status lt_mlp_query(const lt_mlp* mlp, const lt_rays_in* in, const float* lambda_nm,
+                       const lt_rays_out* out, size_t n, int32_t precision, lt_stream stream);
+
+/* One forward and backward pass on an explicit batch with the current
+ * parameters: net 0 = regressor (targets: B x 6 standardised, device), 1 =
+ * classifier (targets: B labels 0/1 as floats, device); X: B x 4 network
+ * inputs (device).  grad (host, FP64, the net's parameter count) receives the
+ * gradient of the batch-mean loss, *loss the loss.  Synchronous. */
+lt_status lt_mlp_grad(const lt_mlp* mlp, int32_t net, const float* X, const float* targets,
+                      int32_t B, double* grad, double* loss);
+
+/* Network inputs of n entrance rays (n x 4 device array out), as the query
+ * and training kernels compute them (FP32). */
+lt_status lt_mlp_features(const lt_mlp* mlp, const lt_rays_in* in, const float* lambda_nm,
+                          float* X, size_t n, lt_stream stream);
+
 /* ------------------------------------------------------------------ profiling */
 
 /* Per-kernel device time.  When enabled, each kernel launch of the library

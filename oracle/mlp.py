@@ -223,3 +223,52 @@ def query(cls_params, reg_params, rays, rho, wmax, t_mean, t_std, lam_lo=380.0, 
     out = unreduce_outputs(red, phi, mirror)
     out[~valid] = 0.0
     return out, valid, logit
+
+
+# ----------------------------------------------------------------------------- inference tanh
+
+# Sec. 5.1: inference replaces tanh by a rational function.  Reading: the
+# truncation of Lambert's continued fraction
+#   tanh x = x / (1 + x^2 / (3 + x^2 / (5 + x^2 / (7 + ...))))
+# after the 19 term, i.e. the 9/10 Pade approximant, clamped to +-1 for
+# |x| >= 6.95 (where the truncation error and 1 - tanh cross).
+_LAMBERT_NUM = [654729075.0, 91891800.0, 2837835.0, 25740.0, 55.0]
+_LAMBERT_DEN = [654729075.0, 310134825.0, 18918900.0, 315315.0, 1485.0, 1.0]
+
+
+def tanh_lambert(x):
+    x = np.asarray(x, np.float64)
+    x2 = x * x
+    num = np.zeros_like(x)
+    for c in reversed(_LAMBERT_NUM):
+        num = num * x2 + c
+    den = np.zeros_like(x)
+    for c in reversed(_LAMBERT_DEN):
+        den = den * x2 + c
+    y = x * num / den
+    return np.where(np.abs(x) >= 6.95, np.sign(x), y)
+
+
+def forward_with(params, X, act):
+    """forward() with a given hidden activation."""
+    acts = [np.asarray(X, np.float64)]
+    for li, (W, b) in enumerate(params):
+        z = acts[-1] @ W.T + b
+        acts.append(z if li == len(params) - 1 else act(z))
+    return acts
+
+
+def query_with(cls_params, reg_params, rays, rho, wmax, t_mean, t_std, act, lam_lo=380.0,
+               lam_hi=780.0, use_classifier=True):
+    """query() with a given activation (the inference-time rational tanh)."""
+    X, phi, mirror = features(rays.arrays() if hasattr(rays, "arrays") else rays, rho, wmax,
+                              lam_lo, lam_hi)
+    logit = forward_with(cls_params, X, act)[-1][:, 0]
+    valid = (logit > 0.0) if use_classifier else np.ones(len(logit), bool)
+    z = forward_with(reg_params, X, act)[-1]
+    red = t_mean + t_std * z
+    d = red[:, 2:5]
+    red[:, 2:5] = d / np.linalg.norm(d, axis=1, keepdims=True)
+    out = unreduce_outputs(red, phi, mirror)
+    out[~valid] = 0.0
+    return out, valid, logit

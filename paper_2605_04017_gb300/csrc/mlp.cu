@@ -1,0 +1,1187 @@
+// Learned lens transport map: the paper's classifier / regressor MLPs
+// (Sec. 4.2 "Neural Ray Masking", "C^1 Continuous Network"; Sec. 5.1 "MLP
+// Training", "Inference") trained and queried by this library's kernels.
+//
+//   g: 4 -> 32 -> 32 -> 1 (tanh hidden, logit out), BCE loss
+//   f: 4 -> 32 x 5 -> 6 (tanh hidden, linear out), MSE on position and
+//      throughput + (1 - cosine) on direction
+// Inputs: the symmetry-reduced entrance ray (Sec. 4.1, Eq. 10).  Training:
+// Adam with lr * decay^(step / every) (Sec. 5.1); per-block gradient sums in
+// FP32, the sum over blocks in FP64.  Queries: FP32 SIMT with a rational tanh
+// (the paper approximates tanh by a rational function, Sec. 5.1; here the
+// 9/10 truncation of Lambert's continued fraction), or BF16 / FP16 tensor-core
+// MMA (mma.sync m16n8k16, FP32 accumulation) with activations kept in
+// registers between layers and tanh.approx on packed pairs.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "profile.h"
+#include "rays.cuh"
+#include "tracer.cuh"
+
+namespace lt {
+
+// ------------------------------------------------------------------ network shapes
+
+template <bool REG>
+struct Net {
+    static constexpr int L = REG ? 6 : 3;
+    static constexpr int NOUT = REG ? 6 : 1;
+    __host__ __device__ static constexpr int in(int l) { return l == 0 ? 4 : 32; }
+    __host__ __device__ static constexpr int out(int l) { return l == L - 1 ? NOUT : 32; }
+    __host__ __device__ static constexpr int woff(int l)
+    {
+        int o = 0;
+        for (int k = 0; k < l; ++k) o += out(k) * in(k) + out(k);
+        return o;
+    }
+    __host__ __device__ static constexpr int boff(int l) { return woff(l) + out(l) * in(l); }
+    static constexpr int NP = woff(L);
+};
+static_assert(Net<true>::NP == LT_MLP_REG_PARAMS, "regressor size");
+static_assert(Net<false>::NP == LT_MLP_CLS_PARAMS, "classifier size");
+
+// input normalisation and output de-standardisation, FP32
+struct MlpFrame {
+    float rho2_inv, winv, winv2, lam_lo, lam_scale;
+    float t_mean[6], t_std[6];
+};
+
+struct RedFrame {
+    float c, s, m;   // rotation cos/sin and mirror sign of the reduced frame
+};
+
+// Symmetry-reduced network input (Sec. 4.1): rotate the entrance point onto
+// +x, mirror y when the rotated d_y < 0, normalise to [-1, 1].
+__device__ __forceinline__ void mlp_features(const MlpFrame& F, float x, float y, float dx,
+                                             float dy, float dz, float lam, float X[4],
+                                             RedFrame& rf)
+{
+    const float r = sqrtf(fmaf(x, x, y * y));
+    float c = 1.0f, s = 0.0f;
+    if (r > 0.0f) {
+        const float ir = 1.0f / r;
+        c = x * ir;
+        s = y * ir;
+    }
+    const float n2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float inv = rsqrtf(n2);
+    inv = inv * fmaf(-0.5f * n2, inv * inv, 1.5f);
+    dx *= inv;
+    dy *= inv;
+    const float dxr = fmaf(c, dx, s * dy);
+    float dyr = fmaf(-s, dx, c * dy);
+    const float m = dyr < 0.0f ? -1.0f : 1.0f;
+    dyr *= m;
+    X[0] = fmaf(r, F.rho2_inv, -1.0f);
+    X[1] = dxr * F.winv;
+    X[2] = fmaf(dyr, F.winv2, -1.0f);
+    X[3] = fmaf(lam - F.lam_lo, F.lam_scale, -1.0f);
+    rf = {c, s, m};
+}
+
+__device__ __forceinline__ void mlp_unreduce(const RedFrame& rf, const float red[6], float o[6])
+{
+    const float yr = red[1] * rf.m, dyr = red[3] * rf.m;
+    o[0] = fmaf(rf.c, red[0], -rf.s * yr);
+    o[1] = fmaf(rf.s, red[0], rf.c * yr);
+    o[2] = fmaf(rf.c, red[2], -rf.s * dyr);
+    o[3] = fmaf(rf.s, red[2], rf.c * dyr);
+    o[4] = red[4];
+    o[5] = red[5];
+}
+
+// Lambert's continued fraction tanh x = x / (1 + x^2 / (3 + x^2 / (5 + ...)))
+// truncated at the 19 term: a 9/10 rational, clamped to +-1 for |x| >= 6.95
+// (max |error| 1.8e-6 on the real line in FP64, 2.0e-6 evaluated in FP32).
+// Coefficients normalised by the constant term.
+__device__ __forceinline__ float tanh_rational(float x)
+{
+    const float ax = fabsf(x);
+    if (ax >= 6.95f) return copysignf(1.0f, x);
+    const float x2 = x * x;
+    const float num = fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 8.400421197e-08f, 3.931397120e-05f),
+                                             4.334365325e-03f), 1.403508772e-01f), 1.0f);
+    const float den = fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.527349309e-09f, 2.268113723e-06f),
+                                                       4.815961472e-04f), 2.889576883e-02f),
+                                    4.736842105e-01f), 1.0f);
+    return x * num * __frcp_rn(den);
+}
+
+// ------------------------------------------------------------------ training data
+
+// Trace each fit ray along the path; write network inputs X (n x 4), the
+// reduced-frame targets T (n x 6, valid rays only) and labels; append valid
+// rays to a list.
+template <bool CAUCHY>
+__global__ void __launch_bounds__(256)
+mlp_prep_kernel(const __grid_constant__ LensDev L, int pi, int pj, RaysInDev fit, uint32_t n,
+                MlpFrame F, float* __restrict__ X, float* __restrict__ T,
+                float* __restrict__ label, uint32_t* __restrict__ vlist, uint32_t* vcount)
+{
+    const uint32_t r = blockIdx.x * 256u + threadIdx.x;
+    bool valid = false;
+    if (r < n) {
+        const float x = __ldg(fit.x + r), y = __ldg(fit.y + r), dx = __ldg(fit.dx + r),
+                    dy = __ldg(fit.dy + r), dz = __ldg(fit.dz + r), lam = __ldg(fit.lam + r);
+        float xin[4];
+        RedFrame rf;
+        mlp_features(F, x, y, dx, dy, dz, lam, xin, rf);
+        TraceOut o;
+        int nint;
+        const uint32_t f = trace_ray<CAUCHY>(L, pi, pj, x, y, dx, dy, dz, lam, o, nint);
+        valid = (f & LT_FLAG_VALID) != 0 && (f & LT_FLAG_BAD_INPUT) == 0;
+        const bool bad = (f & LT_FLAG_BAD_INPUT) != 0;
+        reinterpret_cast<float4*>(X)[r] = bad ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                              : make_float4(xin[0], xin[1], xin[2], xin[3]);
+        label[r] = valid ? 1.0f : 0.0f;
+        float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (valid) {
+            t[0] = fmaf(rf.c, o.x, rf.s * o.y);
+            t[1] = rf.m * fmaf(-rf.s, o.x, rf.c * o.y);
+            t[2] = fmaf(rf.c, o.dx, rf.s * o.dy);
+            t[3] = rf.m * fmaf(-rf.s, o.dx, rf.c * o.dy);
+            t[4] = o.dz;
+            t[5] = o.I;
+        }
+        float2* tp = reinterpret_cast<float2*>(T + (size_t)r * 6);
+        tp[0] = make_float2(t[0], t[1]);
+        tp[1] = make_float2(t[2], t[3]);
+        tp[2] = make_float2(t[4], t[5]);
+    }
+    const unsigned full = 0xffffffffu;
+    const unsigned m = __ballot_sync(full, valid);
+    if (m) {
+        const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(vcount, (uint32_t)__popc(m));
+        base = __shfl_sync(full, base, leader);
+        if (valid) vlist[base + __popc(m & ((1u << lane) - 1u))] = r;
+    }
+}
+
+// FP64 sums of the targets and their squares over the valid list
+__global__ void __launch_bounds__(256)
+mlp_stats_kernel(const float* __restrict__ T, const uint32_t* __restrict__ vlist,
+                 const uint32_t* __restrict__ vcount, double* sums /* 12 */)
+{
+    const uint32_t cnt = *vcount;
+    double s[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) s[q] = 0.0;
+    for (uint32_t i = blockIdx.x * 256u + threadIdx.x; i < cnt; i += gridDim.x * 256u) {
+        const float* t = T + (size_t)vlist[i] * 6;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const double v = t[q];
+            s[q] += v;
+            s[6 + q] += v * v;
+        }
+    }
+    const unsigned full = 0xffffffffu;
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(full, s[q], o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int q = 0; q < 12; ++q) atomicAdd(sums + q, s[q]);
+    }
+}
+
+// ------------------------------------------------------------------ training step
+
+// SplitMix64 (Steele, Lea and Flood, 2014): a counter-based 64-bit mixer.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+constexpr int kTB = 128;   // rays per training block
+
+struct TrainBatch {
+    const float* X;          // inputs (n x 4)
+    const float* T;          // REG: raw reduced-frame targets (n x 6) or standardised batch targets
+    const float* label;      // CLS: labels
+    const uint32_t* list;    // indices to draw from; NULL with n_list > 0: draw rows of [0, n_list);
+    uint32_t n_list;         // NULL with n_list == 0: explicit batch, item b is row b
+    uint64_t seed, step;
+    int B;
+    int standardised;        // targets already standardised (explicit batch)
+};
+
+// One forward + backward pass over rays [blockIdx.x * 128, +128) of the batch.
+// Per-block gradient sums (FP32, over the block's rays) go to G[block][param],
+// the block's loss sum (FP64) to loss[block].  Activations and deltas of the
+// block live in shared memory for the weight-gradient products.
+template <bool REG>
+__global__ void __launch_bounds__(kTB)
+mlp_train_kernel(const float* __restrict__ P, TrainBatch tb, MlpFrame F, float* __restrict__ G,
+                 double* __restrict__ loss)
+{
+    using N = Net<REG>;
+    extern __shared__ float sh[];
+    float* W = sh;                                    // N::NP
+    float* act = W + ((N::NP + 3) & ~3);              // L layers x 32 x kTB (layer 0 = inputs)
+    float* dl = act + N::L * 32 * kTB;                // 32 x kTB deltas
+    __shared__ double lsum[kTB / 32];
+    for (int i = threadIdx.x; i < N::NP; i += kTB) W[i] = P[i];
+    const int j = threadIdx.x;
+    const int b = blockIdx.x * kTB + j;
+    const bool live = b < tb.B;
+    uint32_t row = 0;
+    if (live) {
+        if (tb.n_list) {
+            const uint64_t h = splitmix64(tb.seed + tb.step * (uint64_t)tb.B + (uint64_t)b);
+            row = tb.list ? tb.list[h % tb.n_list] : (uint32_t)(h % tb.n_list);
+        } else {
+            row = (uint32_t)b;
+        }
+    }
+    float a[32];
+    {
+        const float4 x = live ? reinterpret_cast<const float4*>(tb.X)[row] : make_float4(0.f, 0.f, 0.f, 0.f);
+        a[0] = x.x; a[1] = x.y; a[2] = x.z; a[3] = x.w;
+        act[0 * kTB + j] = a[0];
+        act[1 * kTB + j] = a[1];
+        act[2 * kTB + j] = a[2];
+        act[3 * kTB + j] = a[3];
+    }
+    __syncthreads();
+    float z[N::NOUT];
+    // forward
+#pragma unroll
+    for (int l = 0; l < N::L; ++l) {
+        const int ni = N::in(l), no = N::out(l);
+        const float* Wl = W + N::woff(l);
+        const float* bl = W + N::boff(l);
+        float t[32];
+#pragma unroll
+        for (int o = 0; o < 32; ++o) {
+            if (o < no) {
+                float s = bl[o];
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                    if (k < ni) s = fmaf(Wl[o * ni + k], a[k], s);
+                t[o] = s;
+            }
+        }
+        if (l < N::L - 1) {
+#pragma unroll
+            for (int o = 0; o < 32; ++o) {
+                a[o] = tanhf(t[o]);
+                act[((l + 1) * 32 + o) * kTB + j] = a[o];
+            }
+        } else {
+#pragma unroll
+            for (int o = 0; o < N::NOUT; ++o) z[o] = t[o];
+        }
+    }
+    // loss and its gradient w.r.t. the outputs (batch mean)
+    float d[32];
+    double lval = 0.0;
+    const float invB = 1.0f / (float)tb.B;
+    if (REG) {
+        float t[6];
+        if (live) {
+            const float* tp = tb.T + (size_t)row * 6;
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+                t[q] = tb.standardised ? tp[q] : (tp[q] - F.t_mean[q]) / F.t_std[q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) t[q] = 0.0f;
+        }
+        const float e0 = z[0] - t[0], e1 = z[1] - t[1], e5 = z[5 % N::NOUT] - t[5];
+        float dp[3], dt[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            dp[q] = fmaf(F.t_std[2 + q], z[(2 + q) % N::NOUT], F.t_mean[2 + q]);
+            dt[q] = fmaf(F.t_std[2 + q], t[2 + q], F.t_mean[2 + q]);
+        }
+        const float npd = sqrtf(dp[0] * dp[0] + dp[1] * dp[1] + dp[2] * dp[2]);
+        const float ntd = sqrtf(dt[0] * dt[0] + dt[1] * dt[1] + dt[2] * dt[2]);
+        const float cs = (dp[0] * dt[0] + dp[1] * dt[1] + dp[2] * dt[2]) / (npd * ntd);
+        if (live) {
+            lval = 0.5 * ((double)e0 * e0 + (double)e1 * e1) + (double)e5 * e5 + (1.0 - (double)cs);
+            d[0] = e0 * invB;
+            d[1] = e1 * invB;
+            d[5 % N::NOUT] = 2.0f * e5 * invB;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float dc = dt[q] / (npd * ntd) - cs * dp[q] / (npd * npd);
+                d[(2 + q) % N::NOUT] = -dc * F.t_std[2 + q] * invB;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < N::NOUT; ++q) d[q] = 0.0f;
+        }
+    } else {
+        const float y = live ? tb.label[row] : 0.0f;
+        const float zz = z[0];
+        if (live) {
+            lval = (double)fmaxf(zz, 0.0f) - (double)y * zz + log1p(exp(-(double)fabsf(zz)));
+            const float sg = 1.0f / (1.0f + __expf(-zz));
+            d[0] = (sg - y) * invB;
+        } else {
+            d[0] = 0.0f;
+        }
+    }
+    {
+        const unsigned full = 0xffffffffu;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lval += __shfl_xor_sync(full, lval, o);
+        if ((j & 31) == 0) lsum[j >> 5] = lval;
+    }
+    // backward
+    float* Gb = G + (size_t)blockIdx.x * N::NP;
+#pragma unroll
+    for (int l = N::L - 1; l >= 0; --l) {
+        const int ni = N::in(l), no = N::out(l);
+        const float* Wl = W + N::woff(l);
+#pragma unroll
+        for (int o = 0; o < 32; ++o)
+            if (o < no) dl[o * kTB + j] = d[o];
+        __syncthreads();
+        // dW[o][k] = sum_j d[o][j] a_l[k][j], db[o] = sum_j d[o][j]
+        const float* al = act + l * 32 * kTB;
+        for (int e = j; e < no * (ni + 1); e += kTB) {
+            const int o = e / (ni + 1), k = e % (ni + 1);
+            const float* dr = dl + o * kTB;
+            float s = 0.0f;
+            if (k < ni) {
+                const float* ar = al + k * kTB;
+#pragma unroll 8
+                for (int q = 0; q < kTB; ++q) s = fmaf(dr[q], ar[q], s);
+                Gb[N::woff(l) + o * ni + k] = s;
+            } else {
+#pragma unroll 8
+                for (int q = 0; q < kTB; ++q) s += dr[q];
+                Gb[N::boff(l) + o] = s;
+            }
+        }
+        if (l > 0) {
+            float nd[32];
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                float s = 0.0f;
+#pragma unroll
+                for (int o = 0; o < 32; ++o)
+                    if (o < no) s = fmaf(Wl[o * ni + k], d[o], s);
+                const float ak = act[(l * 32 + k) * kTB + j];
+                nd[k] = s * (1.0f - ak * ak);
+            }
+#pragma unroll
+            for (int k = 0; k < 32; ++k) d[k] = nd[k];
+        }
+        __syncthreads();
+    }
+    if (j == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kTB / 32; ++w) s += lsum[w];
+        loss[blockIdx.x] = s;
+    }
+}
+
+// Adam update (beta1 0.9, beta2 0.999, eps 1e-8): the batch gradient is the
+// FP64 sum of the per-block partial sums.
+__global__ void __launch_bounds__(256)
+mlp_adam_kernel(float* __restrict__ P, const float* __restrict__ G, int nblocks, int np,
+                double* __restrict__ m1, double* __restrict__ m2, double lr, double c1, double c2)
+{
+    const int p = blockIdx.x * 256 + threadIdx.x;
+    if (p >= np) return;
+    double g = 0.0;
+    for (int b = 0; b < nblocks; ++b) g += (double)G[(size_t)b * np + p];
+    const double m = 0.9 * m1[p] + 0.1 * g;
+    const double v = 0.999 * m2[p] + 0.001 * g * g;
+    m1[p] = m;
+    m2[p] = v;
+    P[p] = (float)((double)P[p] - lr * (m / c1) / (sqrt(v / c2) + 1e-8));
+}
+
+// ------------------------------------------------------------------ FP32 query
+
+struct MlpDev {
+    MlpFrame F;
+    const float* reg;
+    const float* cls;
+    const uint32_t* frag;     // tensor-core weight fragments (BF16 or FP16 per launch)
+};
+
+template <bool REG>
+__device__ __forceinline__ void forward_f32(const float* __restrict__ W, const float X[4],
+                                            float z[Net<REG>::NOUT])
+{
+    using N = Net<REG>;
+    float a[32];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] = X[k];
+#pragma unroll
+    for (int l = 0; l < N::L; ++l) {
+        const int ni = N::in(l), no = N::out(l);
+        const float* Wl = W + N::woff(l);
+        const float* bl = W + N::boff(l);
+        float t[32];
+#pragma unroll
+        for (int o = 0; o < 32; ++o) {
+            if (o < no) {
+                float s = bl[o];
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                    if (k < ni) s = fmaf(Wl[o * ni + k], a[k], s);
+                t[o] = s;
+            }
+        }
+        if (l < N::L - 1) {
+#pragma unroll
+            for (int o = 0; o < 32; ++o) a[o] = tanh_rational(t[o]);
+        } else {
+#pragma unroll
+            for (int o = 0; o < N::NOUT; ++o) z[o] = t[o];
+        }
+    }
+}
+
+__device__ __forceinline__ void finish_ray(const MlpFrame& F, const RedFrame& rf, const float zr[6],
+                                           float o[6])
+{
+    float red[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) red[q] = fmaf(F.t_std[q], zr[q], F.t_mean[q]);
+    const float n2 = fmaf(red[2], red[2], fmaf(red[3], red[3], red[4] * red[4]));
+    float inv = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
+    inv = inv * fmaf(-0.5f * n2, inv * inv, 1.5f);
+    red[2] *= inv;
+    red[3] *= inv;
+    red[4] *= inv;
+    mlp_unreduce(rf, red, o);
+}
+
+__device__ __forceinline__ bool ray_ok(float x, float y, float dx, float dy, float dz, float lam)
+{
+    const bool finite = isfinite(x) & isfinite(y) & isfinite(dx) & isfinite(dy) & isfinite(dz) &
+                        isfinite(lam);
+    return finite && dz > 0.0f && lam > 0.0f;
+}
+
+constexpr int kMB = 128;
+
+template <bool USE_CLS>
+__global__ void __launch_bounds__(kMB)
+mlp_query_f32_kernel(const __grid_constant__ MlpDev D, RaysInDev in, RaysOutDev out, uint32_t n)
+{
+    __shared__ float W[Net<true>::NP + Net<false>::NP];
+    for (int i = threadIdx.x; i < Net<true>::NP; i += kMB) W[i] = D.reg[i];
+    for (int i = threadIdx.x; i < Net<false>::NP; i += kMB) W[Net<true>::NP + i] = D.cls[i];
+    __syncthreads();
+    const uint32_t r = blockIdx.x * kMB + threadIdx.x;
+    if (r >= n) return;
+    const float x = __ldg(in.x + r), y = __ldg(in.y + r), dx = __ldg(in.dx + r),
+                dy = __ldg(in.dy + r), dz = __ldg(in.dz + r), lam = __ldg(in.lam + r);
+    float o[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    uint32_t f = 0;
+    if (!ray_ok(x, y, dx, dy, dz, lam)) {
+        f = LT_FLAG_BAD_INPUT;
+    } else {
+        float X[4];
+        RedFrame rf;
+        mlp_features(D.F, x, y, dx, dy, dz, lam, X, rf);
+        bool valid = true;
+        if (USE_CLS) {
+            float logit[1];
+            forward_f32<false>(W + Net<true>::NP, X, logit);
+            valid = logit[0] > 0.0f;
+        }
+        if (valid) {
+            float zr[6];
+            forward_f32<true>(W, X, zr);
+            finish_ray(D.F, rf, zr, o);
+            f = LT_FLAG_VALID;
+        }
+    }
+    __stcs(out.x + r, o[0]);
+    __stcs(out.y + r, o[1]);
+    __stcs(out.dx + r, o[2]);
+    __stcs(out.dy + r, o[3]);
+    __stcs(out.dz + r, o[4]);
+    __stcs(out.I + r, o[5]);
+    out.flags[r] = (uint8_t)f;
+}
+
+// ------------------------------------------------------------------ tensor-core query
+
+// Fragment tables: for each layer l (regressor layers 0..5, then classifier
+// layers 0..2), for n-tile j and k-step ks, lane `ln` holds two 32-bit words
+// b0 = (W[8j+g][16ks+2t], W[8j+g][16ks+2t+1]) and b1 = (W[8j+g][16ks+8+2t],
+// W[8j+g][16ks+9+2t]) (g = ln/4, t = ln%4; zero outside the matrix), i.e. the
+// m16n8k16 B operand of act x W^T.  Biases stay FP32 in the parameter arrays.
+struct FragLayout {
+    int off[9];    // word offset of each layer
+    int nt[9];     // n-tiles
+    int ks[9];     // k-steps
+    int total;
+};
+
+__host__ __device__ inline FragLayout frag_layout()
+{
+    FragLayout f{};
+    int o = 0;
+    for (int l = 0; l < 9; ++l) {
+        const bool reg = l < 6;
+        const int ll = reg ? l : l - 6;
+        const int no = reg ? Net<true>::out(ll) : Net<false>::out(ll);
+        const int ni = reg ? Net<true>::in(ll) : Net<false>::in(ll);
+        f.nt[l] = (no + 7) / 8;
+        f.ks[l] = (ni + 15) / 16;
+        f.off[l] = o;
+        o += f.nt[l] * f.ks[l] * 32 * 2;
+    }
+    f.total = o;
+    return f;
+}
+
+template <bool BF16>
+__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1)
+{
+    if (BF16)
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+            "{%8,%9}, {%0,%1,%2,%3};\n"
+            : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    else
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+            "{%8,%9}, {%0,%1,%2,%3};\n"
+            : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <bool BF16>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi)
+{
+    if (BF16) {
+        __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<uint32_t*>(&v);
+    }
+    __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// tanh of a packed pair, result packed (the next layer's A-operand word)
+template <bool BF16>
+__device__ __forceinline__ uint32_t tanh2(float lo, float hi)
+{
+    const uint32_t u = pack2<BF16>(lo, hi);
+    uint32_t r;
+    if (BF16)
+        asm("tanh.approx.bf16x2 %0, %1;\n" : "=r"(r) : "r"(u));
+    else
+        asm("tanh.approx.f16x2 %0, %1;\n" : "=r"(r) : "r"(u));
+    return r;
+}
+
+// One network on two 16-ray M-tiles held by a warp.  ain: the first layer's
+// A operands (K = 16, inputs in columns 0..3).  Hidden activations stay in
+// registers: the C fragment of n-tiles (2ks, 2ks+1) after tanh is exactly the
+// A fragment of k-step ks of the next layer.  cout: last layer's C (n-tile 0).
+template <bool BF16, bool REG>
+__device__ __forceinline__ void mma_net(const uint32_t* __restrict__ frag, int lbase,
+                                        const float* __restrict__ P, const FragLayout& FL,
+                                        const uint32_t ain[2][4], float cout[2][4])
+{
+    using N = Net<REG>;
+    const int lane = threadIdx.x & 31, t = lane & 3;
+    uint32_t A[2][2][4];   // [m-tile][k-step][word]
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) A[m][0][w] = ain[m][w];
+#pragma unroll
+    for (int l = 0; l < N::L; ++l) {
+        const int nt = l == N::L - 1 ? 1 : 4;
+        const int ks = l == 0 ? 1 : 2;
+        const uint32_t* fl = frag + FL.off[lbase + l];
+        const float* bl = P + N::boff(l);
+        float C[2][4][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (j < nt) {
+                const int c0 = 8 * j + 2 * t;
+                const float b0 = c0 < N::out(l) ? bl[c0] : 0.0f;
+                const float b1 = c0 + 1 < N::out(l) ? bl[c0 + 1] : 0.0f;
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    C[m][j][0] = b0; C[m][j][1] = b1; C[m][j][2] = b0; C[m][j][3] = b1;
+                }
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (k < ks) {
+                        const uint2 bw = *reinterpret_cast<const uint2*>(fl + ((j * ks + k) * 32 + lane) * 2);
+#pragma unroll
+                        for (int m = 0; m < 2; ++m) mma16816<BF16>(C[m][j], A[m][k], bw.x, bw.y);
+                    }
+                }
+            }
+        }
+        if (l < N::L - 1) {
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    A[m][k][0] = tanh2<BF16>(C[m][2 * k][0], C[m][2 * k][1]);
+                    A[m][k][1] = tanh2<BF16>(C[m][2 * k][2], C[m][2 * k][3]);
+                    A[m][k][2] = tanh2<BF16>(C[m][2 * k + 1][0], C[m][2 * k + 1][1]);
+                    A[m][k][3] = tanh2<BF16>(C[m][2 * k + 1][2], C[m][2 * k + 1][3]);
+                }
+        } else {
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) cout[m][w] = C[m][0][w];
+        }
+    }
+}
+
+constexpr int kTCBlock = 128;
+
+// Each warp handles 32 rays per iteration: lane l owns ray l (M-tile l / 16,
+// row l % 16); the two networks run on the warp's tensor cores.
+template <bool BF16, bool USE_CLS>
+__global__ void __launch_bounds__(kTCBlock)
+mlp_query_mma_kernel(const __grid_constant__ MlpDev D, RaysInDev in, RaysOutDev out, uint32_t n)
+{
+    const FragLayout FL = frag_layout();
+    extern __shared__ uint32_t sfrag[];
+    for (int i = threadIdx.x; i < FL.total; i += kTCBlock) sfrag[i] = D.frag[i];
+    float* sP = reinterpret_cast<float*>(sfrag + FL.total);
+    for (int i = threadIdx.x; i < Net<true>::NP; i += kTCBlock) sP[i] = D.reg[i];
+    for (int i = threadIdx.x; i < Net<false>::NP; i += kTCBlock) sP[Net<true>::NP + i] = D.cls[i];
+    __syncthreads();
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const uint32_t warp = (blockIdx.x * kTCBlock + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * kTCBlock) >> 5;
+    for (uint32_t base = warp * 32; base < n; base += nwarps * 32) {
+        const uint32_t r = base + lane;
+        const bool live = r < n;
+        float x = 0.f, y = 0.f, dx = 0.f, dy = 0.f, dz = 1.f, lam = 500.f;
+        if (live) {
+            x = __ldg(in.x + r); y = __ldg(in.y + r);
+            dx = __ldg(in.dx + r); dy = __ldg(in.dy + r); dz = __ldg(in.dz + r);
+            lam = __ldg(in.lam + r);
+        }
+        const bool ok = live && ray_ok(x, y, dx, dy, dz, lam);
+        float X[4] = {0.f, 0.f, 0.f, 0.f};
+        RedFrame rf = {1.f, 0.f, 1.f};
+        if (ok) mlp_features(D.F, x, y, dx, dy, dz, lam, X, rf);
+        // first-layer A operands: row g and g+8 of each M-tile, columns 2t, 2t+1
+        const uint32_t p01 = pack2<BF16>(X[0], X[1]), p23 = pack2<BF16>(X[2], X[3]);
+        uint32_t ain[2][4];
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const uint32_t s0a = __shfl_sync(full, p01, 16 * m + g);
+            const uint32_t s0b = __shfl_sync(full, p23, 16 * m + g);
+            const uint32_t s1a = __shfl_sync(full, p01, 16 * m + g + 8);
+            const uint32_t s1b = __shfl_sync(full, p23, 16 * m + g + 8);
+            ain[m][0] = t == 0 ? s0a : (t == 1 ? s0b : 0u);
+            ain[m][1] = t == 0 ? s1a : (t == 1 ? s1b : 0u);
+            ain[m][2] = 0u;
+            ain[m][3] = 0u;
+        }
+        float creg[2][4], ccls[2][4];
+        mma_net<BF16, true>(sfrag, 0, sP, FL, ain, creg);
+        if (USE_CLS) mma_net<BF16, false>(sfrag, 6, sP + Net<true>::NP, FL, ain, ccls);
+        // gather each ray's outputs from the fragment owners (rows g / g+8 of its M-tile)
+        const int mm = lane >> 4, rr = lane & 15, gg = rr & 7, half = rr >> 3;
+        float zr[6];
+#pragma unroll
+        for (int tt = 0; tt < 3; ++tt) {
+            const int src = 4 * gg + tt;
+            const float a0 = __shfl_sync(full, creg[0][0], src), a1 = __shfl_sync(full, creg[0][1], src);
+            const float a2 = __shfl_sync(full, creg[0][2], src), a3 = __shfl_sync(full, creg[0][3], src);
+            const float b0 = __shfl_sync(full, creg[1][0], src), b1 = __shfl_sync(full, creg[1][1], src);
+            const float b2 = __shfl_sync(full, creg[1][2], src), b3 = __shfl_sync(full, creg[1][3], src);
+            const float v0 = mm == 0 ? (half ? a2 : a0) : (half ? b2 : b0);
+            const float v1 = mm == 0 ? (half ? a3 : a1) : (half ? b3 : b1);
+            zr[2 * tt] = v0;
+            zr[2 * tt + 1] = v1;
+        }
+        bool valid = ok;
+        if (USE_CLS) {
+            const float l0 = __shfl_sync(full, ccls[0][0], 4 * gg), l2 = __shfl_sync(full, ccls[0][2], 4 * gg);
+            const float m0 = __shfl_sync(full, ccls[1][0], 4 * gg), m2 = __shfl_sync(full, ccls[1][2], 4 * gg);
+            const float logit = mm == 0 ? (half ? l2 : l0) : (half ? m2 : m0);
+            valid = valid && logit > 0.0f;
+        }
+        if (live) {
+            float o[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (valid) finish_ray(D.F, rf, zr, o);
+            __stcs(out.x + r, o[0]);
+            __stcs(out.y + r, o[1]);
+            __stcs(out.dx + r, o[2]);
+            __stcs(out.dy + r, o[3]);
+            __stcs(out.dz + r, o[4]);
+            __stcs(out.I + r, o[5]);
+            out.flags[r] = (uint8_t)(!ok ? LT_FLAG_BAD_INPUT : (valid ? LT_FLAG_VALID : 0u));
+        }
+    }
+}
+
+// features only (for tests and callers that want the network inputs)
+__global__ void __launch_bounds__(256)
+mlp_features_kernel(MlpFrame F, RaysInDev in, float* __restrict__ X, uint32_t n)
+{
+    const uint32_t r = blockIdx.x * 256u + threadIdx.x;
+    if (r >= n) return;
+    float xin[4];
+    RedFrame rf;
+    mlp_features(F, __ldg(in.x + r), __ldg(in.y + r), __ldg(in.dx + r), __ldg(in.dy + r),
+                 __ldg(in.dz + r), __ldg(in.lam + r), xin, rf);
+    reinterpret_cast<float4*>(X)[r] = make_float4(xin[0], xin[1], xin[2], xin[3]);
+}
+
+}  // namespace lt
+
+using namespace lt;
+
+struct lt_mlp {
+    lt_lens lens;
+    int pi = 0, pj = 0;
+    bool cauchy = true;
+    lt_mlp_frame frame = {};
+    double t_mean[6] = {}, t_std[6] = {};
+    MlpFrame F = {};
+    float* reg = nullptr;
+    float* cls = nullptr;
+    uint32_t* frag_bf16 = nullptr;
+    uint32_t* frag_f16 = nullptr;
+    bool frags_stale = true;
+    lt_mlp_stats stats = {};
+    ~lt_mlp()
+    {
+        if (reg) cudaFree(reg);
+        if (cls) cudaFree(cls);
+        if (frag_bf16) cudaFree(frag_bf16);
+        if (frag_f16) cudaFree(frag_f16);
+    }
+};
+
+namespace lt {
+
+static void set_frame(lt_mlp* m)
+{
+    MlpFrame& F = m->F;
+    F.rho2_inv = (float)(2.0 / m->frame.rho);
+    F.winv = (float)(1.0 / m->frame.wmax);
+    F.winv2 = (float)(2.0 / m->frame.wmax);
+    F.lam_lo = (float)m->frame.lam_lo;
+    F.lam_scale = (float)(2.0 / (m->frame.lam_hi - m->frame.lam_lo));
+    for (int q = 0; q < 6; ++q) {
+        F.t_mean[q] = (float)m->t_mean[q];
+        F.t_std[q] = (float)m->t_std[q];
+    }
+}
+
+static lt_status check_frame(const lt_lens* lens, const lt_mlp_frame* fr, int* pi, int* pj)
+{
+    if (!path_ij(lens->S, fr->path_id, pi, pj)) return fail(LT_EINVAL, "learned map: bad path id %d", fr->path_id);
+    if (!(fr->rho > 0.0) || !(fr->wmax > 0.0) || !(fr->lam_hi > fr->lam_lo))
+        return fail(LT_EINVAL, "learned map: empty input box");
+    return LT_OK;
+}
+
+static lt_mlp* new_mlp(const lt_lens* lens, const lt_mlp_frame* fr, int pi, int pj)
+{
+    lt_mlp* m = new (std::nothrow) lt_mlp();
+    if (!m) return nullptr;
+    m->lens = *lens;
+    m->lens.presc.surfaces = m->lens.surf;
+    m->lens.presc.glasses = m->lens.glass;
+    m->pi = pi;
+    m->pj = pj;
+    m->cauchy = lens_all_cauchy(lens->dev);
+    m->frame = *fr;
+    if (cudaMalloc(&m->reg, LT_MLP_REG_PARAMS * 4) != cudaSuccess ||
+        cudaMalloc(&m->cls, LT_MLP_CLS_PARAMS * 4) != cudaSuccess) {
+        delete m;
+        return nullptr;
+    }
+    return m;
+}
+
+// host-side fragment tables from the current FP32 parameters
+static lt_status build_frags(lt_mlp* m)
+{
+    const FragLayout FL = frag_layout();
+    std::vector<float> reg(LT_MLP_REG_PARAMS), cls(LT_MLP_CLS_PARAMS);
+    LT_CUDA_TRY(cudaMemcpy(reg.data(), m->reg, reg.size() * 4, cudaMemcpyDeviceToHost));
+    LT_CUDA_TRY(cudaMemcpy(cls.data(), m->cls, cls.size() * 4, cudaMemcpyDeviceToHost));
+    std::vector<uint32_t> fb(FL.total), fh(FL.total);
+    for (int l = 0; l < 9; ++l) {
+        const bool isreg = l < 6;
+        const int ll = isreg ? l : l - 6;
+        const int ni = isreg ? Net<true>::in(ll) : Net<false>::in(ll);
+        const int no = isreg ? Net<true>::out(ll) : Net<false>::out(ll);
+        const float* W = isreg ? reg.data() + Net<true>::woff(ll) : cls.data() + Net<false>::woff(ll);
+        auto w = [&](int o, int k) { return (o < no && k < ni) ? W[o * ni + k] : 0.0f; };
+        for (int j = 0; j < FL.nt[l]; ++j)
+            for (int ks = 0; ks < FL.ks[l]; ++ks)
+                for (int ln = 0; ln < 32; ++ln) {
+                    const int g = ln >> 2, t = ln & 3, o = 8 * j + g;
+                    const float v[4] = {w(o, 16 * ks + 2 * t), w(o, 16 * ks + 2 * t + 1),
+                                        w(o, 16 * ks + 8 + 2 * t), w(o, 16 * ks + 9 + 2 * t)};
+                    const size_t at = (size_t)FL.off[l] + ((size_t)(j * FL.ks[l] + ks) * 32 + ln) * 2;
+                    __nv_bfloat162 b0 = __floats2bfloat162_rn(v[0], v[1]);
+                    __nv_bfloat162 b1 = __floats2bfloat162_rn(v[2], v[3]);
+                    __half2 h0 = __floats2half2_rn(v[0], v[1]);
+                    __half2 h1 = __floats2half2_rn(v[2], v[3]);
+                    std::memcpy(&fb[at], &b0, 4);
+                    std::memcpy(&fb[at + 1], &b1, 4);
+                    std::memcpy(&fh[at], &h0, 4);
+                    std::memcpy(&fh[at + 1], &h1, 4);
+                }
+    }
+    if (!m->frag_bf16 && cudaMalloc(&m->frag_bf16, FL.total * 4) != cudaSuccess)
+        return fail(LT_ENOMEM, "learned map: fragment table allocation");
+    if (!m->frag_f16 && cudaMalloc(&m->frag_f16, FL.total * 4) != cudaSuccess)
+        return fail(LT_ENOMEM, "learned map: fragment table allocation");
+    LT_CUDA_TRY(cudaMemcpy(m->frag_bf16, fb.data(), FL.total * 4, cudaMemcpyHostToDevice));
+    LT_CUDA_TRY(cudaMemcpy(m->frag_f16, fh.data(), FL.total * 4, cudaMemcpyHostToDevice));
+    m->frags_stale = false;
+    return LT_OK;
+}
+
+template <bool REG>
+static size_t train_smem()
+{
+    return (size_t)(((Net<REG>::NP + 3) & ~3) + Net<REG>::L * 32 * kTB + 32 * kTB) * sizeof(float);
+}
+
+// one training step of net REG on the batch; returns the batch-mean loss when `want_loss`
+template <bool REG>
+static lt_status train_step(float* P, const TrainBatch& tb, const MlpFrame& F, float* G,
+                            double* lossbuf, double* m1, double* m2, double lr, long t,
+                            cudaStream_t st)
+{
+    const int blocks = (tb.B + kTB - 1) / kTB;
+    {
+        ProfScope prof(REG ? "mlp_train_reg_kernel" : "mlp_train_cls_kernel", st);
+        mlp_train_kernel<REG><<<blocks, kTB, train_smem<REG>(), st>>>(P, tb, F, G, lossbuf);
+    }
+    LT_CUDA_TRY(cudaGetLastError());
+    if (m1) {
+        const double c1 = 1.0 - std::pow(0.9, (double)t), c2 = 1.0 - std::pow(0.999, (double)t);
+        ProfScope prof("mlp_adam_kernel", st);
+        mlp_adam_kernel<<<(Net<REG>::NP + 255) / 256, 256, 0, st>>>(P, G, blocks, Net<REG>::NP, m1, m2, lr, c1, c2);
+        LT_CUDA_TRY(cudaGetLastError());
+    }
+    return LT_OK;
+}
+
+static lt_status set_train_attrs()
+{
+    static bool done = false;
+    if (done) return LT_OK;
+    LT_CUDA_TRY(cudaFuncSetAttribute(mlp_train_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)train_smem<true>()));
+    LT_CUDA_TRY(cudaFuncSetAttribute(mlp_train_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)train_smem<false>()));
+    done = true;
+    return LT_OK;
+}
+
+// run `steps` Adam steps of one network; records the mean loss of the last 100
+template <bool REG>
+static lt_status train_net(lt_mlp* m, float* P, TrainBatch tb, int steps, double lr0, double decay,
+                           int every, double* last_loss, cudaStream_t st)
+{
+    const int max_blocks = (tb.B + kTB - 1) / kTB;
+    float* G = nullptr;
+    double *lossbuf = nullptr, *m1 = nullptr, *m2 = nullptr;
+    const int np = Net<REG>::NP;
+    lt_status s = LT_OK;
+    std::vector<double> hl;
+    const int tail = std::min(steps, 100);
+    double acc = 0.0;
+    if (cudaMalloc(&G, (size_t)max_blocks * np * 4) != cudaSuccess ||
+        cudaMalloc(&lossbuf, (size_t)max_blocks * 8 * (tail > 0 ? tail : 1)) != cudaSuccess ||
+        cudaMalloc(&m1, np * 8) != cudaSuccess || cudaMalloc(&m2, np * 8) != cudaSuccess) {
+        s = fail(LT_ENOMEM, "learned map: training buffers");
+    } else {
+        cudaMemsetAsync(m1, 0, np * 8, st);
+        cudaMemsetAsync(m2, 0, np * 8, st);
+        for (int k = 0; k < steps && s == LT_OK; ++k) {
+            tb.step = (uint64_t)k;
+            const double lr = lr0 * std::pow(decay, (double)(k / (every > 0 ? every : 1)));
+            double* lb = lossbuf;
+            if (k >= steps - tail) lb = lossbuf + (size_t)(k - (steps - tail)) * max_blocks;
+            s = train_step<REG>(P, tb, m->F, G, lb, m1, m2, lr, k + 1, st);
+        }
+        if (s == LT_OK && tail > 0) {
+            hl.resize((size_t)tail * max_blocks);
+            if (cudaMemcpyAsync(hl.data(), lossbuf, hl.size() * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                s = fail(LT_ECUDA, "learned map: loss read-back");
+            for (double v : hl) acc += v;
+            *last_loss = acc / ((double)tail * tb.B);
+        }
+    }
+    if (G) cudaFree(G);
+    if (lossbuf) cudaFree(lossbuf);
+    if (m1) cudaFree(m1);
+    if (m2) cudaFree(m2);
+    return s;
+}
+
+}  // namespace lt
+
+extern "C" {
+
+lt_status lt_mlp_create(const lt_lens* lens, const lt_mlp_frame* frame, const float* reg,
+                        const float* cls, const double* t_mean, const double* t_std, lt_mlp** out)
+{
+    clear_error();
+    if (!lens || !frame || !reg || !cls || !t_mean || !t_std || !out)
+        return fail(LT_EINVAL, "lt_mlp_create: NULL argument");
+    *out = nullptr;
+    int pi, pj;
+    lt_status s = check_frame(lens, frame, &pi, &pj);
+    if (s != LT_OK) return s;
+    lt_mlp* m = new_mlp(lens, frame, pi, pj);
+    if (!m) return fail(LT_ENOMEM, "lt_mlp_create: allocation");
+    for (int q = 0; q < 6; ++q) {
+        if (!(t_std[q] > 0.0)) { delete m; return fail(LT_EINVAL, "lt_mlp_create: t_std must be > 0"); }
+        m->t_mean[q] = t_mean[q];
+        m->t_std[q] = t_std[q];
+        m->stats.t_mean[q] = t_mean[q];
+        m->stats.t_std[q] = t_std[q];
+    }
+    set_frame(m);
+    if (cudaMemcpy(m->reg, reg, LT_MLP_REG_PARAMS * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m->cls, cls, LT_MLP_CLS_PARAMS * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        delete m;
+        return fail(LT_ECUDA, "lt_mlp_create: upload");
+    }
+    *out = m;
+    return LT_OK;
+}
+
+void lt_destroy_mlp(lt_mlp* m) { delete m; }
+
+lt_status lt_mlp_stats_get(const lt_mlp* m, lt_mlp_stats* out)
+{
+    if (!m || !out) return fail(LT_EINVAL, "lt_mlp_stats_get: NULL argument");
+    *out = m->stats;
+    return LT_OK;
+}
+
+lt_status lt_mlp_get_params(const lt_mlp* m, float* reg, float* cls)
+{
+    clear_error();
+    if (!m) return fail(LT_EINVAL, "lt_mlp_get_params: NULL map");
+    if (reg) LT_CUDA_TRY(cudaMemcpy(reg, m->reg, LT_MLP_REG_PARAMS * 4, cudaMemcpyDeviceToHost));
+    if (cls) LT_CUDA_TRY(cudaMemcpy(cls, m->cls, LT_MLP_CLS_PARAMS * 4, cudaMemcpyDeviceToHost));
+    return LT_OK;
+}
+
+lt_status lt_mlp_train(const lt_lens* lens, const lt_mlp_opts* o, lt_mlp** out, lt_stream stream)
+{
+    clear_error();
+    auto t0 = std::chrono::steady_clock::now();
+    if (!lens || !o || !out || !o->init_reg || !o->init_cls) return fail(LT_EINVAL, "lt_mlp_train: NULL argument");
+    *out = nullptr;
+    int pi, pj;
+    lt_status s = check_frame(lens, &o->frame, &pi, &pj);
+    if (s != LT_OK) return s;
+    if (o->n_fit < 1 || o->n_fit >= (1ull << 31)) return fail(LT_EINVAL, "lt_mlp_train: n_fit out of range");
+    const void* ps[] = {o->fit_x, o->fit_y, o->fit_dx, o->fit_dy, o->fit_dz, o->fit_lambda};
+    for (const void* p : ps)
+        if (!p || !aligned16(p)) return fail(LT_EINVAL, "lt_mlp_train: fit arrays must be non-NULL and 16-byte aligned");
+    if (o->reg_batch < 1 || o->cls_batch < 1 || o->reg_steps < 0 || o->cls_steps < 0 ||
+        (o->ft_steps > 0 && o->ft_batch < 1))
+        return fail(LT_EINVAL, "lt_mlp_train: bad step or batch count");
+    if ((s = set_train_attrs()) != LT_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    lt_mlp* m = new_mlp(lens, &o->frame, pi, pj);
+    if (!m) return fail(LT_ENOMEM, "lt_mlp_train: allocation");
+    const uint32_t n = (uint32_t)o->n_fit;
+    float *X = nullptr, *T = nullptr, *lab = nullptr;
+    uint32_t *vlist = nullptr, *vcount = nullptr;
+    double* sums = nullptr;
+    do {
+        if (cudaMemcpy(m->reg, o->init_reg, LT_MLP_REG_PARAMS * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(m->cls, o->init_cls, LT_MLP_CLS_PARAMS * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+            s = fail(LT_ECUDA, "lt_mlp_train: parameter upload");
+            break;
+        }
+        if (cudaMalloc(&X, (size_t)n * 16) != cudaSuccess || cudaMalloc(&T, (size_t)n * 24) != cudaSuccess ||
+            cudaMalloc(&lab, (size_t)n * 4) != cudaSuccess || cudaMalloc(&vlist, (size_t)n * 4) != cudaSuccess ||
+            cudaMalloc(&vcount, 4) != cudaSuccess || cudaMalloc(&sums, 12 * 8) != cudaSuccess) {
+            s = fail(LT_ENOMEM, "lt_mlp_train: training data allocation");
+            break;
+        }
+        // provisional frame for the features (target statistics come next)
+        for (int q = 0; q < 6; ++q) { m->t_mean[q] = 0.0; m->t_std[q] = 1.0; }
+        set_frame(m);
+        cudaMemsetAsync(vcount, 0, 4, st);
+        cudaMemsetAsync(sums, 0, 96, st);
+        RaysInDev fit{o->fit_x, o->fit_y, o->fit_dx, o->fit_dy, o->fit_dz, o->fit_lambda};
+        if (m->cauchy)
+            mlp_prep_kernel<true><<<(n + 255) / 256, 256, 0, st>>>(lens->dev, pi, pj, fit, n, m->F, X, T, lab, vlist, vcount);
+        else
+            mlp_prep_kernel<false><<<(n + 255) / 256, 256, 0, st>>>(lens->dev, pi, pj, fit, n, m->F, X, T, lab, vlist, vcount);
+        mlp_stats_kernel<<<152 * 4, 256, 0, st>>>(T, vlist, vcount, sums);
+        uint32_t nv = 0;
+        double hs[12];
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(&nv, vcount, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(hs, sums, 96, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            s = fail(LT_ECUDA, "lt_mlp_train: data preparation");
+            break;
+        }
+        if (nv < 2) { s = fail(LT_EINVAL, "lt_mlp_train: fewer than 2 valid training rays"); break; }
+        for (int q = 0; q < 6; ++q) {
+            const double mean = hs[q] / nv;
+            const double var = hs[6 + q] / nv - mean * mean;
+            m->t_mean[q] = mean;
+            m->t_std[q] = var > 1e-24 ? std::sqrt(var) : 1.0;
+            m->stats.t_mean[q] = m->t_mean[q];
+            m->stats.t_std[q] = m->t_std[q];
+        }
+        set_frame(m);
+        m->stats.n_train = n;
+        m->stats.n_valid = nv;
+        TrainBatch tr{X, T, lab, vlist, nv, o->seed, 0, o->reg_batch, 0};
+        if (o->reg_steps > 0 &&
+            (s = train_net<true>(m, m->reg, tr, o->reg_steps, o->lr, o->lr_decay, o->decay_every,
+                                 &m->stats.reg_loss, st)) != LT_OK)
+            break;
+        if (o->ft_steps > 0) {
+            TrainBatch ft{X, T, lab, vlist, nv, o->seed ^ 0x5bd1e995ull, 0, o->ft_batch, 0};
+            if ((s = train_net<true>(m, m->reg, ft, o->ft_steps, o->ft_lr, o->lr_decay, o->decay_every,
+                                     &m->stats.reg_loss, st)) != LT_OK)
+                break;
+        }
+        // classifier: batches drawn from all n rays
+        TrainBatch tc{X, T, lab, nullptr, n, o->seed ^ 0x9e3779b97f4a7c15ull, 0, o->cls_batch, 0};
+        if (o->cls_steps > 0)
+            s = train_net<false>(m, m->cls, tc, o->cls_steps, o->lr, o->lr_decay, o->decay_every,
+                                 &m->stats.cls_loss, st);
+    } while (0);
+    if (X) cudaFree(X);
+    if (T) cudaFree(T);
+    if (lab) cudaFree(lab);
+    if (vlist) cudaFree(vlist);
+    if (vcount) cudaFree(vcount);
+    if (sums) cudaFree(sums);
+    if (s != LT_OK) { delete m; return s; }
+    m->frags_stale = true;
+    m->stats.train_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = m;
+    return LT_OK;
+}
+
+lt_status lt_mlp_query(const lt_mlp* mc, const lt_rays_in* in, const float* lam, const lt_rays_out* out,
+                       size_t n, int32_t precision, lt_stream stream)
+{
+    clear_error();
+    lt_mlp* m = const_cast<lt_mlp*>(mc);
+    if (!m) return fail(LT_EINVAL, "lt_mlp_query: NULL map");
+    lt_status s = check_io(in, lam, out, n, "lt_mlp_query");
+    if (s != LT_OK || n == 0) return s;
+    if (n >= (1ull << 31)) return fail(LT_EINVAL, "lt_mlp_query: n must be < 2^31");
+    cudaStream_t st = (cudaStream_t)stream;
+    RaysInDev din{in->x, in->y, in->dx, in->dy, in->dz, lam};
+    RaysOutDev dout{out->x, out->y, out->dx, out->dy, out->dz, out->I, out->flags};
+    MlpDev D{m->F, m->reg, m->cls, nullptr};
+    const uint32_t nn = (uint32_t)n;
+    if (precision == LT_MLP_F32 || precision == LT_MLP_F32_NOCLS) {
+        ProfScope prof("mlp_query_f32_kernel", st);
+        const unsigned g = (nn + kMB - 1) / kMB;
+        if (precision == LT_MLP_F32) mlp_query_f32_kernel<true><<<g, kMB, 0, st>>>(D, din, dout, nn);
+        else mlp_query_f32_kernel<false><<<g, kMB, 0, st>>>(D, din, dout, nn);
+    } else if (precision == LT_MLP_BF16 || precision == LT_MLP_F16) {
+        if (m->frags_stale && (s = build_frags(m)) != LT_OK) return s;
+        const FragLayout FL = frag_layout();
+        const size_t smem = (size_t)FL.total * 4 + (LT_MLP_REG_PARAMS + LT_MLP_CLS_PARAMS) * 4;
+        D.frag = precision == LT_MLP_BF16 ? m->frag_bf16 : m->frag_f16;
+        const void* k = precision == LT_MLP_BF16 ? (const void*)mlp_query_mma_kernel<true, true>
+                                                 : (const void*)mlp_query_mma_kernel<false, true>;
+        LT_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const unsigned g = persistent_blocks(k, kTCBlock, nn, 32);
+        ProfScope prof(precision == LT_MLP_BF16 ? "mlp_query_bf16_kernel" : "mlp_query_f16_kernel", st);
+        if (precision == LT_MLP_BF16) mlp_query_mma_kernel<true, true><<<g, kTCBlock, smem, st>>>(D, din, dout, nn);
+        else mlp_query_mma_kernel<false, true><<<g, kTCBlock, smem, st>>>(D, din, dout, nn);
+    } else {
+        return fail(LT_EINVAL, "lt_mlp_query: unknown precision %d", precision);
+    }
+    LT_CUDA_TRY(cudaGetLastError());
+    return LT_OK;
+}
+
+lt_status lt_mlp_grad(const lt_mlp* m, int32_t net, const float* X, const float* targets, int32_t B,
+                      double* grad, double* loss)
+{
+    clear_error();
+    if (!m || !X || !targets || !grad || B < 1) return fail(LT_EINVAL, "lt_mlp_grad: bad argument");
+    if (net != 0 && net != 1) return fail(LT_EINVAL, "lt_mlp_grad: net must be 0 or 1");
+    lt_status s = set_train_attrs();
+    if (s != LT_OK) return s;
+    const int blocks = (B + kTB - 1) / kTB;
+    const int np = net == 0 ? LT_MLP_REG_PARAMS : LT_MLP_CLS_PARAMS;
+    float* G = nullptr;
+    double* lb = nullptr;
+    if (cudaMalloc(&G, (size_t)blocks * np * 4) != cudaSuccess || cudaMalloc(&lb, (size_t)blocks * 8) != cudaSuccess) {
+        if (G) cudaFree(G);
+        return fail(LT_ENOMEM, "lt_mlp_grad: buffers");
+    }
+    TrainBatch tb{X, net == 0 ? targets : nullptr, net == 1 ? targets : nullptr, nullptr, 0, 0, 0, B, 1};
+    if (net == 0) s = train_step<true>(m->reg, tb, m->F, G, lb, nullptr, nullptr, 0.0, 0, 0);
+    else s = train_step<false>(m->cls, tb, m->F, G, lb, nullptr, nullptr, 0.0, 0, 0);
+    std::vector<float> hg((size_t)blocks * np);
+    std::vector<double> hl(blocks);
+    if (s == LT_OK && (cudaMemcpy(hg.data(), G, hg.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                       cudaMemcpy(hl.data(), lb, hl.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess))
+        s = fail(LT_ECUDA, "lt_mlp_grad: read-back");
+    cudaFree(G);
+    cudaFree(lb);
+    if (s != LT_OK) return s;
+    for (int p = 0; p < np; ++p) {
+        double g = 0.0;
+        for (int b = 0; b < blocks; ++b) g += hg[(size_t)b * np + p];
+        grad[p] = g;
+    }
+    if (loss) {
+        double l = 0.0;
+        for (double v : hl) l += v;
+        *loss = l / B;
+    }
+    return LT_OK;
+}
+
+lt_status lt_mlp_features(const lt_mlp* m, const lt_rays_in* in, const float* lam, float* X, size_t n,
+                          lt_stream stream)
+{
+    clear_error();
+    if (!m || !in || !X) return fail(LT_EINVAL, "lt_mlp_features: NULL argument");
+    if (n == 0) return LT_OK;
+    RaysInDev din{in->x, in->y, in->dx, in->dy, in->dz, lam};
+    mlp_features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(m->F, din, X, (uint32_t)n);
+    LT_CUDA_TRY(cudaGetLastError());
+    return LT_OK;
+}
+
+}  // extern "C"

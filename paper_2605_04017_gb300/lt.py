@@ -413,3 +413,178 @@ def query_noalloc(gmap: "Map", inp: Sequence, lam, out: Sequence, n: int,
     ro = rays_out(*out)
     check(L.lt_query_noalloc(gmap.handle, ctypes.byref(ri), _ptr(lam), ctypes.byref(ro), n, mode,
                              _stream_handle(stream)))
+
+
+# ------------------------------------------------------------------ learned maps
+
+MLP_REG_PARAMS = 4582
+MLP_CLS_PARAMS = 1249
+MLP_F32, MLP_BF16, MLP_F16, MLP_F32_NOCLS = 0, 1, 2, 3
+
+
+class c_mlp_frame(ctypes.Structure):
+    _fields_ = [("path_id", ctypes.c_int32), ("rho", ctypes.c_double), ("wmax", ctypes.c_double),
+                ("lam_lo", ctypes.c_double), ("lam_hi", ctypes.c_double)]
+
+
+class c_mlp_opts(ctypes.Structure):
+    _fields_ = [("frame", c_mlp_frame),
+                ("fit_x", _fptr), ("fit_y", _fptr), ("fit_dx", _fptr), ("fit_dy", _fptr),
+                ("fit_dz", _fptr), ("fit_lambda", _fptr), ("n_fit", ctypes.c_size_t),
+                ("init_reg", _fptr), ("init_cls", _fptr),
+                ("reg_steps", ctypes.c_int32), ("reg_batch", ctypes.c_int32),
+                ("cls_steps", ctypes.c_int32), ("cls_batch", ctypes.c_int32),
+                ("lr", ctypes.c_double), ("lr_decay", ctypes.c_double),
+                ("decay_every", ctypes.c_int32),
+                ("ft_steps", ctypes.c_int32), ("ft_batch", ctypes.c_int32), ("ft_lr", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+class c_mlp_stats(ctypes.Structure):
+    _fields_ = [("n_train", ctypes.c_uint64), ("n_valid", ctypes.c_uint64),
+                ("reg_loss", ctypes.c_double), ("cls_loss", ctypes.c_double),
+                ("t_mean", ctypes.c_double * 6), ("t_std", ctypes.c_double * 6),
+                ("train_ms", ctypes.c_double)]
+
+
+def _declare_mlp(L: ctypes.CDLL) -> None:
+    vp = ctypes.c_void_p
+    st = ctypes.c_int
+    L.lt_mlp_train.restype = st
+    L.lt_mlp_train.argtypes = [vp, ctypes.POINTER(c_mlp_opts), ctypes.POINTER(vp), vp]
+    L.lt_mlp_create.restype = st
+    L.lt_mlp_create.argtypes = [vp, ctypes.POINTER(c_mlp_frame), vp, vp, vp, vp, ctypes.POINTER(vp)]
+    L.lt_destroy_mlp.restype = None
+    L.lt_destroy_mlp.argtypes = [vp]
+    L.lt_mlp_stats_get.restype = st
+    L.lt_mlp_stats_get.argtypes = [vp, ctypes.POINTER(c_mlp_stats)]
+    L.lt_mlp_get_params.restype = st
+    L.lt_mlp_get_params.argtypes = [vp, vp, vp]
+    L.lt_mlp_query.restype = st
+    L.lt_mlp_query.argtypes = [vp, ctypes.POINTER(c_rays_in), vp, ctypes.POINTER(c_rays_out),
+                               ctypes.c_size_t, ctypes.c_int32, vp]
+    L.lt_mlp_grad.restype = st
+    L.lt_mlp_grad.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.c_int32, vp,
+                              ctypes.POINTER(ctypes.c_double)]
+    L.lt_mlp_features.restype = st
+    L.lt_mlp_features.argtypes = [vp, ctypes.POINTER(c_rays_in), vp, vp, ctypes.c_size_t, vp]
+
+
+_prev_declare = _declare
+
+
+def _declare(L: ctypes.CDLL) -> None:  # noqa: F811
+    _prev_declare(L)
+    _declare_mlp(L)
+
+
+def mlp_frame(path_id: int, rho: float, wmax: float, lam_lo: float = 380.0,
+              lam_hi: float = 780.0) -> c_mlp_frame:
+    return c_mlp_frame(path_id, rho, wmax, lam_lo, lam_hi)
+
+
+class Mlp:
+    """A learned map resident on the device."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    @classmethod
+    def create(cls, lens: Lens, frame: c_mlp_frame, reg, cls_params, t_mean, t_std) -> "Mlp":
+        import numpy as np
+        reg = np.ascontiguousarray(reg, np.float32)
+        cp = np.ascontiguousarray(cls_params, np.float32)
+        tm = np.ascontiguousarray(t_mean, np.float64)
+        ts = np.ascontiguousarray(t_std, np.float64)
+        h = ctypes.c_void_p()
+        check(lib().lt_mlp_create(lens.handle, ctypes.byref(frame), reg.ctypes.data, cp.ctypes.data,
+                                  tm.ctypes.data, ts.ctypes.data, ctypes.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def train(cls, lens: Lens, frame: c_mlp_frame, fit, init_reg, init_cls, reg_steps=2000,
+              reg_batch=8192, cls_steps=2000, cls_batch=8192, lr=1e-4, lr_decay=0.95,
+              decay_every=10000, ft_steps=0, ft_batch=8192, ft_lr=1e-6, seed=1,
+              stream=None) -> "Mlp":
+        """fit: a batch.DeviceRays of training rays; init_*: host FP32 parameters."""
+        import numpy as np
+        ir = np.ascontiguousarray(init_reg, np.float32)
+        ic = np.ascontiguousarray(init_cls, np.float32)
+        o = c_mlp_opts()
+        o.frame = frame
+        o.fit_x, o.fit_y, o.fit_dx, o.fit_dy, o.fit_dz = [_ptr(t) for t in fit.inp]
+        o.fit_lambda = _ptr(fit.lam)
+        o.n_fit = fit.n
+        o.init_reg, o.init_cls = ir.ctypes.data, ic.ctypes.data
+        o.reg_steps, o.reg_batch, o.cls_steps, o.cls_batch = reg_steps, reg_batch, cls_steps, cls_batch
+        o.lr, o.lr_decay, o.decay_every = lr, lr_decay, decay_every
+        o.ft_steps, o.ft_batch, o.ft_lr = ft_steps, ft_batch, ft_lr
+        o.seed = seed
+        h = ctypes.c_void_p()
+        check(lib().lt_mlp_train(lens.handle, ctypes.byref(o), ctypes.byref(h), _stream_handle(stream)))
+        return cls(h)
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().lt_destroy_mlp(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        s = c_mlp_stats()
+        check(lib().lt_mlp_stats_get(self.handle, ctypes.byref(s)))
+        return {"n_train": s.n_train, "n_valid": s.n_valid, "reg_loss": s.reg_loss,
+                "cls_loss": s.cls_loss, "t_mean": list(s.t_mean), "t_std": list(s.t_std),
+                "train_ms": s.train_ms}
+
+    def params(self):
+        import numpy as np
+        reg = np.empty(MLP_REG_PARAMS, np.float32)
+        cp = np.empty(MLP_CLS_PARAMS, np.float32)
+        check(lib().lt_mlp_get_params(self.handle, reg.ctypes.data, cp.ctypes.data))
+        return reg, cp
+
+    def query(self, inp: Sequence, lam, out: Sequence, n: int, precision: int = MLP_F32,
+              stream=None) -> None:
+        ri = rays_in(*inp)
+        ro = rays_out(*out)
+        check(lib().lt_mlp_query(self.handle, ctypes.byref(ri), _ptr(lam), ctypes.byref(ro), n,
+                                 precision, _stream_handle(stream)))
+
+    def grad(self, net: int, X, targets, B: int):
+        """(gradient FP64 numpy array, loss) of one batch; X, targets: device tensors."""
+        import numpy as np
+        g = np.zeros(MLP_REG_PARAMS if net == 0 else MLP_CLS_PARAMS, np.float64)
+        loss = ctypes.c_double()
+        check(lib().lt_mlp_grad(self.handle, net, _ptr(X), _ptr(targets), B, g.ctypes.data,
+                                ctypes.byref(loss)))
+        return g, loss.value
+
+    def features(self, inp: Sequence, lam, X, n: int, stream=None) -> None:
+        ri = rays_in(*inp)
+        check(lib().lt_mlp_features(self.handle, ctypes.byref(ri), _ptr(lam), _ptr(X), n,
+                                    _stream_handle(stream)))
+
+
+def flat_params(params) -> "np.ndarray":
+    """Oracle-style [(W, b), ...] (W: out x in) -> the library's flat FP32 layout."""
+    import numpy as np
+    return np.concatenate([np.concatenate([W.reshape(-1), b]) for W, b in params]).astype(np.float32)
+
+
+def unflat_params(flat, sizes):
+    """The library's flat layout -> [(W, b), ...] in FP64 for layer sizes [in, h, ..., out]."""
+    import numpy as np
+    out, o = [], 0
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        W = np.asarray(flat[o:o + a * b], np.float64).reshape(b, a)
+        o += a * b
+        bb = np.asarray(flat[o:o + b], np.float64)
+        o += b
+        out.append((W, bb))
+    return out

@@ -177,3 +177,15 @@ def test_query_masks_invalid():
     out, valid, logit = mlp.query(cls, reg, rays, 12.0, 0.25, np.zeros(6), np.ones(6))
     assert np.all(out[~valid] == 0.0)
     assert np.allclose(np.linalg.norm(out[valid, 2:5], axis=1), 1.0)
+
+
+def test_lambert_tanh_error_bound_and_series():
+    x = np.linspace(-20, 20, 400001)
+    err = np.abs(mlp.tanh_lambert(x) - np.tanh(x))
+    assert err.max() < 1.9e-6
+    # the 9/10 truncation agrees with the Taylor series of tanh to high order at small x
+    s = np.array([1e-3, 0.05, 0.1])
+    taylor = s - s ** 3 / 3 + 2 * s ** 5 / 15 - 17 * s ** 7 / 315 + 62 * s ** 9 / 2835
+    assert np.allclose(mlp.tanh_lambert(s), taylor, rtol=0, atol=1e-12)
+    assert np.allclose(mlp.tanh_lambert(-x), -mlp.tanh_lambert(x))
+    assert mlp.tanh_lambert(np.array([7.0]))[0] == 1.0
