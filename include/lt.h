@@ -162,6 +162,33 @@ lt_status lt_trace(const lt_lens* lens, const lt_rays_in* in, const float* lambd
 lt_status lt_trace_host(const lt_lens* lens, const lt_rays_in* in, const float* lambda_nm,
                         int32_t path_id, const lt_rays_out* out, size_t n);
 
+/* Compacted output of lt_trace_paths: path p owns the segment
+ * [p * capacity, (p + 1) * capacity) of every array.  Only rays that reach
+ * the image plane are written, in no particular order within a segment. */
+typedef struct {
+    float *x, *y, *dx, *dy, *dz, *I;  /* as lt_rays_out, valid rays only */
+    uint8_t* flags;                   /* LT_FLAG_* of each written ray (VALID always set) */
+    uint32_t* ray_index;              /* which entrance ray (0..n-1) the entry belongs to */
+    uint32_t* valid_count;            /* n_paths counters: rays of path p that reached the image */
+    size_t capacity;                  /* entries per path segment (>= 1) */
+} lt_paths_out;
+
+/* Trace the same n entrance rays along n_paths paths in one launch (the flare
+ * workload of Sec. 4.2: the main path plus every two-bounce ghost (i, j),
+ * each ray's wavelength drawn per path).  path_ids: HOST array of n_paths ids
+ * (duplicates allowed).  lambda_nm: device array; path p reads
+ * lambda_nm[p * lambda_stride + r] (lambda_stride = 0: one wavelength array
+ * for all paths).  Rays are compacted per path; valid_count[p] is set to the
+ * true count even when it exceeds capacity, in which case only `capacity`
+ * of them (which ones is unspecified) are written -- compare the count with
+ * capacity after the stream synchronises.  Per-ray results are identical to
+ * lt_trace of the same ray, path and wavelength.
+ * Errors: LT_EINVAL (NULL pointer, misaligned array, n_paths < 1 or > 1024,
+ * bad path id, capacity 0, n >= 2^32), LT_ECUDA.  n = 0 zeroes the counters. */
+lt_status lt_trace_paths(const lt_lens* lens, const lt_rays_in* in, const float* lambda_nm,
+                         size_t lambda_stride, const int32_t* path_ids, int32_t n_paths,
+                         const lt_paths_out* out, size_t n, lt_stream stream);
+
 /* ------------------------------------------------------------------ maps */
 
 /*

@@ -49,3 +49,27 @@ class HostRays:
         self.out = [torch.empty(n, dtype=torch.float32, pin_memory=pin) for _ in range(6)]
         self.flags = torch.empty(n, dtype=torch.uint8, pin_memory=pin)
         self.n = n
+
+
+class PathsOut:
+    """Compacted per-path outputs of lt_trace_paths on the GPU: n_paths
+    segments of `capacity` entries, plus one counter per path."""
+
+    def __init__(self, n_paths, capacity, device="cuda"):
+        m = n_paths * capacity
+        self.f = [torch.empty(m, dtype=torch.float32, device=device) for _ in range(6)]
+        self.flags = torch.empty(m, dtype=torch.uint8, device=device)
+        self.ray_index = torch.empty(m, dtype=torch.int32, device=device)
+        self.valid_count = torch.zeros(n_paths, dtype=torch.int32, device=device)
+        self.n_paths, self.capacity = n_paths, capacity
+
+    def counts(self):
+        return self.valid_count.cpu().numpy().astype(np.int64)
+
+    def path(self, p):
+        """(ray_index[k], out[k, 6], flags[k]) of the entries path p wrote."""
+        k = min(int(self.valid_count[p].item()), self.capacity)
+        lo = p * self.capacity
+        out = torch.stack([t[lo:lo + k] for t in self.f], dim=1).cpu().numpy()
+        idx = self.ray_index[lo:lo + k].cpu().numpy().view(np.uint32)
+        return idx, out, self.flags[lo:lo + k].cpu().numpy()

@@ -239,6 +239,33 @@ def trace_host(lens: Lens, inp: Sequence, lam, path_id: int, out: Sequence, n: i
                               n))
 
 
+class c_paths_out(ctypes.Structure):
+    _fields_ = [("x", _fptr), ("y", _fptr), ("dx", _fptr), ("dy", _fptr), ("dz", _fptr),
+                ("I", _fptr), ("flags", ctypes.c_void_p), ("ray_index", ctypes.c_void_p),
+                ("valid_count", ctypes.c_void_p), ("capacity", ctypes.c_size_t)]
+
+
+def _declare_paths(L: ctypes.CDLL) -> None:
+    L.lt_trace_paths.restype = ctypes.c_int
+    L.lt_trace_paths.argtypes = [ctypes.c_void_p, ctypes.POINTER(c_rays_in), ctypes.c_void_p,
+                                 ctypes.c_size_t, ctypes.c_void_p, ctypes.c_int32,
+                                 ctypes.POINTER(c_paths_out), ctypes.c_size_t, ctypes.c_void_p]
+
+
+def trace_paths(lens: Lens, inp: Sequence, lam, lam_stride: int, path_ids, out, n: int,
+                stream=None) -> None:
+    """lt_trace_paths on device tensors.  out: a batch.PathsOut (or any object
+    with f = [x, y, dx, dy, dz, I], flags, ray_index, valid_count, capacity)."""
+    import numpy as np
+    ids = np.ascontiguousarray(path_ids, np.int32)
+    ri = rays_in(*inp)
+    po = c_paths_out(*[_ptr(t) for t in out.f], _ptr(out.flags), _ptr(out.ray_index),
+                     _ptr(out.valid_count), out.capacity)
+    check(lib().lt_trace_paths(lens.handle, ctypes.byref(ri), _ptr(lam), lam_stride,
+                               ids.ctypes.data, len(ids), ctypes.byref(po), n,
+                               _stream_handle(stream)))
+
+
 # ------------------------------------------------------------------ maps
 
 QUERY_TABLE = 0
@@ -476,6 +503,7 @@ _prev_declare = _declare
 def _declare(L: ctypes.CDLL) -> None:  # noqa: F811
     _prev_declare(L)
     _declare_mlp(L)
+    _declare_paths(L)
 
 
 def mlp_frame(path_id: int, rho: float, wmax: float, lam_lo: float = 380.0,
