@@ -387,6 +387,94 @@ lt_status lt_mlp_grad(const lt_mlp* mlp, int32_t net, const float* X, const floa
 lt_status lt_mlp_features(const lt_mlp* mlp, const lt_rays_in* in, const float* lambda_nm,
                           float* X, size_t n, lt_stream stream);
 
+/* ------------------------------------------------------------------ serving */
+
+/*
+ * A request server over one GPU: callers submit trace / map-query / learned-
+ * map requests from any thread and poll tickets.  A native worker thread
+ * launches them in arrival order on a few streams:
+ *   - continuous batching: the small TRACE requests waiting at the same time
+ *     (n <= fuse_max_rays, any lens and path) run as ONE fused launch whose
+ *     request table is a kernel parameter; per-ray results are identical to
+ *     lt_trace of the same request;
+ *   - memory admission: a request holds device bytes while in flight (host
+ *     staging 49 B/ray, map-query scratch 4 B/ray); a request waits while
+ *     the in-flight total would exceed mem_budget_bytes (one request alone is
+ *     always admitted if it fits the budget, else lt_submit fails LT_ENOMEM);
+ *   - deadlines: a request not launched within deadline_us of submission
+ *     completes with LT_ETIMEOUT without running;
+ *   - completion is signalled by a host function on the request's stream, so
+ *     latency (submission -> done) is measured on the host clock.
+ * Lenses, maps, learned maps and device buffers must stay alive until the
+ * ticket completes.  Context: the rendering pipeline of Sec. 4 (Listing 1)
+ * queries a path's map for every backward pixel sample and for every forward
+ * flare path; such streams of queries are what the server batches.
+ */
+typedef struct lt_server lt_server;
+
+typedef struct {
+    size_t mem_budget_bytes;     /* 0: 1 GiB */
+    int32_t n_streams;           /* 0: 4 */
+    int32_t fuse_max_requests;   /* requests per fused launch, 1..128 (0: 128) */
+    size_t fuse_max_rays;        /* TRACE requests up to this size are fused (0: 65536) */
+    int32_t inject_fail_every;   /* host-side fault injection for tests: every k-th launch
+                                    is not made and its requests fail with LT_ECUDA (0: off) */
+} lt_server_opts;
+
+enum {
+    LT_REQ_TRACE = 0,            /* lt_trace(lens, path_id) */
+    LT_REQ_QUERY = 1,            /* lt_query(map, query_mode) */
+    LT_REQ_MLP = 2               /* lt_mlp_query(mlp, precision) */
+};
+#define LT_REQ_HOST_BUFFERS 0x1  /* in, lambda_nm and out are HOST arrays; the server stages them */
+
+typedef struct {
+    int32_t kind;                /* LT_REQ_* */
+    int32_t flags;               /* LT_REQ_HOST_BUFFERS or 0 (device arrays, 16-byte aligned) */
+    const lt_lens* lens;         /* TRACE */
+    int32_t path_id;             /* TRACE */
+    const lt_map* map;           /* QUERY */
+    int32_t query_mode;          /* QUERY: LT_QUERY_TABLE or LT_QUERY_NO_MASK */
+    const lt_mlp* mlp;           /* MLP */
+    int32_t precision;           /* MLP: LT_MLP_* */
+    lt_rays_in in;
+    const float* lambda_nm;
+    lt_rays_out out;
+    size_t n;                    /* < 2^31 */
+    uint32_t deadline_us;        /* 0: none */
+} lt_request;
+
+typedef struct {
+    double queue_us;             /* submission -> launch */
+    double latency_us;           /* submission -> completion */
+    int32_t fused;               /* requests in the launch that served this one */
+} lt_ticket_info;
+
+typedef struct {
+    uint64_t submitted, completed, failed, timed_out;
+    uint64_t launches, fused_launches, fused_requests, rays;
+    size_t bytes_in_flight, peak_bytes_in_flight;
+} lt_server_stats;
+
+/* Errors: LT_EINVAL (bad option), LT_ECUDA (stream creation). */
+lt_status lt_server_create(const lt_server_opts* opts, lt_server** out);
+/* Stops the worker, waits for every launched request, drops unlaunched ones. */
+void lt_server_destroy(lt_server* server);
+/* Validates and enqueues; *ticket identifies the request.  n = 0 completes at
+ * once.  Errors: LT_EINVAL (NULL, unknown kind, bad path id, misaligned or
+ * NULL device array, n >= 2^31), LT_ENOMEM (request larger than the budget). */
+lt_status lt_submit(lt_server* server, const lt_request* req, uint64_t* ticket);
+/* Waits up to timeout_us (0: no wait) for a ticket.  LT_OK: done (the ticket
+ * is released); LT_ENOTREADY: not done yet (the ticket stays valid; poll
+ * again); the request's own error once it ended unsuccessfully (released):
+ * LT_ETIMEOUT (its deadline passed before launch), LT_ECUDA, LT_ENOMEM ...;
+ * LT_EINVAL: unknown or already released ticket. */
+lt_status lt_poll(lt_server* server, uint64_t ticket, uint32_t timeout_us);
+/* lt_poll that also reports the request's timing (info may be NULL). */
+lt_status lt_poll_info(lt_server* server, uint64_t ticket, uint32_t timeout_us,
+                       lt_ticket_info* info);
+lt_status lt_server_stats_get(lt_server* server, lt_server_stats* out);
+
 /* ------------------------------------------------------------------ profiling */
 
 /* Per-kernel device time.  When enabled, each kernel launch of the library

@@ -616,3 +616,130 @@ def unflat_params(flat, sizes):
         o += b
         out.append((W, bb))
     return out
+
+
+# ------------------------------------------------------------------ serving
+
+REQ_TRACE, REQ_QUERY, REQ_MLP = 0, 1, 2
+REQ_HOST_BUFFERS = 0x1
+OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, ENOTREADY = 0, -1, -2, -3, -4, -5, -6
+
+
+class c_server_opts(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_size_t), ("n_streams", ctypes.c_int32),
+                ("fuse_max_requests", ctypes.c_int32), ("fuse_max_rays", ctypes.c_size_t),
+                ("inject_fail_every", ctypes.c_int32)]
+
+
+class c_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("lens", ctypes.c_void_p), ("path_id", ctypes.c_int32),
+                ("map", ctypes.c_void_p), ("query_mode", ctypes.c_int32),
+                ("mlp", ctypes.c_void_p), ("precision", ctypes.c_int32),
+                ("inp", c_rays_in), ("lambda_nm", ctypes.c_void_p), ("out", c_rays_out),
+                ("n", ctypes.c_size_t), ("deadline_us", ctypes.c_uint32)]
+
+
+class c_ticket_info(ctypes.Structure):
+    _fields_ = [("queue_us", ctypes.c_double), ("latency_us", ctypes.c_double),
+                ("fused", ctypes.c_int32)]
+
+
+class c_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "completed", "failed", "timed_out",
+                                               "launches", "fused_launches", "fused_requests",
+                                               "rays")] + \
+               [("bytes_in_flight", ctypes.c_size_t), ("peak_bytes_in_flight", ctypes.c_size_t)]
+
+
+def _declare_server(L: ctypes.CDLL) -> None:
+    vp = ctypes.c_void_p
+    L.lt_server_create.restype = ctypes.c_int
+    L.lt_server_create.argtypes = [ctypes.POINTER(c_server_opts), ctypes.POINTER(vp)]
+    L.lt_server_destroy.restype = None
+    L.lt_server_destroy.argtypes = [vp]
+    L.lt_submit.restype = ctypes.c_int
+    L.lt_submit.argtypes = [vp, ctypes.POINTER(c_request), ctypes.POINTER(ctypes.c_uint64)]
+    L.lt_poll.restype = ctypes.c_int
+    L.lt_poll.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint32]
+    L.lt_poll_info.restype = ctypes.c_int
+    L.lt_poll_info.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(c_ticket_info)]
+    L.lt_server_stats_get.restype = ctypes.c_int
+    L.lt_server_stats_get.argtypes = [vp, ctypes.POINTER(c_server_stats)]
+
+
+_prev_declare_srv = _declare
+
+
+def _declare(L: ctypes.CDLL) -> None:  # noqa: F811
+    _prev_declare_srv(L)
+    _declare_server(L)
+
+
+class Server:
+    """lt_server: submit trace / query / learned-map requests, poll tickets."""
+
+    def __init__(self, mem_budget_bytes=0, n_streams=0, fuse_max_requests=0, fuse_max_rays=0,
+                 inject_fail_every=0):
+        o = c_server_opts(mem_budget_bytes, n_streams, fuse_max_requests, fuse_max_rays,
+                          inject_fail_every)
+        self.handle = ctypes.c_void_p()
+        check(lib().lt_server_create(ctypes.byref(o), ctypes.byref(self.handle)))
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().lt_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _submit(self, kind, inp, lam, out, n, lens=None, path_id=0, gmap=None, query_mode=0,
+                mlp=None, precision=0, deadline_us=0, host=False) -> int:
+        r = c_request()
+        r.kind = kind
+        r.flags = REQ_HOST_BUFFERS if host else 0
+        r.lens = lens.handle if lens is not None else None
+        r.path_id = path_id
+        r.map = gmap.handle if gmap is not None else None
+        r.query_mode = query_mode
+        r.mlp = mlp.handle if mlp is not None else None
+        r.precision = precision
+        r.inp = rays_in(*inp)
+        r.lambda_nm = _ptr(lam)
+        r.out = rays_out(*out)
+        r.n = n
+        r.deadline_us = deadline_us
+        t = ctypes.c_uint64()
+        check(lib().lt_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    def submit_trace(self, lens, inp, lam, path_id, out, n, **kw) -> int:
+        return self._submit(REQ_TRACE, inp, lam, out, n, lens=lens, path_id=path_id, **kw)
+
+    def submit_query(self, gmap, inp, lam, out, n, query_mode=QUERY_TABLE, **kw) -> int:
+        return self._submit(REQ_QUERY, inp, lam, out, n, gmap=gmap, query_mode=query_mode, **kw)
+
+    def submit_mlp(self, mlp, inp, lam, out, n, precision=MLP_F32, **kw) -> int:
+        return self._submit(REQ_MLP, inp, lam, out, n, mlp=mlp, precision=precision, **kw)
+
+    def poll(self, ticket: int, timeout_us: int = 0):
+        """(status, info dict or None): status is the raw lt_status."""
+        info = c_ticket_info()
+        st = lib().lt_poll_info(self.handle, ticket, timeout_us, ctypes.byref(info))
+        if st in (ENOTREADY, EINVAL):
+            return st, None
+        return st, {"queue_us": info.queue_us, "latency_us": info.latency_us, "fused": info.fused}
+
+    def wait(self, ticket: int, timeout_us: int = 60_000_000) -> dict:
+        st, info = self.poll(ticket, timeout_us)
+        check(st)
+        return info
+
+    def stats(self) -> dict:
+        s = c_server_stats()
+        check(lib().lt_server_stats_get(self.handle, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in c_server_stats._fields_}

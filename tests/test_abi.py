@@ -119,3 +119,32 @@ def test_trace_argument_errors_without_gpu():
     rc = lt.lib().lt_trace(L.handle, ctypes.byref(lt.c_rays_in()), None, 0,
                            ctypes.byref(lt.c_rays_out()), 0, None)
     assert rc == lt.LT_OK
+
+
+def test_trace_paths_argument_errors_without_gpu():
+    L = lt.Lens(w.singlet_lens())
+    ri = lt.c_rays_in()
+    po = lt.c_paths_out()
+    ids = (ctypes.c_int32 * 2)(0, 1)
+    f = lt.lib().lt_trace_paths
+    assert f(None, ctypes.byref(ri), None, 0, ids, 2, ctypes.byref(po), 0, None) == lt.LT_EINVAL
+    po.capacity = 4
+    po.valid_count = 16
+    assert f(L.handle, ctypes.byref(ri), None, 0, ids, 0, ctypes.byref(po), 0, None) == lt.LT_EINVAL
+    bad = (ctypes.c_int32 * 1)(2)          # the singlet has paths 0 and 1 only
+    assert f(L.handle, ctypes.byref(ri), None, 0, bad, 1, ctypes.byref(po), 0, None) == lt.LT_EINVAL
+    assert "path" in lt.last_error()
+    po.capacity = 0
+    assert f(L.handle, ctypes.byref(ri), None, 0, ids, 2, ctypes.byref(po), 0, None) == lt.LT_EINVAL
+
+
+def test_server_entry_points_without_gpu():
+    import torch
+    t = ctypes.c_uint64()
+    assert lt.lib().lt_submit(None, None, ctypes.byref(t)) == lt.LT_EINVAL
+    assert lt.lib().lt_poll(None, 1, 0) == lt.LT_EINVAL
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    h = ctypes.c_void_p()
+    rc = lt.lib().lt_server_create(None, ctypes.byref(h))
+    assert rc != lt.LT_OK and not h.value
