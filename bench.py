@@ -328,6 +328,14 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if world == 1 and not args.skip_extra:
+        extra = {}
+        for key, fn in (("singlet_65k", bench_singlet), ("precision_16M", bench_precision),
+                        ("flares_56x1M", bench_flares)):
+            extra[key] = fn(args, stream, flush, peaks)
+            torch.cuda.empty_cache()
+        extra["serving"] = bench_serving(args, peaks, seconds=args.serve_seconds)
+        line["configs"] = extra
     if rank == 0 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(presc, rays)
     if rank == 0:
@@ -335,6 +343,263 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- other configs
+
+MLP_REG_SIZES = [4, 32, 32, 32, 32, 32, 6]
+MLP_CLS_SIZES = [4, 32, 32, 1]
+MLP_MACS = sum(a * b for a, b in zip(MLP_REG_SIZES[:-1], MLP_REG_SIZES[1:])) + \
+    sum(a * b for a, b in zip(MLP_CLS_SIZES[:-1], MLP_CLS_SIZES[1:]))      # 4,416 + 1,184
+
+
+def xavier_flat(sizes, rng):
+    import numpy as np
+    from paper_2605_04017_gb300 import workloads as w
+    parts = []
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        parts += [w.xavier_uniform(a, b, rng).reshape(-1), np.zeros(b)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def pos_err(a_out, a_flags, b_out, b_flags, FLAG_VALID, FLAG_GRAZING=0x40):
+    """Exit-position distance (mm) over rays valid in both (grazing excluded)."""
+    import numpy as np
+    both = ((a_flags & FLAG_VALID) != 0) & ((b_flags & FLAG_VALID) != 0) & ((b_flags & FLAG_GRAZING) == 0)
+    e = np.hypot(a_out[both, 0].astype(np.float64) - b_out[both, 0], a_out[both, 1].astype(np.float64) - b_out[both, 1])
+    agree = float((((a_flags & FLAG_VALID) != 0) == ((b_flags & FLAG_VALID) != 0)).mean())
+    if not e.size:
+        return {"rms_mm": 0.0, "p99_mm": 0.0, "valid_agreement": agree}
+    return {"rms_mm": float(np.sqrt((e ** 2).mean())), "p99_mm": float(np.percentile(e, 99)),
+            "valid_agreement": round(agree, 6)}
+
+
+def time_kernel(step, name, args, flush, stream, n, lt):
+    """rays/s, mean and p99 step ms and the profiler's record of one entry point."""
+    import numpy as np
+    lt.profile_enable(True)
+    lt.profile_read(reset=True)
+    t = timed_steps(step, args.steps, args.warmup, flush, stream, lambda: lt.profile_read(reset=True))
+    prof = lt.profile_read(reset=True)
+    lt.profile_enable(False)
+    return {"rays_per_s": round(n * len(t) / (sum(t) * 1e-3), 1), "ms_per_step": round(statistics.mean(t), 4),
+            "p99_batch_ms": round(float(np.percentile(t, 99)), 4)}, prof
+
+
+def bench_singlet(args, stream, flush, peaks):
+    """The 2-surface singlet, 65,536 rays; its 32^4 x 8 map fitted on the same rays."""
+    import torch
+    from paper_2605_04017_gb300 import batch, lt, workloads as w
+    presc = w.singlet_lens()
+    lens = lt.Lens(presc)
+    rays = w.singlet_rays()
+    n = len(rays)
+    d = batch.DeviceRays(rays)
+    lo, hi = map_box(w.SINGLET_RHO)
+    gmap = lt.Map.build(lens, 0, RES, lo, hi, fit=d)
+    oq, ot = batch.DeviceOut(n), batch.DeviceOut(n)
+    q, _ = time_kernel(lambda: gmap.query(d.inp, d.lam, oq.out, n, lt.QUERY_TABLE, stream), "q", args, flush,
+                       stream, n, lt)
+    t, _ = time_kernel(lambda: lt.trace(lens, d.inp, d.lam, 0, ot.out, n, stream), "t", args, flush, stream, n, lt)
+    torch.cuda.synchronize()
+    qo, qf = oq.numpy()
+    to, tf = ot.numpy()
+    return {"workload": "2-surface singlet (R +-50 mm, t 5 mm, a 10 mm), 65,536 rays, map 32^4x8 fitted on them",
+            "query": q, "trace": t, "map_err_vs_fp32_trace": pos_err(qo, qf, to, tf, lt.FLAG_VALID)}
+
+
+def bench_precision(args, stream, flush, peaks):
+    """Config-1 lens, 16,777,216 rays: the learned map (classifier + regressor)
+    in FP32, BF16 and FP16 (tensor cores), the FP32 table map and the FP32
+    tracer on the same batch."""
+    import numpy as np
+    import torch
+    from paper_2605_04017_gb300 import batch, lt, workloads as w
+    presc = w.singlet_lens()
+    lens = lt.Lens(presc)
+    rho = w.SINGLET_RHO
+    rng = np.random.Generator(np.random.PCG64(w.SEED_BASE + 3))
+    fit = batch.DeviceRays(w.entrance_rays(1 << 21, w.SEED_BASE + 3 + 1000, rho))
+    t0 = time.perf_counter()
+    m = lt.Mlp.train(lens, lt.mlp_frame(0, rho, 0.2421), fit, xavier_flat(MLP_REG_SIZES, rng),
+                     xavier_flat(MLP_CLS_SIZES, rng), reg_steps=6000, reg_batch=8192, cls_steps=4000,
+                     cls_batch=8192, lr=1e-3, lr_decay=0.95, decay_every=500, seed=5)
+    train_s = time.perf_counter() - t0
+    lo, hi = map_box(rho)
+    gmap = lt.Map.build(lens, 0, RES, lo, hi, fit=fit)
+    del fit
+    rays = w.precision_rays()
+    n = len(rays)
+    d = batch.DeviceRays(rays)
+    del rays
+    o = batch.DeviceOut(n)
+    res, outs = {}, {}
+    runs = [("mlp_f32", lambda: m.query(d.inp, d.lam, o.out, n, lt.MLP_F32, stream), "mlp_query_f32_kernel"),
+            ("mlp_bf16", lambda: m.query(d.inp, d.lam, o.out, n, lt.MLP_BF16, stream), "mlp_query_bf16_kernel"),
+            ("mlp_f16", lambda: m.query(d.inp, d.lam, o.out, n, lt.MLP_F16, stream), "mlp_query_f16_kernel"),
+            ("table_f32", lambda: gmap.query(d.inp, d.lam, o.out, n, lt.QUERY_TABLE, stream), None),
+            ("trace_f32", lambda: lt.trace(lens, d.inp, d.lam, 0, o.out, n, stream), None)]
+    bf16_peak = None
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        bf16_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    for key, step, kname in runs:
+        r, prof = time_kernel(step, key, args, flush, stream, n, lt)
+        torch.cuda.synchronize()
+        outs[key] = o.numpy()
+        if kname and kname in prof:
+            launches, ms, _ = prof[kname]
+            avg_s = ms / launches * 1e-3
+            tflops = 2.0 * MLP_MACS * n / avg_s / 1e12
+            r["kernel"] = {"name": kname, "mlp_tflops": round(tflops, 2), "avg_launch_ms": round(ms / launches, 4),
+                           "hbm_gbs": round(49.0 * n / avg_s / 1e9, 1)}
+            if key != "mlp_f32" and bf16_peak:
+                peak = bf16_peak
+                r["kernel"]["tensor_frac"] = round(tflops / peak, 4)
+                r["kernel"]["tensor_peak"] = "%.1f TFLOP/s of measured (bf16 burst; fp16 taken equal)" % peak
+            r["kernel"]["hbm_frac"] = round(49.0 * n / avg_s / 1e9 / peaks["hbm_gbs"], 4)
+        res[key] = r
+    to, tf = outs["trace_f32"]
+    errs = {k: pos_err(outs[k][0], outs[k][1], to, tf, lt.FLAG_VALID) for k in outs if k != "trace_f32"}
+    f32o, f32f = outs["mlp_f32"]
+    for k in ("mlp_bf16", "mlp_f16"):
+        errs[k]["vs_mlp_f32"] = pos_err(outs[k][0], outs[k][1], f32o, f32f, lt.FLAG_VALID)
+    st = m.stats()
+    return {"workload": "singlet, 16,777,216 rays (seed +3); learned map = classifier 4-32-32-1 + "
+                        "regressor 4-(32x5)-6, trained on the GPU from 2,097,152 traced rays",
+            "train": {"s": round(train_s, 2), "reg_loss": st["reg_loss"], "cls_loss": st["cls_loss"],
+                      "steps": "reg 6000 + cls 4000, batch 8192, Adam lr 1e-3 x0.95/500"},
+            "rays_per_s": res, "pos_err_vs_fp32_trace": errs}
+
+
+def bench_flares(args, stream, flush, peaks):
+    """The 11-surface lens, main path + all 55 two-bounce ghosts, 1,048,576 rays
+    each with wavelengths redrawn per path, one lt_trace_paths launch."""
+    import numpy as np
+    import torch
+    from paper_2605_04017_gb300 import batch, lt, workloads as w
+    presc = w.eleven_surface_lens(lib_accept)
+    lens = lt.Lens(presc)
+    P = lens.n_paths
+    rays = w.flare_rays(presc)
+    n = len(rays)
+    d = batch.DeviceRays(rays)
+    lam = torch.from_numpy(np.concatenate([w.flare_wavelengths(p, n) for p in range(P)])).cuda()
+    po = batch.PathsOut(P, n)
+    ids = list(range(P))
+    r, prof = time_kernel(lambda: lt.trace_paths(lens, d.inp, lam, n, ids, po, n, stream), "paths", args, flush,
+                          stream, n * P, lt)
+    counts = po.counts()
+    launches, ms, work = prof["trace_paths_kernel"]
+    avg_s = ms / launches * 1e-3
+    useful = work / launches * FLOPS_PER_INTERACTION / avg_s / 1e12
+    peak = fp32_peak_tflops(peaks["sm_max_mhz"])
+    return {"workload": "11-surface lens, 56 paths (main + 55 ghosts) x 1,048,576 rays, lambda per path",
+            "rays_per_s": r["rays_per_s"], "ms_per_step": r["ms_per_step"], "p99_batch_ms": r["p99_batch_ms"],
+            "valid_rays_per_launch": int(counts.sum()),
+            "valid_rays_per_s": round(int(counts.sum()) / avg_s, 1),
+            "roofline": {"kernel": "trace_paths_kernel", "bound": "alu", "achieved": round(useful, 2),
+                         "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(useful / peak, 4),
+                         "interactions_per_launch": int(work / launches),
+                         "note": "useful FP32 flop: interactions actually executed x 89"}}
+
+
+def bench_serving(args, peaks, seconds=10.0, warm=1.0, rate=2000.0):
+    """8 seeded lenses (S ~ U{4..22}); Poisson arrivals; sizes log-uniform on
+    [1,024, 4,194,304]; lens uniform; main path (its resident table map) with
+    probability 0.5, else a uniform ghost (traced).  Latency = submission ->
+    completion on the host clock, requests submitted after the warm-up."""
+    import queue
+    import numpy as np
+    import torch
+    from paper_2605_04017_gb300 import batch, lt, workloads as w
+    pres = w.serving_lenses(lib_accept, 8)
+    lenses = [lt.Lens(p) for p in pres]
+    NMAX = 1 << 22
+    inputs, maps = [], []
+    for k, p in enumerate(pres):
+        rho = 1.2 * p.surfaces[0].aperture_r
+        lo, hi = map_box(rho)
+        fit = batch.DeviceRays(w.entrance_rays(1 << 21, w.SEED_BASE + 5 + 7 * k, rho))
+        maps.append(lt.Map.build(lenses[k], 0, RES, lo, hi, fit=fit))
+        del fit
+        inputs.append(batch.DeviceRays(w.entrance_rays(NMAX, w.SEED_BASE + 5 + 7 * k + 1, rho)))
+    SLOTS = 48
+    slots = [batch.DeviceOut(NMAX) for _ in range(SLOTS)]
+    free = queue.Queue()
+    for i in range(SLOTS):
+        free.put(i)
+    torch.cuda.synchronize()
+    rng = np.random.Generator(np.random.PCG64(w.SEED_BASE + 5))
+    total = seconds + warm
+    n_req = int(rate * total * 1.2) + 16
+    gaps = rng.exponential(1.0 / rate, n_req)
+    t_arr = np.cumsum(gaps)
+    n_req = int(np.searchsorted(t_arr, total))
+    t_arr = t_arr[:n_req]
+    sizes = np.exp(rng.uniform(np.log(1024), np.log(NMAX), n_req)).astype(np.int64)
+    which = rng.integers(0, len(pres), n_req)
+    main = rng.uniform(size=n_req) < 0.5
+    ghost = [int(rng.integers(1, lenses[k].n_paths)) for k in which]
+    srv = lt.Server(n_streams=4)
+    tickets = queue.Queue()
+    stalls = [0]
+
+    def submitter():
+        t0 = time.perf_counter()
+        for i in range(n_req):
+            while True:
+                dt = t0 + t_arr[i] - time.perf_counter()
+                if dt <= 0:
+                    break
+                time.sleep(dt if dt > 2e-4 else 0)
+            try:
+                slot = free.get_nowait()
+            except queue.Empty:
+                stalls[0] += 1
+                slot = free.get()
+            k, nn = int(which[i]), int(sizes[i])
+            d, o = inputs[k], slots[slot]
+            if main[i]:
+                t = srv.submit_query(maps[k], d.inp, d.lam, o.out, nn)
+            else:
+                t = srv.submit_trace(lenses[k], d.inp, d.lam, ghost[i], o.out, nn)
+            tickets.put((i, t, slot, time.perf_counter() - t0))
+        tickets.put(None)
+
+    lat, rays_done, first_t, last_t = [], 0, None, 0.0
+    th = threading.Thread(target=submitter)
+    wall0 = time.perf_counter()
+    th.start()
+    fails = 0
+    while True:
+        item = tickets.get()
+        if item is None:
+            break
+        i, t, slot, ts = item
+        st, info = srv.poll(t, 60_000_000)
+        free.put(slot)
+        if st != lt.OK:
+            fails += 1
+            continue
+        if t_arr[i] >= warm:
+            lat.append(info["latency_us"])
+            rays_done += int(sizes[i])
+    wall = time.perf_counter() - wall0
+    th.join()
+    stats = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    meas = seconds
+    return {"workload": "8 seeded lenses (S 4..22), Poisson %g req/s, sizes log-uniform [1024, 4194304], "
+                        "main path via resident 32^4x8 map else a uniform ghost traced; %g s after %g s warm-up"
+                        % (rate, seconds, warm),
+            "requests": int(len(lat)), "failed": fails, "offered_req_per_s": rate,
+            "achieved_req_per_s": round(n_req / wall, 1),
+            "p50_latency_ms": round(float(np.percentile(lat, 50)) / 1e3, 4) if lat.size else None,
+            "p99_latency_ms": round(float(np.percentile(lat, 99)) / 1e3, 4) if lat.size else None,
+            "rays_per_s": round(rays_done / meas, 1),
+            "fused_launches": int(stats["fused_launches"]), "fused_requests": int(stats["fused_requests"]),
+            "launches": int(stats["launches"]), "client_slot_stalls": stalls[0]}
 
 
 def oracle_map(presc):
@@ -399,6 +664,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-extra", action="store_true", help="headline workload only")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
