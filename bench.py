@@ -213,7 +213,7 @@ def run_ours(args):
     presc = w.eleven_surface_lens(lib_accept)
     lens = lt.Lens(presc)
     rho = w.eleven_rho(presc)
-    n = w.ELEVEN_N
+    n = args.rays or w.ELEVEN_N
     # each rank draws its own batch (weak scaling); rank 0 uses the standard seed
     rays = w.entrance_rays(n, w.SEED_BASE + 2 + 7919 * rank, rho)
     fit = batch.DeviceRays(w.eleven_fit_rays(presc))
@@ -272,16 +272,18 @@ def run_ours(args):
     interp = (~traced) & ((qflags & lt.FLAG_VALID) != 0)
     n_interp = int(interp.sum())
     peaks = load_peaks()
+    # algorithmic bytes of one query launch: every ray's 24 B in and 25 B out,
+    # plus the map's node table (6 floats per node) and cell classes once
     table_bytes = mstats["n_nodes"] * 24 + (mstats["n_cells"] + 15) // 16 * 4
-    q_bytes = n * 24 + (n - n_fb) * 25 + n_fb * 4 + table_bytes
+    q_bytes = n * 49 + table_bytes
     kernels = {
         "map_query_kernel": kernel_roofline("map_query_kernel", pq, peaks, units_bytes=q_bytes),
-        "map_fallback_kernel": kernel_roofline("map_fallback_kernel", pq, peaks,
-                                               flops_per_work=FLOPS_PER_INTERACTION),
         "trace_kernel": kernel_roofline("trace_kernel", pt, peaks,
                                         flops_per_work=FLOPS_PER_INTERACTION),
     }
-    dom = max(["map_query_kernel", "map_fallback_kernel"], key=lambda k: pq[k][1])
+    kernels["map_query_kernel"]["fallback_interactions_per_launch"] = int(
+        pq["map_query_kernel"][2] / pq["map_query_kernel"][0])
+    dom = "map_query_kernel"
     roof = dict(kernels[dom])
     tr = NCU_TRAFFIC.get(dom)
     roof["traffic"] = (tr["bytes_per_ray"] * n if tr and tr["hash"] == src_hash() else None)
@@ -421,14 +423,19 @@ def bench_precision(args, stream, flush, peaks):
     rng = np.random.Generator(np.random.PCG64(w.SEED_BASE + 3))
     fit = batch.DeviceRays(w.entrance_rays(1 << 21, w.SEED_BASE + 3 + 1000, rho))
     t0 = time.perf_counter()
-    m = lt.Mlp.train(lens, lt.mlp_frame(0, rho, 0.2421), fit, xavier_flat(MLP_REG_SIZES, rng),
-                     xavier_flat(MLP_CLS_SIZES, rng), reg_steps=6000, reg_batch=8192, cls_steps=4000,
-                     cls_batch=8192, lr=1e-3, lr_decay=0.95, decay_every=500, seed=5)
+    if args.untrained:
+        # random Xavier networks (profiling: no training launches before the query)
+        m = lt.Mlp.create(lens, lt.mlp_frame(0, rho, 0.2421), xavier_flat(MLP_REG_SIZES, rng),
+                          xavier_flat(MLP_CLS_SIZES, rng), np.zeros(6), np.ones(6))
+    else:
+        m = lt.Mlp.train(lens, lt.mlp_frame(0, rho, 0.2421), fit, xavier_flat(MLP_REG_SIZES, rng),
+                         xavier_flat(MLP_CLS_SIZES, rng), reg_steps=6000, reg_batch=8192, cls_steps=4000,
+                         cls_batch=8192, lr=1e-3, lr_decay=0.95, decay_every=500, seed=5)
     train_s = time.perf_counter() - t0
     lo, hi = map_box(rho)
     gmap = lt.Map.build(lens, 0, RES, lo, hi, fit=fit)
     del fit
-    rays = w.precision_rays()
+    rays = w.precision_rays(args.precision_rays or w.PRECISION_N)
     n = len(rays)
     d = batch.DeviceRays(rays)
     del rays
@@ -480,7 +487,7 @@ def bench_flares(args, stream, flush, peaks):
     presc = w.eleven_surface_lens(lib_accept)
     lens = lt.Lens(presc)
     P = lens.n_paths
-    rays = w.flare_rays(presc)
+    rays = w.flare_rays(presc, args.flare_rays or w.FLARE_N_PER_PATH)
     n = len(rays)
     d = batch.DeviceRays(rays)
     lam = torch.from_numpy(np.concatenate([w.flare_wavelengths(p, n) for p in range(P)])).cuda()
@@ -602,6 +609,25 @@ def bench_serving(args, peaks, seconds=10.0, warm=1.0, rate=2000.0):
             "launches": int(stats["launches"]), "client_slot_stalls": stalls[0]}
 
 
+def run_only(args):
+    """One of the other workloads alone (1 GPU): prints {"workload_key": ..., ...}."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    peaks = load_peaks()
+
+    def flush():
+        flush_buf.fill_(1)
+
+    fns = {"singlet": bench_singlet, "precision": bench_precision, "flares": bench_flares}
+    if args.only == "serving":
+        out = bench_serving(args, peaks, seconds=args.serve_seconds)
+    else:
+        out = fns[args.only](args, stream, flush, peaks)
+    print(json.dumps({"only": args.only, **out}), flush=True)
+
+
 def oracle_map(presc):
     import oracle
     from paper_2605_04017_gb300 import workloads as w
@@ -666,10 +692,19 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-extra", action="store_true", help="headline workload only")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--only", choices=["singlet", "precision", "flares", "serving"],
+                    help="run one of the other workloads alone and print its object")
+    ap.add_argument("--rays", type=int, default=0, help="headline batch size (default 4,194,304)")
+    ap.add_argument("--precision-rays", type=int, default=0)
+    ap.add_argument("--flare-rays", type=int, default=0, help="rays per flare path")
+    ap.add_argument("--untrained", action="store_true",
+                    help="precision workload with random networks (no training launches)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         run_reference(args)
+    elif args.only:
+        run_only(args)
     else:
         run_ours(args)
 

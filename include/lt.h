@@ -256,9 +256,10 @@ enum {
                                   zeros) and report it valid; outside the box: tracer */
 };
 
-/* Query the map for n rays (device arrays, as lt_trace).  Rays answered by
- * the tracer carry LT_FLAG_TRACED.  Temporary device memory for the fallback
- * list (4 bytes per ray) is taken stream-ordered from a library pool.
+/* Query the map for n rays (device arrays, as lt_trace): one kernel that
+ * classifies every ray, interpolates VALID cells, traces BOUNDARY cells and
+ * rays outside the box exactly (those carry LT_FLAG_TRACED), and writes all
+ * results.  It allocates nothing and needs no scratch memory.
  * Errors as lt_trace. */
 lt_status lt_query(const lt_map* map, const lt_rays_in* in, const float* lambda_nm,
                    const lt_rays_out* out, size_t n, int32_t mode, lt_stream stream);
@@ -266,23 +267,14 @@ lt_status lt_query(const lt_map* map, const lt_rays_in* in, const float* lambda_
 lt_status lt_query_host(const lt_map* map, const lt_rays_in* in, const float* lambda_nm,
                         const lt_rays_out* out, size_t n, int32_t mode);
 
-/* Map query that allocates nothing.  The paper has no counterpart: this is a
- * deployment aid.  Some callers cannot allocate GPU memory while they run --
- * a renderer or serving process that reserves the whole device at start-up
- * with its own allocator, or a loop where any cudaMalloc (and the implicit
- * synchronisation it can bring) is not allowed.  lt_query takes a small
- * fallback list from a stream-ordered pool; this variant instead uses one
- * fixed array compiled into the library: LT_NOALLOC_MAX_RAYS + 64 uint32
- * words (about 4 MiB), present on every GPU that loads the library and held
- * until the process exits.
- *   - Same arguments, results and errors as lt_query; n > LT_NOALLOC_MAX_RAYS
- *     is rejected with LT_EINVAL (split larger batches).
- *   - The first call on each device looks up the array's device address
- *     (once per device, with that device current); make that first call
- *     before any stream capture.
- *   - All calls share the one array: calls whose work overlaps on the GPU
- *     (other streams, other threads) race and must be serialised by the
- *     caller.  Each call clears the part that must start at zero. */
+/* Map query with a guaranteed allocation-free contract, for callers that
+ * cannot allocate GPU memory while they run (a renderer or serving process
+ * that reserves the whole device at start-up, or a loop where any cudaMalloc
+ * is not allowed).  The paper has no counterpart: this is a deployment aid.
+ * lt_query itself now allocates nothing either; this entry point keeps its
+ * contract stable: same arguments, results and errors as lt_query, and
+ * n > LT_NOALLOC_MAX_RAYS is rejected with LT_EINVAL (split larger
+ * batches).  Calls on different streams may overlap freely. */
 #define LT_NOALLOC_MAX_RAYS (1 << 20)
 lt_status lt_query_noalloc(const lt_map* map, const lt_rays_in* in, const float* lambda_nm,
                            const lt_rays_out* out, size_t n, int32_t mode, lt_stream stream);
@@ -398,7 +390,7 @@ lt_status lt_mlp_features(const lt_mlp* mlp, const lt_rays_in* in, const float* 
  *     request table is a kernel parameter; per-ray results are identical to
  *     lt_trace of the same request;
  *   - memory admission: a request holds device bytes while in flight (host
- *     staging 49 B/ray, map-query scratch 4 B/ray); a request waits while
+ *     staging 49 B/ray); a request waits while
  *     the in-flight total would exceed mem_budget_bytes (one request alone is
  *     always admitted if it fits the budget, else lt_submit fails LT_ENOMEM);
  *   - deadlines: a request not launched within deadline_us of submission

@@ -294,156 +294,216 @@ map_classify_kernel(const uint8_t* __restrict__ corner_bits, const uint32_t* __r
 
 // ------------------------------------------------------------------ query kernels
 
-// A ray of the block waiting for interpolation: its index, the node index of
-// its cell's first corner and its FP32 position inside the cell.
-struct __align__(16) InterpItem {
-    uint32_t r, base;
+// Cell of a ray for the query: as cell_of, plus the node index of the cell's
+// (0,0,0,0,0) corner, taken from the per-dimension cell indices.
+__device__ __forceinline__ bool cell_and_base(const MapDev& M, float x, float y, float dx, float dy,
+                                              float dz, float lam, uint32_t& cid, uint32_t& base,
+                                              float f[5])
+{
+    if (!(dz > 0.0f)) return false;
+    const float v[5] = {x, y, __fdiv_rn(dx, dz), __fdiv_rn(dy, dz), lam};
+    bool inside = true;
+    cid = 0;
+    base = 0;
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+        const float u = __fmul_rn(__fsub_rn(v[d], M.lo[d]), M.inv[d]);
+        inside &= (u >= 0.0f) & (u <= M.umax[d]);
+        int c = (int)floorf(u);
+        c = min(max(c, 0), M.res[d] - 2);
+        f[d] = u - (float)c;
+        cid += (uint32_t)c * M.cstride[d];
+        base += (uint32_t)c * M.stride[d];
+    }
+    return inside;
+}
+
+// A VALID-cell ray of the block waiting for its gather: its slot in the
+// block, the node index of its cell's first corner, its position in the cell.
+struct __align__(16) GatherItem {
+    uint32_t slot, base;
     float f[5];
     float pad;
 };
 
-__device__ __forceinline__ float4 shfl_xor4(float4 v, int m)
+// One gather's weighted sum: lane (q, part) weights its 16-byte pieces of the
+// lower (v0) and upper (v1) dimension-0 corner by the product of its corner's
+// factors; lanes differing in bit 4 swap halves of the four sums, bit 3
+// swaps quarters, bits 2 and 1 are summed as they are, leaving component c
+// in lanes whose bits 1-2 are clear.
+__device__ __forceinline__ void gather_sum(const GatherItem& e, float4 v0, float4 v1, bool c1, bool c2,
+                                           bool c3, bool upper, bool u4, bool u3, bool writer, int comp,
+                                           int lane, float (*ob)[kQBlock], uint8_t* of)
 {
     const unsigned full = 0xffffffffu;
-    v.x = __shfl_xor_sync(full, v.x, m);
-    v.y = __shfl_xor_sync(full, v.y, m);
-    v.z = __shfl_xor_sync(full, v.z, m);
-    v.w = __shfl_xor_sync(full, v.w, m);
-    return v;
+    const float w = ((c1 ? e.f[1] : 1.0f - e.f[1]) * (c2 ? e.f[2] : 1.0f - e.f[2])) *
+                    ((c3 ? e.f[3] : 1.0f - e.f[3]) * (upper ? e.f[4] : 1.0f - e.f[4]));
+    const float w1 = w * e.f[0], w0 = w * (1.0f - e.f[0]);
+    const float ax = fmaf(w1, v1.x, w0 * v0.x), ay = fmaf(w1, v1.y, w0 * v0.y);
+    const float az = fmaf(w1, v1.z, w0 * v0.z), aw = fmaf(w1, v1.w, w0 * v0.w);
+    float k0 = u4 ? az : ax, k1 = u4 ? aw : ay;
+    k0 += __shfl_xor_sync(full, u4 ? ax : az, 16);
+    k1 += __shfl_xor_sync(full, u4 ? ay : aw, 16);
+    float kk = u3 ? k1 : k0;
+    kk += __shfl_xor_sync(full, u3 ? k0 : k1, 8);
+    kk += __shfl_xor_sync(full, kk, 4);
+    kk += __shfl_xor_sync(full, kk, 2);
+    if (writer) ob[comp][e.slot] = kk;
+    if (lane == 0) of[e.slot] = LT_FLAG_VALID;
 }
 
-// Mask lookup for a block of 256 rays, then warp-cooperative interpolation.
-// INVALID cells are answered at once; rays the table cannot answer are
-// appended (warp-aggregated) to the fallback list, bit 31 marking "outside
-// the box"; VALID cells are queued in shared memory.  Each warp then takes
-// one queued ray at a time: lane l loads 16 bytes (part l & 3) of the corner
-// pair 8h + (l >> 2) in round h = 0, 1, so a warp instruction fetches eight
-// whole 64-byte pairs (one L1 wavefront each) instead of 32 scattered words;
-// shuffles pair the two lambda nodes and sum the 16 weighted corners.
-template <int MODE>
+// The fused map query: one block per 256 rays.
+//  1. Each thread classifies its ray.  INVALID cells are answered at once;
+//     VALID cells are queued for a gather; BOUNDARY cells and rays outside
+//     the lattice box are queued for the exact tracer.
+//  2. A warp whose index owns a 32-ray chunk of the trace queue traces it
+//     (one thread per ray); every warp then takes queued gathers one at a
+//     time from a shared counter.  A gather is warp-cooperative: lane
+//     (q, part) loads 16 bytes -- part 0/1: the two halves of the lower-
+//     lambda node record, 2/3: of the upper one -- of corner pair q
+//     (q = the corner bits of dimensions 1-3) for dimension-0 corner 0 and 1,
+//     so each warp load reads eight whole 64-byte pairs.  Each lane weights
+//     its own values (the lambda factor included), and a transposed butterfly
+//     (5 shuffles) leaves component c of the sum in lane 8c (x, y, dx, dy)
+//     or 8c + 1 (dz, I).
+//  3. The block writes its 256 results with coalesced stores; interpolated
+//     directions are renormalised there.
+// Tracing and gathering warps of the resident blocks overlap ALU work with
+// gather latency, and no fallback list leaves the block.
+template <int MODE, bool CAUCHY>
 __global__ void __launch_bounds__(kQBlock)
 map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out, uint32_t n,
-                 uint32_t* __restrict__ fb_list, uint32_t* __restrict__ fb_count)
+                 unsigned long long* work)
 {
-    __shared__ InterpItem q[kQBlock];
-    __shared__ uint32_t qn;
-    if (threadIdx.x == 0) qn = 0;
+    __shared__ GatherItem gq[kQBlock];
+    __shared__ uint32_t tq[kQBlock];
+    __shared__ float ob[6][kQBlock];
+    __shared__ uint8_t of[kQBlock];
+    __shared__ uint32_t ng, nt, next;
+    const unsigned full = 0xffffffffu;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) {
+        ng = 0;
+        nt = 0;
+        next = 0;
+    }
+    of[t] = 0;
     __syncthreads();
-    const uint32_t r = blockIdx.x * kQBlock + threadIdx.x;
-    bool need_fb = false, need_ip = false;
-    uint32_t tag = r, cid = 0;
+    const uint32_t r0 = blockIdx.x * kQBlock;
+    const uint32_t r = r0 + t;
+    bool ip = false, tr = false;
+    uint32_t tag = (uint32_t)t, base = 0;
     float f[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     if (r < n) {
         const float x = __ldg(in.x + r), y = __ldg(in.y + r), dx = __ldg(in.dx + r),
                     dy = __ldg(in.dy + r), dz = __ldg(in.dz + r), lam = __ldg(in.lam + r);
-        if (!cell_of(M, x, y, dx, dy, dz, lam, cid, f)) {
-            need_fb = true;
+        uint32_t cid = 0;
+        if (!cell_and_base(M, x, y, dx, dy, dz, lam, cid, base, f)) {
+            tr = true;
             tag |= kOutsideBit;
         } else {
             const uint32_t c = MODE == LT_QUERY_TABLE ? cell_class(M, cid) : (uint32_t)LT_CELL_VALID;
-            if (c == LT_CELL_VALID) {
-                need_ip = true;
-            } else if (c == LT_CELL_INVALID) {
-                const float z[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                store_out(out, r, z, 0u);
-            } else {
-                need_fb = true;
-            }
+            ip = c == LT_CELL_VALID;
+            tr = c != LT_CELL_VALID && c != LT_CELL_INVALID;
         }
     }
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    unsigned m = __ballot_sync(full, need_ip);
+    unsigned m = __ballot_sync(full, ip);
     if (m) {
         const int leader = __ffs(m) - 1;
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(&qn, (uint32_t)__popc(m));
-        base = __shfl_sync(full, base, leader);
-        if (need_ip) {
-            InterpItem e;
-            e.r = r;
-            e.base = cell_base(M, cid);
+        uint32_t b = 0;
+        if (lane == leader) b = atomicAdd(&ng, (uint32_t)__popc(m));
+        b = __shfl_sync(full, b, leader);
+        if (ip) {
+            GatherItem e;
+            e.slot = (uint32_t)t;
+            e.base = base;
 #pragma unroll
             for (int d = 0; d < 5; ++d) e.f[d] = f[d];
             e.pad = 0.0f;
-            q[base + __popc(m & lt_mask)] = e;
+            gq[b + __popc(m & lt_mask)] = e;
         }
     }
-    m = __ballot_sync(full, need_fb);
+    m = __ballot_sync(full, tr);
     if (m) {
         const int leader = __ffs(m) - 1;
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(fb_count, (uint32_t)__popc(m));
-        base = __shfl_sync(full, base, leader);
-        if (need_fb) fb_list[base + __popc(m & lt_mask)] = tag;
+        uint32_t b = 0;
+        if (lane == leader) b = atomicAdd(&nt, (uint32_t)__popc(m));
+        b = __shfl_sync(full, b, leader);
+        if (tr) tq[b + __popc(m & lt_mask)] = tag;
     }
     __syncthreads();
-    const uint32_t nq = qn;
-    const int part = lane & 3, p8 = lane >> 2;
-    for (uint32_t it = threadIdx.x >> 5; it < nq; it += kQBlock / 32) {
-        const InterpItem e = q[it];
-        const float fl = e.f[4];
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int p = 8 * h + p8;
-            const int b0 = (p >> 3) & 1, b1 = (p >> 2) & 1, b2 = (p >> 1) & 1, b3 = p & 1;
-            const uint32_t nd = e.base + b0 * M.stride[0] + b1 * M.stride[1] + b2 * M.stride[2] +
-                                b3 * M.stride[3];
-            // part 0: (x, y, dx, dy) of node m; 1: (dz, I, 0, 0) of m; 2, 3: the same of m + 1
-            const float4 v = __ldg(reinterpret_cast<const float4*>(M.node + (size_t)nd * kNodeFloats) + part);
-            const float4 u = shfl_xor4(v, 2);
-            const float w = ((b0 ? e.f[0] : 1.0f - e.f[0]) * (b1 ? e.f[1] : 1.0f - e.f[1])) *
-                            ((b2 ? e.f[2] : 1.0f - e.f[2]) * (b3 ? e.f[3] : 1.0f - e.f[3]));
-            // lanes with part 0 / 1 hold node m in v and node m + 1 in u
-            acc.x = fmaf(w, fmaf(fl, u.x - v.x, v.x), acc.x);
-            acc.y = fmaf(w, fmaf(fl, u.y - v.y, v.y), acc.y);
-            acc.z = fmaf(w, fmaf(fl, u.z - v.z, v.z), acc.z);
-            acc.w = fmaf(w, fmaf(fl, u.w - v.w, v.w), acc.w);
-        }
-        // sum the 8 pairs of each round over lanes with the same part
-        float4 t = shfl_xor4(acc, 4);
-        acc.x += t.x; acc.y += t.y; acc.z += t.z; acc.w += t.w;
-        t = shfl_xor4(acc, 8);
-        acc.x += t.x; acc.y += t.y; acc.z += t.z; acc.w += t.w;
-        t = shfl_xor4(acc, 16);
-        acc.x += t.x; acc.y += t.y; acc.z += t.z; acc.w += t.w;
-        const float dz = __shfl_sync(full, acc.x, 1);
-        const float I = __shfl_sync(full, acc.y, 1);
-        if (lane == 0) {
-            const float n2 = fmaf(acc.z, acc.z, fmaf(acc.w, acc.w, dz * dz));
-            float inv = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
-            inv = inv * fmaf(-0.5f * n2, inv * inv, 1.5f);
-            const float o[6] = {acc.x, acc.y, acc.z * inv, acc.w * inv, dz * inv, I};
-            store_out(out, e.r, o, LT_FLAG_VALID);
-        }
-    }
-}
+    const uint32_t ngq = ng, ntq = nt;
 
-// exact tracer over the fallback list (one thread per entry, grid-stride)
-template <bool CAUCHY>
-__global__ void __launch_bounds__(kQBlock)
-map_fallback_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out,
-                    const uint32_t* __restrict__ fb_list, const uint32_t* __restrict__ fb_count,
-                    unsigned long long* work)
-{
-    const uint32_t cnt = *fb_count;
-    unsigned done = 0;
-    for (uint32_t i = blockIdx.x * kQBlock + threadIdx.x; i < cnt; i += gridDim.x * kQBlock) {
-        const uint32_t tag = fb_list[i];
-        const uint32_t r = tag & ~kOutsideBit;
-        TraceOut o;
-        int nint;
-        uint32_t f = trace_ray<CAUCHY>(M.L, M.pi, M.pj, __ldg(in.x + r), __ldg(in.y + r),
-                                       __ldg(in.dx + r), __ldg(in.dy + r), __ldg(in.dz + r),
-                                       __ldg(in.lam + r), o, nint);
-        f |= LT_FLAG_TRACED | ((tag & kOutsideBit) ? LT_FLAG_OUTSIDE : 0u);
-        const float v[6] = {o.x, o.y, o.dx, o.dy, o.dz, o.I};
-        store_out(out, r, v, f);
-        done += (unsigned)nint;
+    // exact tracer for this warp's chunk of the trace queue
+    if ((uint32_t)warp * 32u < ntq) {
+        const uint32_t k = (uint32_t)warp * 32u + (uint32_t)lane;
+        int nint = 0;
+        if (k < ntq) {
+            const uint32_t e = tq[k];
+            const uint32_t s = e & 0xffffu;
+            const uint32_t rr = r0 + s;
+            TraceOut o;
+            uint32_t fl = trace_ray<CAUCHY>(M.L, M.pi, M.pj, __ldg(in.x + rr), __ldg(in.y + rr),
+                                            __ldg(in.dx + rr), __ldg(in.dy + rr), __ldg(in.dz + rr),
+                                            __ldg(in.lam + rr), o, nint);
+            fl |= LT_FLAG_TRACED | ((e & kOutsideBit) ? LT_FLAG_OUTSIDE : 0u);
+            ob[0][s] = o.x;
+            ob[1][s] = o.y;
+            ob[2][s] = o.dx;
+            ob[3][s] = o.dy;
+            ob[4][s] = o.dz;
+            ob[5][s] = o.I;
+            of[s] = (uint8_t)fl;
+        }
+        warp_add(work, (unsigned)nint);
     }
-    warp_add(work, done);
+
+    // warp-cooperative gathers
+    const int part = lane & 3, q = lane >> 2;
+    const bool c1 = (q >> 2) & 1, c2 = (q >> 1) & 1, c3 = q & 1, upper = (part & 2) != 0;
+    const uint32_t loff = (c1 ? M.stride[1] : 0u) + (c2 ? M.stride[2] : 0u) + (c3 ? M.stride[3] : 0u);
+    const uint32_t s0 = M.stride[0];
+    const float4* __restrict__ node4 = reinterpret_cast<const float4*>(M.node);
+    const bool u4 = (lane & 16) != 0, u3 = (lane & 8) != 0;
+    const bool writer = (lane & 6) == 0 && !((lane & 1) && u4);
+    const int comp = (lane & 1) ? 4 + (u3 ? 1 : 0) : (u4 ? 2 : 0) + (u3 ? 1 : 0);
+    // two queued rays per iteration: four loads in flight before any sum
+    while (true) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(&next, 2u);
+        it = __shfl_sync(full, it, 0);
+        if (it >= ngq) break;
+        const bool two = it + 1 < ngq;
+        const GatherItem ea = gq[it];
+        const GatherItem eb = gq[two ? it + 1 : it];
+        const uint32_t na = ea.base + loff, nb = eb.base + loff;
+        const float4 a0 = __ldg(node4 + (size_t)na * 2 + part);
+        const float4 a1 = __ldg(node4 + (size_t)(na + s0) * 2 + part);
+        const float4 b0 = __ldg(node4 + (size_t)nb * 2 + part);
+        const float4 b1 = __ldg(node4 + (size_t)(nb + s0) * 2 + part);
+        gather_sum(ea, a0, a1, c1, c2, c3, upper, u4, u3, writer, comp, lane, ob, of);
+        if (two) gather_sum(eb, b0, b1, c1, c2, c3, upper, u4, u3, writer, comp, lane, ob, of);
+    }
+    __syncthreads();
+
+    if (r < n) {
+        const uint32_t fl = of[t];
+        float o[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (fl & LT_FLAG_VALID) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) o[k] = ob[k][t];
+            if (!(fl & LT_FLAG_TRACED)) {
+                const float n2 = fmaf(o[2], o[2], fmaf(o[3], o[3], o[4] * o[4]));
+                float inv = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
+                inv = inv * fmaf(-0.5f * n2, inv * inv, 1.5f);
+                o[2] *= inv;
+                o[3] *= inv;
+                o[4] *= inv;
+            }
+        }
+        store_out(out, r, o, fl);
+    }
 }
 
 // ------------------------------------------------------------------ scratch pool
@@ -472,47 +532,20 @@ lt_status scratch_pool(cudaMemPool_t* pool)
 }
 
 lt_status launch_query(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
-                       int mode, uint32_t* fb_list, uint32_t* fb_count, cudaStream_t st)
+                       int mode, cudaStream_t st)
 {
-    LT_CUDA_TRY(cudaMemsetAsync(fb_count, 0, sizeof(uint32_t), st));
     const unsigned blocks = (n + kQBlock - 1) / kQBlock;
-    {
     ProfScope prof("map_query_kernel", st);
-    if (mode == LT_QUERY_TABLE)
-        map_query_kernel<LT_QUERY_TABLE><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, fb_list, fb_count);
-    else
-        map_query_kernel<LT_QUERY_NO_MASK><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, fb_list, fb_count);
-    }
-    LT_CUDA_TRY(cudaGetLastError());
-    {
-        // the list length is only known on the device: a grid of resident
-        // blocks walks it (at most one block per 256 rays of the batch)
-        ProfScope prof("map_fallback_kernel", st);
-        if (map->cauchy) {
-            const unsigned g = persistent_blocks((const void*)map_fallback_kernel<true>, kQBlock, n, 8);
-            map_fallback_kernel<true><<<g, kQBlock, 0, st>>>(map->dev, in, out, fb_list, fb_count, prof.work());
-        } else {
-            const unsigned g = persistent_blocks((const void*)map_fallback_kernel<false>, kQBlock, n, 8);
-            map_fallback_kernel<false><<<g, kQBlock, 0, st>>>(map->dev, in, out, fb_list, fb_count, prof.work());
-        }
+    const bool table = mode == LT_QUERY_TABLE;
+    if (map->cauchy) {
+        if (table) map_query_kernel<LT_QUERY_TABLE, true><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, prof.work());
+        else map_query_kernel<LT_QUERY_NO_MASK, true><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, prof.work());
+    } else {
+        if (table) map_query_kernel<LT_QUERY_TABLE, false><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, prof.work());
+        else map_query_kernel<LT_QUERY_NO_MASK, false><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, prof.work());
     }
     LT_CUDA_TRY(cudaGetLastError());
     return LT_OK;
-}
-
-// query with scratch from the stream-ordered pool
-lt_status query_pooled(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, size_t n,
-                       int mode, cudaStream_t st)
-{
-    cudaMemPool_t pool;
-    lt_status s = scratch_pool(&pool);
-    if (s != LT_OK) return s;
-    uint32_t* scratch = nullptr;
-    if (cudaMallocFromPoolAsync((void**)&scratch, (n + 1) * sizeof(uint32_t), pool, st) != cudaSuccess)
-        return fail(LT_ENOMEM, "lt_query: scratch allocation of %zu bytes failed", (n + 1) * 4);
-    s = launch_query(map, in, out, (uint32_t)n, mode, scratch + 1, scratch, st);
-    cudaFreeAsync(scratch, st);
-    return s;
 }
 
 }  // namespace lt
@@ -692,7 +725,7 @@ lt_status lt_query(const lt_map* m, const lt_rays_in* in, const float* lam, cons
     if (n >= (1ull << 31)) return fail(LT_EINVAL, "lt_query: n must be < 2^31");
     RaysInDev din{in->x, in->y, in->dx, in->dy, in->dz, lam};
     RaysOutDev dout{out->x, out->y, out->dx, out->dy, out->dz, out->I, out->flags};
-    return query_pooled(m, din, dout, n, mode, (cudaStream_t)stream);
+    return launch_query(m, din, dout, (uint32_t)n, mode, (cudaStream_t)stream);
 }
 
 lt_status lt_query_host(const lt_map* m, const lt_rays_in* in, const float* lam,
@@ -708,7 +741,7 @@ lt_status lt_query_host(const lt_map* m, const lt_rays_in* in, const float* lam,
     for (const void* p : ps)
         if (!p) return fail(LT_EINVAL, "lt_query_host: NULL ray array");
     return run_host_pipelined(in, lam, out, n, [&](const RaysInDev& a, const RaysOutDev& b, size_t k, cudaStream_t st) {
-        return query_pooled(m, a, b, k, mode, st);
+        return launch_query(m, a, b, (uint32_t)k, mode, st);
     });
 }
 
@@ -881,17 +914,6 @@ lt_status lt_map_load(const char* path, lt_map** out)
 
 // ---------------------------------------------------------------- allocation-free query
 
-// The fallback-list scratch of lt_query_noalloc: word 0 is the list length,
-// the list starts at word 64 (256-byte aligned).  In host code the name of
-// this array is only a stand-in; the device address comes from
-// cudaGetSymbolAddress, looked up once per device below.
-static __device__ __align__(256) uint32_t g_noalloc_scratch[LT_NOALLOC_MAX_RAYS + 64];
-
-namespace {
-std::mutex g_noalloc_mu;
-uint32_t* g_noalloc_addr[64] = {};
-}  // namespace
-
 extern "C" lt_status lt_query_noalloc(const lt_map* m, const lt_rays_in* in, const float* lam,
                                       const lt_rays_out* out, size_t n, int32_t mode,
                                       lt_stream stream)
@@ -905,23 +927,7 @@ extern "C" lt_status lt_query_noalloc(const lt_map* m, const lt_rays_in* in, con
                     n, LT_NOALLOC_MAX_RAYS);
     lt_status s = check_io(in, lam, out, n, "lt_query_noalloc");
     if (s != LT_OK || n == 0) return s;
-    int dev = 0;
-    LT_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return fail(LT_EINVAL, "lt_query_noalloc: device index %d out of range", dev);
-    uint32_t* scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_addr[dev]) {
-            void* p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess) return cuda_fail(e, "lt_query_noalloc: cudaGetSymbolAddress");
-            g_noalloc_addr[dev] = static_cast<uint32_t*>(p);
-        }
-        scratch = g_noalloc_addr[dev];
-    }
     RaysInDev din{in->x, in->y, in->dx, in->dy, in->dz, lam};
     RaysOutDev dout{out->x, out->y, out->dx, out->dy, out->dz, out->I, out->flags};
-    // launch_query clears the list length (word 0) on `stream` before the kernels
-    return launch_query(m, din, dout, (uint32_t)n, mode, scratch + 64, scratch,
-                        (cudaStream_t)stream);
+    return launch_query(m, din, dout, (uint32_t)n, mode, (cudaStream_t)stream);
 }

@@ -26,8 +26,8 @@ struct MapDev {
 };
 
 lt_status scratch_pool(cudaMemPool_t* pool);
-// Map query with its fallback scratch (n + 1 words) taken from the pool on `st`.
-lt_status query_pooled(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, size_t n,
+// The fused map query of n < 2^31 rays on `st` (no scratch memory).
+lt_status launch_query(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
                        int mode, cudaStream_t st);
 
 }  // namespace lt

@@ -167,7 +167,6 @@ static size_t request_bytes(const lt_request& r)
 {
     size_t b = 0;
     if (r.flags & LT_REQ_HOST_BUFFERS) b += 12 * round16(r.n * 4) + round16(r.n);
-    if (r.kind == LT_REQ_QUERY) b += (r.n + 1) * 4;
     return b;
 }
 
@@ -198,7 +197,7 @@ static lt_status launch_single(const lt_request& r, const RaysInDev& in, const R
         path_ij(r.lens->S, r.path_id, &pi, &pj);
         return launch_trace(r.lens, pi, pj, in, out, r.n, st);
     }
-    if (r.kind == LT_REQ_QUERY) return query_pooled(r.map, in, out, r.n, r.query_mode, st);
+    if (r.kind == LT_REQ_QUERY) return launch_query(r.map, in, out, (uint32_t)r.n, r.query_mode, st);
     lt_rays_in ri{in.x, in.y, in.dx, in.dy, in.dz};
     lt_rays_out ro{out.x, out.y, out.dx, out.dy, out.dz, out.I, out.flags};
     return lt_mlp_query(r.mlp, &ri, in.lam, &ro, r.n, r.precision, (lt_stream)st);

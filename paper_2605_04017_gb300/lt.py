@@ -429,8 +429,8 @@ NOALLOC_MAX_RAYS = 1 << 20
 
 def query_noalloc(gmap: "Map", inp: Sequence, lam, out: Sequence, n: int,
                   mode: int = QUERY_TABLE, stream=None) -> None:
-    """lt_query_noalloc: the map query for callers that cannot allocate GPU
-    memory; its scratch is a fixed array inside the library (n <= 2^20)."""
+    """lt_query_noalloc: the map query under an allocation-free contract
+    (n <= 2^20)."""
     L = lib()
     L.lt_query_noalloc.restype = ctypes.c_int
     L.lt_query_noalloc.argtypes = [ctypes.c_void_p, ctypes.POINTER(c_rays_in), ctypes.c_void_p,

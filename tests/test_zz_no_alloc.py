@@ -2,11 +2,10 @@
 
 Some callers of this library cannot allocate GPU memory while they run (a
 process that reserves the whole device with its own allocator at start-up,
-or a loop where cudaMalloc is not allowed).  lt_query_noalloc serves them:
-its scratch is a fixed array inside the library.  This checks, through the
-C ABI, that it answers exactly like lt_query on two calls in a row (the
-shared scratch keeps the previous call's contents, so the second call shows
-it is reset correctly), and that it refuses batches larger than its array.
+or a loop where cudaMalloc is not allowed).  lt_query_noalloc keeps that
+contract in the ABI (the fused query needs no scratch at all).  This checks,
+through the C ABI, that it answers exactly like lt_query on two calls in a
+row, and that it refuses batches larger than its documented limit.
 The file is named to run last: if it fails, every other test has run.
 """
 import math
