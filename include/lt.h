@@ -338,6 +338,7 @@ typedef struct {
     double reg_loss, cls_loss;      /* mean training loss of the last 100 steps */
     double t_mean[6], t_std[6];     /* target standardisation */
     double train_ms;
+    uint64_t tc_wait_timeouts;      /* tensor-core query waits that ran out (0 when healthy) */
 } lt_mlp_stats;
 
 enum {

@@ -15,6 +15,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -739,6 +740,12 @@ mlp_query_mma_kernel(const __grid_constant__ MlpDev D, RaysInDev in, RaysOutDev 
     }
 }
 
+}  // namespace lt
+
+#include "mlp_tc.cuh"
+
+namespace lt {
+
 // features only (for tests and callers that want the network inputs)
 __global__ void __launch_bounds__(256)
 mlp_features_kernel(MlpFrame F, RaysInDev in, float* __restrict__ X, uint32_t n)
@@ -767,6 +774,9 @@ struct lt_mlp {
     float* cls = nullptr;
     uint32_t* frag_bf16 = nullptr;
     uint32_t* frag_f16 = nullptr;
+    unsigned char* tc_bf16 = nullptr;   // tcgen05 weight images (BF16 / FP16 + FP32 biases)
+    unsigned char* tc_f16 = nullptr;
+    uint32_t* tc_err = nullptr;         // count of tensor-core waits that ran out
     bool frags_stale = true;
     lt_mlp_stats stats = {};
     ~lt_mlp()
@@ -775,6 +785,9 @@ struct lt_mlp {
         if (cls) cudaFree(cls);
         if (frag_bf16) cudaFree(frag_bf16);
         if (frag_f16) cudaFree(frag_f16);
+        if (tc_bf16) cudaFree(tc_bf16);
+        if (tc_f16) cudaFree(tc_f16);
+        if (tc_err) cudaFree(tc_err);
     }
 };
 
@@ -859,6 +872,60 @@ static lt_status build_frags(lt_mlp* m)
         return fail(LT_ENOMEM, "learned map: fragment table allocation");
     LT_CUDA_TRY(cudaMemcpy(m->frag_bf16, fb.data(), FL.total * 4, cudaMemcpyHostToDevice));
     LT_CUDA_TRY(cudaMemcpy(m->frag_f16, fh.data(), FL.total * 4, cudaMemcpyHostToDevice));
+    m->frags_stale = false;
+    return LT_OK;
+}
+
+// The tcgen05 weight images: every weight at its place in the canonical
+// K-major layout (tc_elem_offset), zero padding elsewhere, then the FP32
+// biases; one image in BF16 and one in FP16.
+static lt_status build_tc_image(lt_mlp* m)
+{
+    std::vector<float> reg(LT_MLP_REG_PARAMS), cls(LT_MLP_CLS_PARAMS);
+    LT_CUDA_TRY(cudaMemcpy(reg.data(), m->reg, reg.size() * 4, cudaMemcpyDeviceToHost));
+    LT_CUDA_TRY(cudaMemcpy(cls.data(), m->cls, cls.size() * 4, cudaMemcpyDeviceToHost));
+    std::vector<unsigned char> ib(kImgBytes, 0), ih(kImgBytes, 0);
+    auto put = [&](int base, int N, int row, int k, float v) {
+        const int off = base + tc_elem_offset(N, row, k);
+        const __nv_bfloat16 b = __float2bfloat16_rn(v);
+        const __half h = __float2half_rn(v);
+        std::memcpy(&ib[off], &b, 2);
+        std::memcpy(&ih[off], &h, 2);
+    };
+    using R = Net<true>;
+    using C = Net<false>;
+    for (int o = 0; o < 32; ++o)
+        for (int k = 0; k < 4; ++k) {
+            put(kImgB0, 64, o, k, reg[R::woff(0) + o * 4 + k]);
+            put(kImgB0, 64, 32 + o, k, cls[C::woff(0) + o * 4 + k]);
+        }
+    for (int l = 1; l <= 4; ++l)
+        for (int o = 0; o < 32; ++o)
+            for (int k = 0; k < 32; ++k) put(kImgR1 + (l - 1) * 2048, 32, o, k, reg[R::woff(l) + o * 32 + k]);
+    for (int o = 0; o < 6; ++o)
+        for (int k = 0; k < 32; ++k) put(kImgR5, 32, o, k, reg[R::woff(5) + o * 32 + k]);
+    for (int o = 0; o < 32; ++o)
+        for (int k = 0; k < 32; ++k) put(kImgC1, 32, o, k, cls[C::woff(1) + o * 32 + k]);
+    for (int k = 0; k < 32; ++k) put(kImgC2, 32, 0, k, cls[C::woff(2) + k]);
+    std::vector<float> bias(9 * 32, 0.0f);
+    for (int l = 0; l < 5; ++l)
+        for (int o = 0; o < 32; ++o) bias[kBiasReg + 32 * l + o] = reg[R::boff(l) + o];
+    for (int q = 0; q < 6; ++q) bias[kBiasRegOut + q] = reg[R::boff(5) + q];
+    for (int l = 0; l < 2; ++l)
+        for (int o = 0; o < 32; ++o) bias[kBiasCls + 32 * l + o] = cls[C::boff(l) + o];
+    bias[kBiasClsOut] = cls[C::boff(2)];
+    std::memcpy(&ib[kImgBias], bias.data(), bias.size() * 4);
+    std::memcpy(&ih[kImgBias], bias.data(), bias.size() * 4);
+    if (!m->tc_bf16 && cudaMalloc(&m->tc_bf16, kImgBytes) != cudaSuccess)
+        return fail(LT_ENOMEM, "learned map: weight image allocation");
+    if (!m->tc_f16 && cudaMalloc(&m->tc_f16, kImgBytes) != cudaSuccess)
+        return fail(LT_ENOMEM, "learned map: weight image allocation");
+    if (!m->tc_err) {
+        if (cudaMalloc(&m->tc_err, 4) != cudaSuccess) return fail(LT_ENOMEM, "learned map: error counter");
+        LT_CUDA_TRY(cudaMemset(m->tc_err, 0, 4));
+    }
+    LT_CUDA_TRY(cudaMemcpy(m->tc_bf16, ib.data(), kImgBytes, cudaMemcpyHostToDevice));
+    LT_CUDA_TRY(cudaMemcpy(m->tc_f16, ih.data(), kImgBytes, cudaMemcpyHostToDevice));
     m->frags_stale = false;
     return LT_OK;
 }
@@ -984,6 +1051,12 @@ lt_status lt_mlp_stats_get(const lt_mlp* m, lt_mlp_stats* out)
 {
     if (!m || !out) return fail(LT_EINVAL, "lt_mlp_stats_get: NULL argument");
     *out = m->stats;
+    out->tc_wait_timeouts = 0;
+    if (m->tc_err) {
+        uint32_t e = 0;
+        LT_CUDA_TRY(cudaMemcpy(&e, m->tc_err, 4, cudaMemcpyDeviceToHost));
+        out->tc_wait_timeouts = e;
+    }
     return LT_OK;
 }
 
@@ -1114,17 +1187,21 @@ lt_status lt_mlp_query(const lt_mlp* mc, const lt_rays_in* in, const float* lam,
         if (precision == LT_MLP_F32) mlp_query_f32_kernel<true><<<g, kMB, 0, st>>>(D, din, dout, nn);
         else mlp_query_f32_kernel<false><<<g, kMB, 0, st>>>(D, din, dout, nn);
     } else if (precision == LT_MLP_BF16 || precision == LT_MLP_F16) {
-        if (m->frags_stale && (s = build_frags(m)) != LT_OK) return s;
-        const FragLayout FL = frag_layout();
-        const size_t smem = (size_t)FL.total * 4 + (LT_MLP_REG_PARAMS + LT_MLP_CLS_PARAMS) * 4;
-        D.frag = precision == LT_MLP_BF16 ? m->frag_bf16 : m->frag_f16;
-        const void* k = precision == LT_MLP_BF16 ? (const void*)mlp_query_mma_kernel<true, true>
-                                                 : (const void*)mlp_query_mma_kernel<false, true>;
+        if (m->frags_stale && (s = build_tc_image(m)) != LT_OK) return s;
+        const bool bf = precision == LT_MLP_BF16;
+        // more than half of an SM's shared memory: one CTA (and one TMEM
+        // allocation of all 512 columns) per SM
+        const size_t smem = std::max(sizeof(TcShared) + 16, (size_t)116 * 1024);
+        const void* k = bf ? (const void*)mlp_query_tc_kernel<true> : (const void*)mlp_query_tc_kernel<false>;
         LT_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        const unsigned g = persistent_blocks(k, kTCBlock, nn, 32);
-        ProfScope prof(precision == LT_MLP_BF16 ? "mlp_query_bf16_kernel" : "mlp_query_f16_kernel", st);
-        if (precision == LT_MLP_BF16) mlp_query_mma_kernel<true, true><<<g, kTCBlock, smem, st>>>(D, din, dout, nn);
-        else mlp_query_mma_kernel<false, true><<<g, kTCBlock, smem, st>>>(D, din, dout, nn);
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const unsigned per_cta = 128 * kTcWG;
+        const unsigned g = std::min<unsigned>((unsigned)sms, (nn + per_cta - 1) / per_cta);
+        ProfScope prof(bf ? "mlp_query_bf16_kernel" : "mlp_query_f16_kernel", st);
+        if (bf) mlp_query_tc_kernel<true><<<g, kTcThreads, smem, st>>>(m->F, m->tc_bf16, din, dout, nn, m->tc_err);
+        else mlp_query_tc_kernel<false><<<g, kTcThreads, smem, st>>>(m->F, m->tc_f16, din, dout, nn, m->tc_err);
     } else {
         return fail(LT_EINVAL, "lt_mlp_query: unknown precision %d", precision);
     }

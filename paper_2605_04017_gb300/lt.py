@@ -471,7 +471,7 @@ class c_mlp_stats(ctypes.Structure):
     _fields_ = [("n_train", ctypes.c_uint64), ("n_valid", ctypes.c_uint64),
                 ("reg_loss", ctypes.c_double), ("cls_loss", ctypes.c_double),
                 ("t_mean", ctypes.c_double * 6), ("t_std", ctypes.c_double * 6),
-                ("train_ms", ctypes.c_double)]
+                ("train_ms", ctypes.c_double), ("tc_wait_timeouts", ctypes.c_uint64)]
 
 
 def _declare_mlp(L: ctypes.CDLL) -> None:
@@ -568,7 +568,7 @@ class Mlp:
         check(lib().lt_mlp_stats_get(self.handle, ctypes.byref(s)))
         return {"n_train": s.n_train, "n_valid": s.n_valid, "reg_loss": s.reg_loss,
                 "cls_loss": s.cls_loss, "t_mean": list(s.t_mean), "t_std": list(s.t_std),
-                "train_ms": s.train_ms}
+                "train_ms": s.train_ms, "tc_wait_timeouts": s.tc_wait_timeouts}
 
     def params(self):
         import numpy as np
