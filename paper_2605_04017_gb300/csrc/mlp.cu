@@ -9,9 +9,9 @@
 // Adam with lr * decay^(step / every) (Sec. 5.1); per-block gradient sums in
 // FP32, the sum over blocks in FP64.  Queries: FP32 SIMT with a rational tanh
 // (the paper approximates tanh by a rational function, Sec. 5.1; here the
-// 9/10 truncation of Lambert's continued fraction), or BF16 / FP16 tensor-core
-// MMA (mma.sync m16n8k16, FP32 accumulation) with activations kept in
-// registers between layers and tanh.approx on packed pairs.
+// 9/10 truncation of Lambert's continued fraction), or BF16 / FP16 on the
+// 5th-generation tensor cores (tcgen05.mma, FP32 accumulation in TMEM; see
+// mlp_tc.cuh) with tanh.approx on packed pairs.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -417,7 +417,6 @@ struct MlpDev {
     MlpFrame F;
     const float* reg;
     const float* cls;
-    const uint32_t* frag;     // tensor-core weight fragments (BF16 or FP16 per launch)
 };
 
 template <bool REG>
@@ -522,53 +521,6 @@ mlp_query_f32_kernel(const __grid_constant__ MlpDev D, RaysInDev in, RaysOutDev 
 
 // ------------------------------------------------------------------ tensor-core query
 
-// Fragment tables: for each layer l (regressor layers 0..5, then classifier
-// layers 0..2), for n-tile j and k-step ks, lane `ln` holds two 32-bit words
-// b0 = (W[8j+g][16ks+2t], W[8j+g][16ks+2t+1]) and b1 = (W[8j+g][16ks+8+2t],
-// W[8j+g][16ks+9+2t]) (g = ln/4, t = ln%4; zero outside the matrix), i.e. the
-// m16n8k16 B operand of act x W^T.  Biases stay FP32 in the parameter arrays.
-struct FragLayout {
-    int off[9];    // word offset of each layer
-    int nt[9];     // n-tiles
-    int ks[9];     // k-steps
-    int total;
-};
-
-__host__ __device__ inline FragLayout frag_layout()
-{
-    FragLayout f{};
-    int o = 0;
-    for (int l = 0; l < 9; ++l) {
-        const bool reg = l < 6;
-        const int ll = reg ? l : l - 6;
-        const int no = reg ? Net<true>::out(ll) : Net<false>::out(ll);
-        const int ni = reg ? Net<true>::in(ll) : Net<false>::in(ll);
-        f.nt[l] = (no + 7) / 8;
-        f.ks[l] = (ni + 15) / 16;
-        f.off[l] = o;
-        o += f.nt[l] * f.ks[l] * 32 * 2;
-    }
-    f.total = o;
-    return f;
-}
-
-template <bool BF16>
-__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1)
-{
-    if (BF16)
-        asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-            "{%8,%9}, {%0,%1,%2,%3};\n"
-            : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-    else
-        asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-            "{%8,%9}, {%0,%1,%2,%3};\n"
-            : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 template <bool BF16>
 __device__ __forceinline__ uint32_t pack2(float lo, float hi)
 {
@@ -592,154 +544,6 @@ __device__ __forceinline__ uint32_t tanh2(float lo, float hi)
         asm("tanh.approx.f16x2 %0, %1;\n" : "=r"(r) : "r"(u));
     return r;
 }
-
-// One network on two 16-ray M-tiles held by a warp.  ain: the first layer's
-// A operands (K = 16, inputs in columns 0..3).  Hidden activations stay in
-// registers: the C fragment of n-tiles (2ks, 2ks+1) after tanh is exactly the
-// A fragment of k-step ks of the next layer.  cout: last layer's C (n-tile 0).
-template <bool BF16, bool REG>
-__device__ __forceinline__ void mma_net(const uint32_t* __restrict__ frag, int lbase,
-                                        const float* __restrict__ P, const FragLayout& FL,
-                                        const uint32_t ain[2][4], float cout[2][4])
-{
-    using N = Net<REG>;
-    const int lane = threadIdx.x & 31, t = lane & 3;
-    uint32_t A[2][2][4];   // [m-tile][k-step][word]
-#pragma unroll
-    for (int m = 0; m < 2; ++m)
-#pragma unroll
-        for (int w = 0; w < 4; ++w) A[m][0][w] = ain[m][w];
-#pragma unroll
-    for (int l = 0; l < N::L; ++l) {
-        const int nt = l == N::L - 1 ? 1 : 4;
-        const int ks = l == 0 ? 1 : 2;
-        const uint32_t* fl = frag + FL.off[lbase + l];
-        const float* bl = P + N::boff(l);
-        float C[2][4][4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (j < nt) {
-                const int c0 = 8 * j + 2 * t;
-                const float b0 = c0 < N::out(l) ? bl[c0] : 0.0f;
-                const float b1 = c0 + 1 < N::out(l) ? bl[c0 + 1] : 0.0f;
-#pragma unroll
-                for (int m = 0; m < 2; ++m) {
-                    C[m][j][0] = b0; C[m][j][1] = b1; C[m][j][2] = b0; C[m][j][3] = b1;
-                }
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    if (k < ks) {
-                        const uint2 bw = *reinterpret_cast<const uint2*>(fl + ((j * ks + k) * 32 + lane) * 2);
-#pragma unroll
-                        for (int m = 0; m < 2; ++m) mma16816<BF16>(C[m][j], A[m][k], bw.x, bw.y);
-                    }
-                }
-            }
-        }
-        if (l < N::L - 1) {
-#pragma unroll
-            for (int m = 0; m < 2; ++m)
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    A[m][k][0] = tanh2<BF16>(C[m][2 * k][0], C[m][2 * k][1]);
-                    A[m][k][1] = tanh2<BF16>(C[m][2 * k][2], C[m][2 * k][3]);
-                    A[m][k][2] = tanh2<BF16>(C[m][2 * k + 1][0], C[m][2 * k + 1][1]);
-                    A[m][k][3] = tanh2<BF16>(C[m][2 * k + 1][2], C[m][2 * k + 1][3]);
-                }
-        } else {
-#pragma unroll
-            for (int m = 0; m < 2; ++m)
-#pragma unroll
-                for (int w = 0; w < 4; ++w) cout[m][w] = C[m][0][w];
-        }
-    }
-}
-
-constexpr int kTCBlock = 128;
-
-// Each warp handles 32 rays per iteration: lane l owns ray l (M-tile l / 16,
-// row l % 16); the two networks run on the warp's tensor cores.
-template <bool BF16, bool USE_CLS>
-__global__ void __launch_bounds__(kTCBlock)
-mlp_query_mma_kernel(const __grid_constant__ MlpDev D, RaysInDev in, RaysOutDev out, uint32_t n)
-{
-    const FragLayout FL = frag_layout();
-    extern __shared__ uint32_t sfrag[];
-    for (int i = threadIdx.x; i < FL.total; i += kTCBlock) sfrag[i] = D.frag[i];
-    float* sP = reinterpret_cast<float*>(sfrag + FL.total);
-    for (int i = threadIdx.x; i < Net<true>::NP; i += kTCBlock) sP[i] = D.reg[i];
-    for (int i = threadIdx.x; i < Net<false>::NP; i += kTCBlock) sP[Net<true>::NP + i] = D.cls[i];
-    __syncthreads();
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const uint32_t warp = (blockIdx.x * kTCBlock + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * kTCBlock) >> 5;
-    for (uint32_t base = warp * 32; base < n; base += nwarps * 32) {
-        const uint32_t r = base + lane;
-        const bool live = r < n;
-        float x = 0.f, y = 0.f, dx = 0.f, dy = 0.f, dz = 1.f, lam = 500.f;
-        if (live) {
-            x = __ldg(in.x + r); y = __ldg(in.y + r);
-            dx = __ldg(in.dx + r); dy = __ldg(in.dy + r); dz = __ldg(in.dz + r);
-            lam = __ldg(in.lam + r);
-        }
-        const bool ok = live && ray_ok(x, y, dx, dy, dz, lam);
-        float X[4] = {0.f, 0.f, 0.f, 0.f};
-        RedFrame rf = {1.f, 0.f, 1.f};
-        if (ok) mlp_features(D.F, x, y, dx, dy, dz, lam, X, rf);
-        // first-layer A operands: row g and g+8 of each M-tile, columns 2t, 2t+1
-        const uint32_t p01 = pack2<BF16>(X[0], X[1]), p23 = pack2<BF16>(X[2], X[3]);
-        uint32_t ain[2][4];
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-            const uint32_t s0a = __shfl_sync(full, p01, 16 * m + g);
-            const uint32_t s0b = __shfl_sync(full, p23, 16 * m + g);
-            const uint32_t s1a = __shfl_sync(full, p01, 16 * m + g + 8);
-            const uint32_t s1b = __shfl_sync(full, p23, 16 * m + g + 8);
-            ain[m][0] = t == 0 ? s0a : (t == 1 ? s0b : 0u);
-            ain[m][1] = t == 0 ? s1a : (t == 1 ? s1b : 0u);
-            ain[m][2] = 0u;
-            ain[m][3] = 0u;
-        }
-        float creg[2][4], ccls[2][4];
-        mma_net<BF16, true>(sfrag, 0, sP, FL, ain, creg);
-        if (USE_CLS) mma_net<BF16, false>(sfrag, 6, sP + Net<true>::NP, FL, ain, ccls);
-        // gather each ray's outputs from the fragment owners (rows g / g+8 of its M-tile)
-        const int mm = lane >> 4, rr = lane & 15, gg = rr & 7, half = rr >> 3;
-        float zr[6];
-#pragma unroll
-        for (int tt = 0; tt < 3; ++tt) {
-            const int src = 4 * gg + tt;
-            const float a0 = __shfl_sync(full, creg[0][0], src), a1 = __shfl_sync(full, creg[0][1], src);
-            const float a2 = __shfl_sync(full, creg[0][2], src), a3 = __shfl_sync(full, creg[0][3], src);
-            const float b0 = __shfl_sync(full, creg[1][0], src), b1 = __shfl_sync(full, creg[1][1], src);
-            const float b2 = __shfl_sync(full, creg[1][2], src), b3 = __shfl_sync(full, creg[1][3], src);
-            const float v0 = mm == 0 ? (half ? a2 : a0) : (half ? b2 : b0);
-            const float v1 = mm == 0 ? (half ? a3 : a1) : (half ? b3 : b1);
-            zr[2 * tt] = v0;
-            zr[2 * tt + 1] = v1;
-        }
-        bool valid = ok;
-        if (USE_CLS) {
-            const float l0 = __shfl_sync(full, ccls[0][0], 4 * gg), l2 = __shfl_sync(full, ccls[0][2], 4 * gg);
-            const float m0 = __shfl_sync(full, ccls[1][0], 4 * gg), m2 = __shfl_sync(full, ccls[1][2], 4 * gg);
-            const float logit = mm == 0 ? (half ? l2 : l0) : (half ? m2 : m0);
-            valid = valid && logit > 0.0f;
-        }
-        if (live) {
-            float o[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (valid) finish_ray(D.F, rf, zr, o);
-            __stcs(out.x + r, o[0]);
-            __stcs(out.y + r, o[1]);
-            __stcs(out.dx + r, o[2]);
-            __stcs(out.dy + r, o[3]);
-            __stcs(out.dz + r, o[4]);
-            __stcs(out.I + r, o[5]);
-            out.flags[r] = (uint8_t)(!ok ? LT_FLAG_BAD_INPUT : (valid ? LT_FLAG_VALID : 0u));
-        }
-    }
-}
-
 }  // namespace lt
 
 #include "mlp_tc.cuh"
@@ -772,19 +576,16 @@ struct lt_mlp {
     MlpFrame F = {};
     float* reg = nullptr;
     float* cls = nullptr;
-    uint32_t* frag_bf16 = nullptr;
-    uint32_t* frag_f16 = nullptr;
     unsigned char* tc_bf16 = nullptr;   // tcgen05 weight images (BF16 / FP16 + FP32 biases)
     unsigned char* tc_f16 = nullptr;
     uint32_t* tc_err = nullptr;         // count of tensor-core waits that ran out
-    bool frags_stale = true;
+    TcBias tc_bias = {};                // FP32 biases of the tensor-core query
+    bool frags_stale = true;            // tensor-core weight images out of date
     lt_mlp_stats stats = {};
     ~lt_mlp()
     {
         if (reg) cudaFree(reg);
         if (cls) cudaFree(cls);
-        if (frag_bf16) cudaFree(frag_bf16);
-        if (frag_f16) cudaFree(frag_f16);
         if (tc_bf16) cudaFree(tc_bf16);
         if (tc_f16) cudaFree(tc_f16);
         if (tc_err) cudaFree(tc_err);
@@ -834,48 +635,6 @@ static lt_mlp* new_mlp(const lt_lens* lens, const lt_mlp_frame* fr, int pi, int 
     return m;
 }
 
-// host-side fragment tables from the current FP32 parameters
-static lt_status build_frags(lt_mlp* m)
-{
-    const FragLayout FL = frag_layout();
-    std::vector<float> reg(LT_MLP_REG_PARAMS), cls(LT_MLP_CLS_PARAMS);
-    LT_CUDA_TRY(cudaMemcpy(reg.data(), m->reg, reg.size() * 4, cudaMemcpyDeviceToHost));
-    LT_CUDA_TRY(cudaMemcpy(cls.data(), m->cls, cls.size() * 4, cudaMemcpyDeviceToHost));
-    std::vector<uint32_t> fb(FL.total), fh(FL.total);
-    for (int l = 0; l < 9; ++l) {
-        const bool isreg = l < 6;
-        const int ll = isreg ? l : l - 6;
-        const int ni = isreg ? Net<true>::in(ll) : Net<false>::in(ll);
-        const int no = isreg ? Net<true>::out(ll) : Net<false>::out(ll);
-        const float* W = isreg ? reg.data() + Net<true>::woff(ll) : cls.data() + Net<false>::woff(ll);
-        auto w = [&](int o, int k) { return (o < no && k < ni) ? W[o * ni + k] : 0.0f; };
-        for (int j = 0; j < FL.nt[l]; ++j)
-            for (int ks = 0; ks < FL.ks[l]; ++ks)
-                for (int ln = 0; ln < 32; ++ln) {
-                    const int g = ln >> 2, t = ln & 3, o = 8 * j + g;
-                    const float v[4] = {w(o, 16 * ks + 2 * t), w(o, 16 * ks + 2 * t + 1),
-                                        w(o, 16 * ks + 8 + 2 * t), w(o, 16 * ks + 9 + 2 * t)};
-                    const size_t at = (size_t)FL.off[l] + ((size_t)(j * FL.ks[l] + ks) * 32 + ln) * 2;
-                    __nv_bfloat162 b0 = __floats2bfloat162_rn(v[0], v[1]);
-                    __nv_bfloat162 b1 = __floats2bfloat162_rn(v[2], v[3]);
-                    __half2 h0 = __floats2half2_rn(v[0], v[1]);
-                    __half2 h1 = __floats2half2_rn(v[2], v[3]);
-                    std::memcpy(&fb[at], &b0, 4);
-                    std::memcpy(&fb[at + 1], &b1, 4);
-                    std::memcpy(&fh[at], &h0, 4);
-                    std::memcpy(&fh[at + 1], &h1, 4);
-                }
-    }
-    if (!m->frag_bf16 && cudaMalloc(&m->frag_bf16, FL.total * 4) != cudaSuccess)
-        return fail(LT_ENOMEM, "learned map: fragment table allocation");
-    if (!m->frag_f16 && cudaMalloc(&m->frag_f16, FL.total * 4) != cudaSuccess)
-        return fail(LT_ENOMEM, "learned map: fragment table allocation");
-    LT_CUDA_TRY(cudaMemcpy(m->frag_bf16, fb.data(), FL.total * 4, cudaMemcpyHostToDevice));
-    LT_CUDA_TRY(cudaMemcpy(m->frag_f16, fh.data(), FL.total * 4, cudaMemcpyHostToDevice));
-    m->frags_stale = false;
-    return LT_OK;
-}
-
 // The tcgen05 weight images: every weight at its place in the canonical
 // K-major layout (tc_elem_offset), zero padding elsewhere, then the FP32
 // biases; one image in BF16 and one in FP16.
@@ -901,21 +660,18 @@ static lt_status build_tc_image(lt_mlp* m)
         }
     for (int l = 1; l <= 4; ++l)
         for (int o = 0; o < 32; ++o)
-            for (int k = 0; k < 32; ++k) put(kImgR1 + (l - 1) * 2048, 32, o, k, reg[R::woff(l) + o * 32 + k]);
+            for (int k = 0; k < 32; ++k) put(kImgR1 + (l - 1) * kLayerBytes, 32, o, k, reg[R::woff(l) + o * 32 + k]);
     for (int o = 0; o < 6; ++o)
         for (int k = 0; k < 32; ++k) put(kImgR5, 32, o, k, reg[R::woff(5) + o * 32 + k]);
     for (int o = 0; o < 32; ++o)
         for (int k = 0; k < 32; ++k) put(kImgC1, 32, o, k, cls[C::woff(1) + o * 32 + k]);
     for (int k = 0; k < 32; ++k) put(kImgC2, 32, 0, k, cls[C::woff(2) + k]);
-    std::vector<float> bias(9 * 32, 0.0f);
     for (int l = 0; l < 5; ++l)
-        for (int o = 0; o < 32; ++o) bias[kBiasReg + 32 * l + o] = reg[R::boff(l) + o];
-    for (int q = 0; q < 6; ++q) bias[kBiasRegOut + q] = reg[R::boff(5) + q];
+        for (int o = 0; o < 32; ++o) m->tc_bias.b[kBiasReg + 32 * l + o] = reg[R::boff(l) + o];
+    for (int q = 0; q < 6; ++q) m->tc_bias.b[kBiasRegOut + q] = reg[R::boff(5) + q];
     for (int l = 0; l < 2; ++l)
-        for (int o = 0; o < 32; ++o) bias[kBiasCls + 32 * l + o] = cls[C::boff(l) + o];
-    bias[kBiasClsOut] = cls[C::boff(2)];
-    std::memcpy(&ib[kImgBias], bias.data(), bias.size() * 4);
-    std::memcpy(&ih[kImgBias], bias.data(), bias.size() * 4);
+        for (int o = 0; o < 32; ++o) m->tc_bias.b[kBiasCls + 32 * l + o] = cls[C::boff(l) + o];
+    m->tc_bias.b[kBiasClsOut] = cls[C::boff(2)];
     if (!m->tc_bf16 && cudaMalloc(&m->tc_bf16, kImgBytes) != cudaSuccess)
         return fail(LT_ENOMEM, "learned map: weight image allocation");
     if (!m->tc_f16 && cudaMalloc(&m->tc_f16, kImgBytes) != cudaSuccess)
@@ -1179,7 +935,7 @@ lt_status lt_mlp_query(const lt_mlp* mc, const lt_rays_in* in, const float* lam,
     cudaStream_t st = (cudaStream_t)stream;
     RaysInDev din{in->x, in->y, in->dx, in->dy, in->dz, lam};
     RaysOutDev dout{out->x, out->y, out->dx, out->dy, out->dz, out->I, out->flags};
-    MlpDev D{m->F, m->reg, m->cls, nullptr};
+    MlpDev D{m->F, m->reg, m->cls};
     const uint32_t nn = (uint32_t)n;
     if (precision == LT_MLP_F32 || precision == LT_MLP_F32_NOCLS) {
         ProfScope prof("mlp_query_f32_kernel", st);
@@ -1200,8 +956,8 @@ lt_status lt_mlp_query(const lt_mlp* mc, const lt_rays_in* in, const float* lam,
         const unsigned per_cta = 128 * kTcWG;
         const unsigned g = std::min<unsigned>((unsigned)sms, (nn + per_cta - 1) / per_cta);
         ProfScope prof(bf ? "mlp_query_bf16_kernel" : "mlp_query_f16_kernel", st);
-        if (bf) mlp_query_tc_kernel<true><<<g, kTcThreads, smem, st>>>(m->F, m->tc_bf16, din, dout, nn, m->tc_err);
-        else mlp_query_tc_kernel<false><<<g, kTcThreads, smem, st>>>(m->F, m->tc_f16, din, dout, nn, m->tc_err);
+        if (bf) mlp_query_tc_kernel<true><<<g, kTcThreads, smem, st>>>(m->F, m->tc_bias, m->tc_bf16, din, dout, nn, m->tc_err);
+        else mlp_query_tc_kernel<false><<<g, kTcThreads, smem, st>>>(m->F, m->tc_bias, m->tc_f16, din, dout, nn, m->tc_err);
     } else {
         return fail(LT_EINVAL, "lt_mlp_query: unknown precision %d", precision);
     }
