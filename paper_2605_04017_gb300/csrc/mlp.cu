@@ -112,7 +112,7 @@ __device__ __forceinline__ float tanh_rational(float x)
     const float den = fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.527349309e-09f, 2.268113723e-06f),
                                                        4.815961472e-04f), 2.889576883e-02f),
                                     4.736842105e-01f), 1.0f);
-    return x * num * __frcp_rn(den);
+    return __fdividef(x * num, den);   // den >= 1: the fast division is within 2 ulp
 }
 
 // ------------------------------------------------------------------ training data
@@ -430,7 +430,7 @@ __device__ __forceinline__ void forward_f32(const float* __restrict__ W, const f
 #pragma unroll
     for (int l = 0; l < N::L; ++l) {
         const int ni = N::in(l), no = N::out(l);
-        const float* Wl = W + N::woff(l);
+        const float4* Wl = reinterpret_cast<const float4*>(W + N::woff(l));   // rows of ni / 4 float4
         const float* bl = W + N::boff(l);
         float t[32];
 #pragma unroll
@@ -438,8 +438,15 @@ __device__ __forceinline__ void forward_f32(const float* __restrict__ W, const f
             if (o < no) {
                 float s = bl[o];
 #pragma unroll
-                for (int k = 0; k < 32; ++k)
-                    if (k < ni) s = fmaf(Wl[o * ni + k], a[k], s);
+                for (int k4 = 0; k4 < 8; ++k4) {
+                    if (4 * k4 < ni) {
+                        const float4 w = Wl[o * (ni / 4) + k4];   // one shared-memory load, four FMAs
+                        s = fmaf(w.x, a[4 * k4], s);
+                        s = fmaf(w.y, a[4 * k4 + 1], s);
+                        s = fmaf(w.z, a[4 * k4 + 2], s);
+                        s = fmaf(w.w, a[4 * k4 + 3], s);
+                    }
+                }
                 t[o] = s;
             }
         }
@@ -481,9 +488,12 @@ template <bool USE_CLS>
 __global__ void __launch_bounds__(kMB)
 mlp_query_f32_kernel(const __grid_constant__ MlpDev D, RaysInDev in, RaysOutDev out, uint32_t n)
 {
-    __shared__ float W[Net<true>::NP + Net<false>::NP];
+    // the classifier starts on a 16-byte boundary so both networks' weight
+    // rows load as float4
+    constexpr int kClsAt = (Net<true>::NP + 3) & ~3;
+    __shared__ __align__(16) float W[kClsAt + Net<false>::NP];
     for (int i = threadIdx.x; i < Net<true>::NP; i += kMB) W[i] = D.reg[i];
-    for (int i = threadIdx.x; i < Net<false>::NP; i += kMB) W[Net<true>::NP + i] = D.cls[i];
+    for (int i = threadIdx.x; i < Net<false>::NP; i += kMB) W[kClsAt + i] = D.cls[i];
     __syncthreads();
     const uint32_t r = blockIdx.x * kMB + threadIdx.x;
     if (r >= n) return;
@@ -500,7 +510,7 @@ mlp_query_f32_kernel(const __grid_constant__ MlpDev D, RaysInDev in, RaysOutDev 
         bool valid = true;
         if (USE_CLS) {
             float logit[1];
-            forward_f32<false>(W + Net<true>::NP, X, logit);
+            forward_f32<false>(W + kClsAt, X, logit);
             valid = logit[0] > 0.0f;
         }
         if (valid) {
