@@ -149,10 +149,16 @@ typedef struct {
     uint8_t* flags;              /* LT_FLAG_* */
 } lt_rays_out;
 
-/* Brute-force FP32 trace of n rays along one path (Sec. 3, Eq. 6-7):
- * one GPU thread per ray.  in/out/lambda_nm: device arrays of n entries.
+/* Brute-force FP32 trace of n rays along one path (Sec. 3, Eq. 6-7).
+ * in/out/lambda_nm: device arrays of n entries.  Paths of more than 4
+ * interactions run as two kernels per wave of at most 2^24 rays: one thread
+ * per ray through the first two interactions (where most rays of a lens
+ * die), then the survivors, queued, in dense warps to the end; the queue
+ * (54 B per ray of the wave) is taken stream-ordered from the library's
+ * memory pool.  Shorter paths run as one kernel whose blocks compact their
+ * surviving rays in shared memory.
  * Errors: LT_EINVAL (NULL pointer with n > 0, misaligned array, bad path id),
- * LT_ECUDA (launch failed).  n = 0 is a no-op. */
+ * LT_ENOMEM (queue allocation), LT_ECUDA (launch failed).  n = 0 is a no-op. */
 lt_status lt_trace(const lt_lens* lens, const lt_rays_in* in, const float* lambda_nm,
                    int32_t path_id, const lt_rays_out* out, size_t n, lt_stream stream);
 
@@ -182,9 +188,13 @@ typedef struct {
  * true count even when it exceeds capacity, in which case only `capacity`
  * of them (which ones is unspecified) are written -- compare the count with
  * capacity after the stream synchronises.  Per-ray results are identical to
- * lt_trace of the same ray, path and wavelength.
+ * lt_trace of the same ray, path and wavelength.  The paths run in waves of
+ * at most 2^24 (path, ray) pairs, each as two kernels: every ray through its
+ * first two interactions, then the queued survivors to the end; the queue
+ * (54 B per pair of a wave) comes stream-ordered from the library's pool.
  * Errors: LT_EINVAL (NULL pointer, misaligned array, n_paths < 1 or > 1024,
- * bad path id, capacity 0, n >= 2^32), LT_ECUDA.  n = 0 zeroes the counters. */
+ * bad path id, capacity 0, n >= 2^32), LT_ENOMEM (queue allocation),
+ * LT_ECUDA.  n = 0 zeroes the counters. */
 lt_status lt_trace_paths(const lt_lens* lens, const lt_rays_in* in, const float* lambda_nm,
                          size_t lambda_stride, const int32_t* path_ids, int32_t n_paths,
                          const lt_paths_out* out, size_t n, lt_stream stream);
@@ -391,7 +401,9 @@ lt_status lt_mlp_features(const lt_mlp* mlp, const lt_rays_in* in, const float* 
  *     request table is a kernel parameter; per-ray results are identical to
  *     lt_trace of the same request;
  *   - memory admission: a request holds device bytes while in flight (host
- *     staging 49 B/ray); a request waits while
+ *     staging 49 B/ray; a trace launched on its own also holds the tracer's
+ *     queue of surviving rays, 54 B/ray of a wave of at most 2^24 rays); a
+ *     request waits while
  *     the in-flight total would exceed mem_budget_bytes (one request alone is
  *     always admitted if it fits the budget, else lt_submit fails LT_ENOMEM);
  *   - deadlines: a request not launched within deadline_us of submission

@@ -25,7 +25,6 @@ struct MapDev {
     const uint32_t* cls;    // 2 bits per cell
 };
 
-lt_status scratch_pool(cudaMemPool_t* pool);
 // The fused map query of n < 2^31 rays on `st` (no scratch memory).
 lt_status launch_query(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
                        int mode, cudaStream_t st);

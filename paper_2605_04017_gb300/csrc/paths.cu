@@ -2,12 +2,12 @@
 // where the same entrance rays follow the main path and every two-bounce
 // ghost (i, j), each path with its own wavelength draw.
 //
-// Grid: blockIdx.y = path, blockIdx.x = tile of 256 rays.  Ghost rays die at
-// very different depths, so the hardware block scheduler (which hands a free
-// SM slot the next tile as soon as one retires) balances the load; a
-// persistent loop would only re-implement it.  Valid rays are compacted per
-// warp: a ballot, one atomic on the path's counter by the first valid lane,
-// and rank-ordered writes into the path's segment.
+// A wavefront per wave of paths: the front kernel (grid: tile of 256 rays x
+// path) takes every ray through its first interactions, where most rays of a
+// lens die; the survivors of all the wave's paths are queued and a
+// persistent rest kernel traces them to the end in dense warps.  Valid rays
+// are compacted into their path's segment: lanes grouped by path, one atomic
+// on the path's counter per group, rank-ordered writes.
 #include "profile.h"
 #include "rays.cuh"
 #include "tracer.cuh"
@@ -16,6 +16,7 @@ namespace lt {
 
 constexpr int kPathsBlock = 256;
 constexpr int kMaxPaths = 1024;
+constexpr size_t kWavePairs = (size_t)1 << 24;   // (path, ray) pairs per front/rest pair
 
 struct PathTable {
     int8_t ij[2 * kMaxPaths];   // (i, j) of each path; (0, 0) is the main path
@@ -30,45 +31,102 @@ struct PathsOutDev {
     size_t capacity;
 };
 
-template <bool CAUCHY>
-__global__ void __launch_bounds__(kPathsBlock)
-trace_paths_kernel(const __grid_constant__ LensDev L, const __grid_constant__ PathTable P,
-                   RaysInDev in, size_t lam_stride, PathsOutDev out, uint32_t n,
-                   unsigned long long* work)
+// Append a finished valid ray to its path's segment.  Lanes of a warp may
+// hold different paths: lanes of one path are grouped, and each group's
+// first lane takes one atomic on the path's counter.
+__device__ __forceinline__ void paths_append(const PathsOutDev& out, bool v, int p, uint32_t r,
+                                             const RayState& st)
 {
     const unsigned full = 0xffffffffu;
-    const int p = blockIdx.y;
-    const uint32_t r = blockIdx.x * kPathsBlock + threadIdx.x;
-    const int pi = P.ij[2 * p], pj = P.ij[2 * p + 1];
-    int nint = 0;
-    TraceOut o;
-    uint32_t f = 0;
-    if (r < n)
-        f = trace_ray<CAUCHY>(L, pi, pj, __ldg(in.x + r), __ldg(in.y + r), __ldg(in.dx + r),
-                              __ldg(in.dy + r), __ldg(in.dz + r),
-                              __ldg(in.lam + (size_t)p * lam_stride + r), o, nint);
-    const bool v = (r < n) && (f & LT_FLAG_VALID);
-    const unsigned m = __ballot_sync(full, v);
-    if (m) {
-        const int lane = threadIdx.x & 31;
-        const int leader = __ffs(m) - 1;
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(out.count + p, (uint32_t)__popc(m));
-        base = __shfl_sync(full, base, leader);
-        if (v) {
-            const uint32_t k = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
-            if (k < out.capacity) {
-                const size_t e = (size_t)p * out.capacity + k;
-                __stcs(out.x + e, o.x);
-                __stcs(out.y + e, o.y);
-                __stcs(out.dx + e, o.dx);
-                __stcs(out.dy + e, o.dy);
-                __stcs(out.dz + e, o.dz);
-                __stcs(out.I + e, o.I);
-                __stcs(out.ray_index + e, r);
-                out.flags[e] = (uint8_t)f;
-            }
+    const unsigned act = __ballot_sync(full, v);
+    if (!act) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned grp = __match_any_sync(full, v ? p : -1);
+    const int leader = __ffs(grp) - 1;
+    uint32_t base = 0;
+    if (v && lane == leader) base = atomicAdd(out.count + p, (uint32_t)__popc(grp));
+    base = __shfl_sync(full, base, leader);
+    if (v) {
+        const uint32_t k = base + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+        if (k < out.capacity) {
+            const size_t e = (size_t)p * out.capacity + k;
+            __stcs(out.x + e, st.x);
+            __stcs(out.y + e, st.y);
+            __stcs(out.dx + e, st.dx);
+            __stcs(out.dy + e, st.dy);
+            __stcs(out.dz + e, st.dz);
+            __stcs(out.I + e, st.I);
+            __stcs(out.ray_index + e, r);
+            out.flags[e] = (uint8_t)st.flags;
         }
+    }
+}
+
+// Front of the wavefront: block (tile, path p0 + blockIdx.y), one thread per
+// ray through the first kFront interactions; survivors are queued with
+// their path.
+template <bool CAUCHY>
+__global__ void __launch_bounds__(kPathsBlock)
+paths_front_kernel(const __grid_constant__ LensDev L, const __grid_constant__ PathTable P, int p0,
+                   RaysInDev in, size_t lam_stride, PathsOutDev out, uint32_t n, RayQueue Q,
+                   unsigned long long* work)
+{
+    const int p = p0 + (int)blockIdx.y;
+    const int pi = P.ij[2 * p], pj = P.ij[2 * p + 1];
+    const uint32_t r = blockIdx.x * kPathsBlock + threadIdx.x;
+    const int K = path_length(L.S, pi, pj);
+    RayState st;
+    bool live = false, valid = false;
+    int nint = 0;
+    if (r < n) {
+        live = trace_init(__ldg(in.x + r), __ldg(in.y + r), __ldg(in.dx + r), __ldg(in.dy + r),
+                          __ldg(in.dz + r), __ldg(in.lam + (size_t)p * lam_stride + r), st);
+        int res = live ? STEP_GO : STEP_DEAD;
+        for (int i = 0; i < kFront && res == STEP_GO; ++i) res = trace_step<CAUCHY>(L, pi, pj, K, st);
+        if (res != STEP_GO) {
+            if (live) nint = st.k + (res == STEP_DONE ? 1 : 0);
+            valid = res == STEP_DONE;
+            live = false;
+        }
+    }
+    paths_append(out, valid, p, r, st);
+    queue_push(Q, live, st, r, (uint16_t)p);
+    warp_add(work, (unsigned)nint);
+}
+
+// Rest of the wavefront: a persistent grid traces the queue to the end.
+template <bool CAUCHY>
+__global__ void __launch_bounds__(kPathsBlock)
+paths_rest_kernel(const __grid_constant__ LensDev L, const __grid_constant__ PathTable P, RayQueue Q,
+                  PathsOutDev out, unsigned long long* work)
+{
+    const uint32_t cnt = *Q.count;
+    int nint = 0;
+    const uint32_t stride = gridDim.x * kPathsBlock;
+    // every lane of a warp takes the same number of iterations (the append
+    // is warp-collective), idle lanes past the end included
+    const uint32_t rounds = (cnt + stride - 1) / stride;
+    for (uint32_t q = 0; q < rounds; ++q) {
+        const uint32_t i = q * stride + blockIdx.x * kPathsBlock + threadIdx.x;
+        RayState st;
+        bool valid = false;
+        int p = 0;
+        uint32_t r = 0;
+        if (i < cnt) {
+            queue_load(Q, i, st);
+            p = Q.path[i];
+            r = Q.ray[i];
+            const int pi = P.ij[2 * p], pj = P.ij[2 * p + 1];
+            const int K = path_length(L.S, pi, pj);
+            int res;
+#pragma unroll 1
+            do {
+                res = trace_step<CAUCHY>(L, pi, pj, K, st);
+            } while (res == STEP_GO);
+            nint += st.k + (res == STEP_DONE ? 1 : 0);
+            valid = res == STEP_DONE;
+        }
+        paths_append(out, valid, p, r, st);
     }
     warp_add(work, (unsigned)nint);
 }
@@ -109,14 +167,44 @@ extern "C" lt_status lt_trace_paths(const lt_lens* L, const lt_rays_in* in, cons
     PathsOutDev dout{out->x, out->y, out->dx, out->dy, out->dz, out->I, out->flags,
                      out->ray_index, out->valid_count, out->capacity};
     const uint32_t nn = (uint32_t)n;
-    const dim3 grid((unsigned)((n + kPathsBlock - 1) / kPathsBlock), (unsigned)n_paths);
+    const bool cauchy = lens_all_cauchy(L->dev);
+    // waves of whole paths, at most 2^24 (path, ray) pairs (one path at least)
+    const int per_wave = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_paths, kWavePairs / n));
+    const size_t cap = (((size_t)per_wave * n) + 63) & ~(size_t)63;
+    cudaMemPool_t pool;
+    lt_status s = scratch_pool(&pool);
+    if (s != LT_OK) return s;
+    char* buf = nullptr;
+    if (cudaMallocFromPoolAsync((void**)&buf, cap * kQueueBytesPerRay + 256, pool, st) != cudaSuccess)
+        return fail(LT_ENOMEM, "lt_trace_paths: ray queue allocation of %zu bytes failed",
+                    cap * kQueueBytesPerRay + 256);
+    RayQueue Q;
+    float** fq[10] = {&Q.x, &Q.y, &Q.z, &Q.dx, &Q.dy, &Q.dz, &Q.I, &Q.n, &Q.il2, &Q.l2};
+    for (int q = 0; q < 10; ++q) *fq[q] = reinterpret_cast<float*>(buf + (size_t)q * cap * 4);
+    Q.k = reinterpret_cast<int*>(buf + 10 * cap * 4);
+    Q.flags = reinterpret_cast<uint32_t*>(buf + 11 * cap * 4);
+    Q.ray = reinterpret_cast<uint32_t*>(buf + 12 * cap * 4);
+    Q.path = reinterpret_cast<uint16_t*>(buf + 13 * cap * 4);
+    Q.count = reinterpret_cast<uint32_t*>(buf + 13 * cap * 4 + cap * 2 + 64);
+    const void* rest = cauchy ? (const void*)paths_rest_kernel<true> : (const void*)paths_rest_kernel<false>;
     ProfScope prof("trace_paths_kernel", st);
-    if (lens_all_cauchy(L->dev))
-        trace_paths_kernel<true><<<grid, kPathsBlock, 0, st>>>(L->dev, P, din, lam_stride, dout, nn,
-                                                               prof.work());
-    else
-        trace_paths_kernel<false><<<grid, kPathsBlock, 0, st>>>(L->dev, P, din, lam_stride, dout, nn,
-                                                                prof.work());
-    LT_CUDA_TRY(cudaGetLastError());
-    return LT_OK;
+    for (int p0 = 0; p0 < n_paths && s == LT_OK; p0 += per_wave) {
+        const int np = std::min(per_wave, n_paths - p0);
+        if (cudaMemsetAsync(Q.count, 0, 4, st) != cudaSuccess) {
+            s = cuda_fail(cudaGetLastError(), "lt_trace_paths: memset");
+            break;
+        }
+        const dim3 grid((unsigned)((n + kPathsBlock - 1) / kPathsBlock), (unsigned)np);
+        const unsigned gr = persistent_blocks(rest, kPathsBlock, (size_t)np * n, 32);
+        if (cauchy) {
+            paths_front_kernel<true><<<grid, kPathsBlock, 0, st>>>(L->dev, P, p0, din, lam_stride, dout, nn, Q, prof.work());
+            paths_rest_kernel<true><<<gr, kPathsBlock, 0, st>>>(L->dev, P, Q, dout, prof.work());
+        } else {
+            paths_front_kernel<false><<<grid, kPathsBlock, 0, st>>>(L->dev, P, p0, din, lam_stride, dout, nn, Q, prof.work());
+            paths_rest_kernel<false><<<gr, kPathsBlock, 0, st>>>(L->dev, P, Q, dout, prof.work());
+        }
+        if (cudaGetLastError() != cudaSuccess) s = cuda_fail(cudaGetLastError(), "lt_trace_paths: launch");
+    }
+    cudaFreeAsync(buf, st);
+    return s;
 }

@@ -28,6 +28,9 @@ lt_status launch_trace(const lt_lens* L, int pi, int pj, const RaysInDev& in,
                        const RaysOutDev& out, size_t n, cudaStream_t st);
 // blocks for a persistent kernel: resident blocks per SM x SMs, capped by the work
 unsigned persistent_blocks(const void* kernel, int block, size_t items, size_t per_warp);
+// the library's stream-ordered memory pool of the current device (freed
+// blocks are kept for reuse)
+lt_status scratch_pool(cudaMemPool_t* pool);
 
 // ---------------------------------------------------------------- host staging
 

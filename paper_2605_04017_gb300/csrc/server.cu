@@ -162,11 +162,15 @@ static void CUDART_CB on_done(void* p)
 
 static size_t round16(size_t b) { return (b + 15) & ~(size_t)15; }
 
-// Device bytes a request holds while in flight.
-static size_t request_bytes(const lt_request& r)
+// Device bytes a request holds while in flight: host staging, and the ray
+// queue of the tracer's second kernel (kQueueBytesPerRay per ray of a wave
+// of at most 2^24 rays) for a trace launched on its own.
+static size_t request_bytes(const lt_request& r, size_t fuse_max_rays)
 {
     size_t b = 0;
     if (r.flags & LT_REQ_HOST_BUFFERS) b += 12 * round16(r.n * 4) + round16(r.n);
+    if (r.kind == LT_REQ_TRACE && (r.n > fuse_max_rays || (r.flags & LT_REQ_HOST_BUFFERS)))
+        b += (std::min(r.n, (size_t)1 << 24) + 64) * kQueueBytesPerRay + 256;
     return b;
 }
 
@@ -483,7 +487,7 @@ lt_status lt_submit(lt_server* s, const lt_request* r, uint64_t* ticket)
                 return fail(LT_EINVAL, "lt_submit: device ray arrays must be 16-byte aligned");
         }
     }
-    const size_t bytes = request_bytes(*r);
+    const size_t bytes = request_bytes(*r, s->o.fuse_max_rays);
     if (bytes > s->o.mem_budget_bytes)
         return fail(LT_ENOMEM, "lt_submit: request needs %zu bytes, budget %zu", bytes, s->o.mem_budget_bytes);
     const Clock::time_point now = Clock::now();

@@ -10,27 +10,102 @@ namespace lt {
 
 constexpr int kTraceBlock = 256;
 
-// One thread per ray.  Inputs are read once through the non-coherent path,
-// outputs written with an evict-first hint (nothing here re-reads them).
+// The tracer runs as a two-kernel wavefront.  Most rays of a real lens die
+// at its first surfaces (the entrance disk overfills the front aperture),
+// the rest go on to the image; one thread per ray would keep each warp
+// running to its longest ray with most lanes idle.
+//  - trace_front_kernel: one thread per ray through the first kFront
+//    interactions; finished rays are written at once, survivors' states go
+//    to a queue (warp-aggregated appends, structure of arrays).
+//  - trace_rest_kernel: a persistent grid traces the queue to the end with
+//    every lane busy and writes each result at its ray's index.
+// Per-ray arithmetic is that of trace_ray, bit for bit.
+// Paths of up to kShortPath interactions (the whole path is about as long
+// as the front) run instead as one block-compacting kernel (trace_block),
+// where queueing survivors would cost more than it saves.
+constexpr int kShortPath = 4;
+constexpr size_t kWaveRays = (size_t)1 << 24;   // rays per front/rest pair (queue <= 872 MB)
+
 template <bool CAUCHY>
 __global__ void __launch_bounds__(kTraceBlock)
-trace_kernel(const __grid_constant__ LensDev L, int pi, int pj, RaysInDev in, RaysOutDev out,
-             uint32_t n, unsigned long long* work)
+trace_short_kernel(const __grid_constant__ LensDev L, int pi, int pj, RaysInDev in, RaysOutDev out,
+                   uint32_t n, unsigned long long* work)
+{
+    __shared__ TraceSmem<kTraceBlock> S;
+    const uint32_t r0 = blockIdx.x * kTraceBlock;
+    const int nint = trace_block<CAUCHY, kTraceBlock>(L, pi, pj, in.x, in.y, in.dx, in.dy, in.dz, in.lam,
+                                                      n, r0, S);
+    __syncthreads();
+    const int t = threadIdx.x;
+    const uint32_t r = r0 + (uint32_t)t;
+    if (r < n) {
+        __stcs(out.x + r, S.ob[0][t]);
+        __stcs(out.y + r, S.ob[1][t]);
+        __stcs(out.dx + r, S.ob[2][t]);
+        __stcs(out.dy + r, S.ob[3][t]);
+        __stcs(out.dz + r, S.ob[4][t]);
+        __stcs(out.I + r, S.ob[5][t]);
+        out.flags[r] = S.of[t];
+    }
+    warp_add(work, (unsigned)nint);
+}
+
+
+__device__ __forceinline__ void store_result(const RaysOutDev& out, uint32_t r, const RayState& st, int res)
+{
+    const bool done = res == STEP_DONE;
+    __stcs(out.x + r, done ? st.x : 0.0f);
+    __stcs(out.y + r, done ? st.y : 0.0f);
+    __stcs(out.dx + r, done ? st.dx : 0.0f);
+    __stcs(out.dy + r, done ? st.dy : 0.0f);
+    __stcs(out.dz + r, done ? st.dz : 0.0f);
+    __stcs(out.I + r, done ? st.I : 0.0f);
+    out.flags[r] = (uint8_t)(done ? st.flags : (st.flags & ~LT_FLAG_VALID));
+}
+
+template <bool CAUCHY>
+__global__ void __launch_bounds__(kTraceBlock)
+trace_front_kernel(const __grid_constant__ LensDev L, int pi, int pj, RaysInDev in, RaysOutDev out,
+                   uint32_t n, RayQueue Q, unsigned long long* work)
 {
     const uint32_t r = blockIdx.x * kTraceBlock + threadIdx.x;
+    const int K = path_length(L.S, pi, pj);
+    RayState st;
+    bool live = false;
     int nint = 0;
     if (r < n) {
-        TraceOut o;
-        const uint32_t f = trace_ray<CAUCHY>(L, pi, pj, __ldg(in.x + r), __ldg(in.y + r),
-                                             __ldg(in.dx + r), __ldg(in.dy + r), __ldg(in.dz + r),
-                                             __ldg(in.lam + r), o, nint);
-        __stcs(out.x + r, o.x);
-        __stcs(out.y + r, o.y);
-        __stcs(out.dx + r, o.dx);
-        __stcs(out.dy + r, o.dy);
-        __stcs(out.dz + r, o.dz);
-        __stcs(out.I + r, o.I);
-        out.flags[r] = (uint8_t)f;
+        live = trace_init(__ldg(in.x + r), __ldg(in.y + r), __ldg(in.dx + r), __ldg(in.dy + r),
+                          __ldg(in.dz + r), __ldg(in.lam + r), st);
+        int res = live ? STEP_GO : STEP_DEAD;
+        for (int i = 0; i < kFront && res == STEP_GO; ++i) res = trace_step<CAUCHY>(L, pi, pj, K, st);
+        if (res != STEP_GO) {
+            if (live) nint = st.k + (res == STEP_DONE ? 1 : 0);
+            live = false;
+            store_result(out, r, st, res);
+        }
+    }
+    queue_push(Q, live, st, r, 0);
+    warp_add(work, (unsigned)nint);
+}
+
+template <bool CAUCHY>
+__global__ void __launch_bounds__(kTraceBlock)
+trace_rest_kernel(const __grid_constant__ LensDev L, int pi, int pj, RayQueue Q, RaysOutDev out,
+                  unsigned long long* work)
+{
+    const uint32_t cnt = *Q.count;
+    const int K = path_length(L.S, pi, pj);
+    int nint = 0;
+    for (uint32_t i = blockIdx.x * kTraceBlock + threadIdx.x; i < cnt; i += gridDim.x * kTraceBlock) {
+        RayState st;
+        queue_load(Q, i, st);
+        int res;
+#pragma unroll 1
+        do {
+            res = trace_step<CAUCHY>(L, pi, pj, K, st);
+        } while (res == STEP_GO);
+        nint += st.k + (res == STEP_DONE ? 1 : 0);
+        store_result(out, Q.ray[i], st, res);
     }
     warp_add(work, (unsigned)nint);
 }
@@ -55,20 +130,58 @@ lt_status launch_trace(const lt_lens* L, int pi, int pj, const RaysInDev& in,
                        const RaysOutDev& out, size_t n, cudaStream_t st)
 {
     const bool cauchy = lens_all_cauchy(L->dev);
-    for (size_t off = 0; off < n; off += ((size_t)1 << 30)) {
-        const uint32_t m = (uint32_t)std::min<size_t>(n - off, (size_t)1 << 30);
+    if (path_length(L->S, pi, pj) <= kShortPath) {
+        for (size_t off = 0; off < n; off += ((size_t)1 << 30)) {
+            const uint32_t m = (uint32_t)std::min<size_t>(n - off, (size_t)1 << 30);
+            RaysInDev a{in.x + off, in.y + off, in.dx + off, in.dy + off, in.dz + off, in.lam + off};
+            RaysOutDev b{out.x + off, out.y + off, out.dx + off, out.dy + off, out.dz + off,
+                         out.I + off, out.flags + off};
+            ProfScope prof("trace_kernel", st);
+            const unsigned g = (m + kTraceBlock - 1) / kTraceBlock;
+            if (cauchy) trace_short_kernel<true><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, prof.work());
+            else trace_short_kernel<false><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, prof.work());
+            LT_CUDA_TRY(cudaGetLastError());
+        }
+        return LT_OK;
+    }
+    const size_t wave = std::min(n, kWaveRays);
+    cudaMemPool_t pool;
+    lt_status s = scratch_pool(&pool);
+    if (s != LT_OK) return s;
+    const size_t cap = (wave + 63) & ~(size_t)63;
+    char* buf = nullptr;
+    if (cudaMallocFromPoolAsync((void**)&buf, cap * kQueueBytesPerRay + 256, pool, st) != cudaSuccess)
+        return fail(LT_ENOMEM, "lt_trace: ray queue allocation of %zu bytes failed", cap * kQueueBytesPerRay + 256);
+    RayQueue Q;
+    float** fq[10] = {&Q.x, &Q.y, &Q.z, &Q.dx, &Q.dy, &Q.dz, &Q.I, &Q.n, &Q.il2, &Q.l2};
+    for (int q = 0; q < 10; ++q) *fq[q] = reinterpret_cast<float*>(buf + (size_t)q * cap * 4);
+    Q.k = reinterpret_cast<int*>(buf + 10 * cap * 4);
+    Q.flags = reinterpret_cast<uint32_t*>(buf + 11 * cap * 4);
+    Q.ray = reinterpret_cast<uint32_t*>(buf + 12 * cap * 4);
+    Q.path = nullptr;
+    Q.count = reinterpret_cast<uint32_t*>(buf + 13 * cap * 4);
+    const void* rest = cauchy ? (const void*)trace_rest_kernel<true> : (const void*)trace_rest_kernel<false>;
+    for (size_t off = 0; off < n && s == LT_OK; off += wave) {
+        const uint32_t m = (uint32_t)std::min(n - off, wave);
         RaysInDev a{in.x + off, in.y + off, in.dx + off, in.dy + off, in.dz + off, in.lam + off};
         RaysOutDev b{out.x + off, out.y + off, out.dx + off, out.dy + off, out.dz + off,
                      out.I + off, out.flags + off};
         ProfScope prof("trace_kernel", st);
+        if (cudaMemsetAsync(Q.count, 0, 4, st) != cudaSuccess) { s = cuda_fail(cudaGetLastError(), "lt_trace: memset"); break; }
         const unsigned g = (m + kTraceBlock - 1) / kTraceBlock;
-        if (cauchy)
-            trace_kernel<true><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, prof.work());
-        else
-            trace_kernel<false><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, prof.work());
-        LT_CUDA_TRY(cudaGetLastError());
+        // the rest kernel's grid: resident blocks, no more than the wave could need
+        const unsigned gr = persistent_blocks(rest, kTraceBlock, m, 32);
+        if (cauchy) {
+            trace_front_kernel<true><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, Q, prof.work());
+            trace_rest_kernel<true><<<gr, kTraceBlock, 0, st>>>(L->dev, pi, pj, Q, b, prof.work());
+        } else {
+            trace_front_kernel<false><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, Q, prof.work());
+            trace_rest_kernel<false><<<gr, kTraceBlock, 0, st>>>(L->dev, pi, pj, Q, b, prof.work());
+        }
+        if (cudaGetLastError() != cudaSuccess) s = cuda_fail(cudaGetLastError(), "lt_trace: launch");
     }
-    return LT_OK;
+    cudaFreeAsync(buf, st);
+    return s;
 }
 
 // ---------------------------------------------------------------- host staging

@@ -136,7 +136,8 @@ def test_admission_deadline_and_poll(lenses):
     it can be admitted, and everything admitted completes."""
     pres, ls = lenses
     n = 1 << 22
-    need = 12 * n * 4 + n
+    # host staging (49 B/ray, arrays rounded to 16 B) + the tracer's queue (54 B/ray)
+    need = 12 * n * 4 + n + (n + 64) * 54 + 256
     srv = lt.Server(mem_budget_bytes=need + 1000)
     rays = rays_for(pres[1], n, 8)
     h1, h2, h3 = batch.HostRays(rays), batch.HostRays(rays), batch.HostRays(rays)
