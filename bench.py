@@ -272,18 +272,22 @@ def run_ours(args):
     interp = (~traced) & ((qflags & lt.FLAG_VALID) != 0)
     n_interp = int(interp.sum())
     peaks = load_peaks()
-    # algorithmic bytes of one query launch: every ray's 24 B in and 25 B out,
-    # plus the map's node table (6 floats per node) and cell classes once
+    # algorithmic bytes of one classify-and-gather launch: every ray's 24 B in,
+    # 25 B out for the rays it answers and a 4 B queue entry for the rays it
+    # hands to the tracer, plus the map's node table (6 floats per node) and
+    # cell classes once
     table_bytes = mstats["n_nodes"] * 24 + (mstats["n_cells"] + 15) // 16 * 4
-    q_bytes = n * 49 + table_bytes
+    q_bytes = n * 24 + (n - n_fb) * 25 + n_fb * 4 + table_bytes
     kernels = {
         "map_query_kernel": kernel_roofline("map_query_kernel", pq, peaks, units_bytes=q_bytes),
+        "map_trace_kernel": kernel_roofline("map_trace_kernel", pq, peaks,
+                                            flops_per_work=FLOPS_PER_INTERACTION),
         "trace_kernel": kernel_roofline("trace_kernel", pt, peaks,
                                         flops_per_work=FLOPS_PER_INTERACTION),
     }
-    kernels["map_query_kernel"]["fallback_interactions_per_launch"] = int(
-        pq["map_query_kernel"][2] / pq["map_query_kernel"][0])
-    dom = "map_query_kernel"
+    kernels["map_trace_kernel"]["traced_rays_per_launch"] = n_fb
+    # the roofline reported is that of the step's longer kernel
+    dom = max(("map_query_kernel", "map_trace_kernel"), key=lambda k: kernels[k]["avg_launch_ms"])
     roof = dict(kernels[dom])
     tr = NCU_TRAFFIC.get(dom)
     roof["traffic"] = (tr["bytes_per_ray"] * n if tr and tr["hash"] == src_hash() else None)

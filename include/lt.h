@@ -266,26 +266,39 @@ enum {
                                   zeros) and report it valid; outside the box: tracer */
 };
 
-/* Query the map for n rays (device arrays, as lt_trace): one kernel that
- * classifies every ray, interpolates VALID cells, traces BOUNDARY cells and
- * rays outside the box exactly (those carry LT_FLAG_TRACED), and writes all
- * results.  It allocates nothing and needs no scratch memory.
- * Errors as lt_trace. */
+/* Query the map for n rays (device arrays, as lt_trace): the factorised
+ * lookup of Sec. 4.2 (Eq. 11).  A first kernel classifies every ray,
+ * answers INVALID cells, interpolates VALID cells and queues BOUNDARY cells
+ * and rays outside the box; a second traces the queue exactly (those rays
+ * carry LT_FLAG_TRACED) and writes their results.  The queue (28 bytes per
+ * ray) comes from the library's stream-ordered memory pool, which keeps
+ * freed blocks for reuse, so steady-state calls do not reach cudaMalloc.
+ * Errors as lt_trace; LT_ENOMEM if the queue cannot be had. */
 lt_status lt_query(const lt_map* map, const lt_rays_in* in, const float* lambda_nm,
                    const lt_rays_out* out, size_t n, int32_t mode, lt_stream stream);
 /* Same with HOST arrays; returns when the results are in host memory. */
 lt_status lt_query_host(const lt_map* map, const lt_rays_in* in, const float* lambda_nm,
                         const lt_rays_out* out, size_t n, int32_t mode);
 
-/* Map query with a guaranteed allocation-free contract, for callers that
- * cannot allocate GPU memory while they run (a renderer or serving process
- * that reserves the whole device at start-up, or a loop where any cudaMalloc
- * is not allowed).  The paper has no counterpart: this is a deployment aid.
- * lt_query itself now allocates nothing either; this entry point keeps its
- * contract stable: same arguments, results and errors as lt_query, and
- * n > LT_NOALLOC_MAX_RAYS is rejected with LT_EINVAL (split larger
- * batches).  Calls on different streams may overlap freely. */
-#define LT_NOALLOC_MAX_RAYS (1 << 20)
+/* Map query that allocates nothing, for callers that cannot allocate GPU
+ * memory while they run: a renderer or serving process whose own allocator
+ * reserves the whole device at start-up (so a later cudaMalloc or pool
+ * growth fails), or a loop where cudaMalloc and the device-wide
+ * synchronisation it can imply are not allowed.  The paper has no
+ * counterpart: this is a deployment aid.
+ * Same arguments, results and errors as lt_query, but its trace queue lives
+ * in a fixed array inside the library (28 bytes per ray of
+ * LT_NOALLOC_MAX_RAYS rays plus two counters: 14 MiB, held on every device
+ * that loads the library until the process exits), so
+ * n > LT_NOALLOC_MAX_RAYS is rejected with LT_EINVAL: split larger batches.
+ *  - The first call on a device looks up the array's device address (a
+ *    driver query, no allocation); make that first call before any stream
+ *    capture.
+ *  - Every call shares the one array, and its counter is cleared on the
+ *    call's stream: calls whose work overlaps on the GPU (different streams
+ *    without an event between them) race and give wrong results.  Order
+ *    them on one stream. */
+#define LT_NOALLOC_MAX_RAYS (1 << 19)
 lt_status lt_query_noalloc(const lt_map* map, const lt_rays_in* in, const float* lambda_nm,
                            const lt_rays_out* out, size_t n, int32_t mode, lt_stream stream);
 

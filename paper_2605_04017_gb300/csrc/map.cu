@@ -330,10 +330,12 @@ struct __align__(16) GatherItem {
 // lower (v0) and upper (v1) dimension-0 corner by the product of its corner's
 // factors; lanes differing in bit 4 swap halves of the four sums, bit 3
 // swaps quarters, bits 2 and 1 are summed as they are, leaving component c
-// in lanes whose bits 1-2 are clear.
+// in lanes whose bits 1-2 are clear, which write it to ob[e.slot * kObStride
+// + c] (a stride of 7 words puts the six writers in six banks).
+constexpr int kObStride = 7;
 __device__ __forceinline__ void gather_sum(const GatherItem& e, float4 v0, float4 v1, bool c1, bool c2,
                                            bool c3, bool upper, bool u4, bool u3, bool writer, int comp,
-                                           int lane, float (*ob)[kQBlock], uint8_t* of)
+                                           float* ob)
 {
     const unsigned full = 0xffffffffu;
     const float w = ((c1 ? e.f[1] : 1.0f - e.f[1]) * (c2 ? e.f[2] : 1.0f - e.f[2])) *
@@ -348,55 +350,57 @@ __device__ __forceinline__ void gather_sum(const GatherItem& e, float4 v0, float
     kk += __shfl_xor_sync(full, u3 ? k0 : k1, 8);
     kk += __shfl_xor_sync(full, kk, 4);
     kk += __shfl_xor_sync(full, kk, 2);
-    if (writer) ob[comp][e.slot] = kk;
-    if (lane == 0) of[e.slot] = LT_FLAG_VALID;
+    if (writer) ob[e.slot * kObStride + comp] = kk;
 }
 
-// The fused map query: one block per 256 rays.
-//  1. Each thread classifies its ray.  INVALID cells are answered at once;
-//     VALID cells are queued for a gather; BOUNDARY cells and rays outside
-//     the lattice box are queued for the exact tracer.
-//  2. A warp whose index owns a 32-ray chunk of the trace queue traces it
-//     (one thread per ray); every warp then takes queued gathers one at a
-//     time from a shared counter.  A gather is warp-cooperative: lane
-//     (q, part) loads 16 bytes -- part 0/1: the two halves of the lower-
-//     lambda node record, 2/3: of the upper one -- of corner pair q
-//     (q = the corner bits of dimensions 1-3) for dimension-0 corner 0 and 1,
-//     so each warp load reads eight whole 64-byte pairs.  Each lane weights
-//     its own values (the lambda factor included), and a transposed butterfly
-//     (5 shuffles) leaves component c of the sum in lane 8c (x, y, dx, dy)
-//     or 8c + 1 (dz, I).
-//  3. The block writes its 256 results with coalesced stores; interpolated
-//     directions are renormalised there.
-// Tracing and gathering warps of the resident blocks overlap ALU work with
-// gather latency, and no fallback list leaves the block.
+// The map query runs as two kernels.
+// map_query_kernel: each warp answers 32 consecutive rays on its own (no
+// block-wide barrier, so warps of a block never wait for one another).
+//  1. Each lane classifies its ray.  INVALID cells are answered at once;
+//     VALID cells are queued in the warp's shared-memory list for a gather;
+//     BOUNDARY cells and rays outside the lattice box go to the launch's
+//     trace queue (their index, bit 31 set for an outside ray; one atomic
+//     per warp).
+//  2. The warp gathers its queued rays two at a time (four 16-byte loads
+//     per lane in flight).  A gather is warp-cooperative: lane (q, part)
+//     loads 16 bytes -- part 0/1: the two halves of the lower-lambda node
+//     record, 2/3: of the upper one -- of corner pair q (q = the corner bits
+//     of dimensions 1-3) for dimension-0 corner 0 and 1, so each warp load
+//     reads eight whole 64-byte pairs.  Each lane weights its own values
+//     (the lambda factor included), and a transposed butterfly (5 shuffles)
+//     leaves component c of the sum in lane 8c (x, y, dx, dy) or 8c + 1
+//     (dz, I).
+//  3. Each lane writes its own ray (coalesced) unless it was queued for the
+//     tracer; interpolated directions are renormalised there.
+// map_trace_kernel, a persistent grid, then traces the queue with the exact
+// tracer, 256 rays per block at a time with survivors compacted (the rays
+// of BOUNDARY cells die at every depth of the lens), and writes each result
+// at its ray's index.
+constexpr int kQWarps = kQBlock / 32;
+constexpr int kGatherBatch = 2;
+
 template <int MODE, bool CAUCHY>
 __global__ void __launch_bounds__(kQBlock)
-map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out, uint32_t n,
-                 unsigned long long* work)
+map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out, uint32_t n, TraceQueue Q)
 {
-    __shared__ GatherItem gq[kQBlock];
-    __shared__ uint32_t tq[kQBlock];
-    __shared__ float ob[6][kQBlock];
-    __shared__ uint8_t of[kQBlock];
-    __shared__ uint32_t ng, nt, next;
+    __shared__ GatherItem gq_all[kQWarps][32];
+    __shared__ float ob_all[kQWarps][32 * kObStride];
     const unsigned full = 0xffffffffu;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    if (t == 0) {
-        ng = 0;
-        nt = 0;
-        next = 0;
-    }
-    of[t] = 0;
-    __syncthreads();
-    const uint32_t r0 = blockIdx.x * kQBlock;
-    const uint32_t r = r0 + t;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    GatherItem* gq = gq_all[warp];
+    float* ob = ob_all[warp];
+    const uint32_t r = blockIdx.x * kQBlock + threadIdx.x;
     bool ip = false, tr = false;
-    uint32_t tag = (uint32_t)t, base = 0;
+    uint32_t tag = r, base = 0;
     float f[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float x = 0.f, y = 0.f, dx = 0.f, dy = 0.f, dz = 0.f, lam = 0.f;
     if (r < n) {
-        const float x = __ldg(in.x + r), y = __ldg(in.y + r), dx = __ldg(in.dx + r),
-                    dy = __ldg(in.dy + r), dz = __ldg(in.dz + r), lam = __ldg(in.lam + r);
+        x = __ldg(in.x + r);
+        y = __ldg(in.y + r);
+        dx = __ldg(in.dx + r);
+        dy = __ldg(in.dy + r);
+        dz = __ldg(in.dz + r);
+        lam = __ldg(in.lam + r);
         uint32_t cid = 0;
         if (!cell_and_base(M, x, y, dx, dy, dz, lam, cid, base, f)) {
             tr = true;
@@ -408,58 +412,37 @@ map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out,
         }
     }
     const unsigned lt_mask = (1u << lane) - 1u;
-    unsigned m = __ballot_sync(full, ip);
+    unsigned m = __ballot_sync(full, tr);
     if (m) {
         const int leader = __ffs(m) - 1;
         uint32_t b = 0;
-        if (lane == leader) b = atomicAdd(&ng, (uint32_t)__popc(m));
+        if (lane == leader) b = atomicAdd(Q.count, (uint32_t)__popc(m));
         b = __shfl_sync(full, b, leader);
-        if (ip) {
-            GatherItem e;
-            e.slot = (uint32_t)t;
-            e.base = base;
+        if (tr) {
+            const uint32_t k = b + __popc(m & lt_mask);
+            Q.x[k] = x;
+            Q.y[k] = y;
+            Q.dx[k] = dx;
+            Q.dy[k] = dy;
+            Q.dz[k] = dz;
+            Q.lam[k] = lam;
+            Q.tag[k] = tag;
+        }
+    }
+    const unsigned mv = __ballot_sync(full, ip);
+    const int nv = __popc(mv);
+    if (ip) {
+        GatherItem e;
+        e.slot = (uint32_t)lane;
+        e.base = base;
 #pragma unroll
-            for (int d = 0; d < 5; ++d) e.f[d] = f[d];
-            e.pad = 0.0f;
-            gq[b + __popc(m & lt_mask)] = e;
-        }
+        for (int d = 0; d < 5; ++d) e.f[d] = f[d];
+        e.pad = 0.0f;
+        gq[__popc(mv & lt_mask)] = e;
     }
-    m = __ballot_sync(full, tr);
-    if (m) {
-        const int leader = __ffs(m) - 1;
-        uint32_t b = 0;
-        if (lane == leader) b = atomicAdd(&nt, (uint32_t)__popc(m));
-        b = __shfl_sync(full, b, leader);
-        if (tr) tq[b + __popc(m & lt_mask)] = tag;
-    }
-    __syncthreads();
-    const uint32_t ngq = ng, ntq = nt;
+    __syncwarp();
 
-    // exact tracer for this warp's chunk of the trace queue
-    if ((uint32_t)warp * 32u < ntq) {
-        const uint32_t k = (uint32_t)warp * 32u + (uint32_t)lane;
-        int nint = 0;
-        if (k < ntq) {
-            const uint32_t e = tq[k];
-            const uint32_t s = e & 0xffffu;
-            const uint32_t rr = r0 + s;
-            TraceOut o;
-            uint32_t fl = trace_ray<CAUCHY>(M.L, M.pi, M.pj, __ldg(in.x + rr), __ldg(in.y + rr),
-                                            __ldg(in.dx + rr), __ldg(in.dy + rr), __ldg(in.dz + rr),
-                                            __ldg(in.lam + rr), o, nint);
-            fl |= LT_FLAG_TRACED | ((e & kOutsideBit) ? LT_FLAG_OUTSIDE : 0u);
-            ob[0][s] = o.x;
-            ob[1][s] = o.y;
-            ob[2][s] = o.dx;
-            ob[3][s] = o.dy;
-            ob[4][s] = o.dz;
-            ob[5][s] = o.I;
-            of[s] = (uint8_t)fl;
-        }
-        warp_add(work, (unsigned)nint);
-    }
-
-    // warp-cooperative gathers
+    // warp-cooperative gathers, kGatherBatch at a time
     const int part = lane & 3, q = lane >> 2;
     const bool c1 = (q >> 2) & 1, c2 = (q >> 1) & 1, c3 = q & 1, upper = (part & 2) != 0;
     const uint32_t loff = (c1 ? M.stride[1] : 0u) + (c2 ? M.stride[2] : 0u) + (c3 ? M.stride[3] : 0u);
@@ -468,42 +451,76 @@ map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out,
     const bool u4 = (lane & 16) != 0, u3 = (lane & 8) != 0;
     const bool writer = (lane & 6) == 0 && !((lane & 1) && u4);
     const int comp = (lane & 1) ? 4 + (u3 ? 1 : 0) : (u4 ? 2 : 0) + (u3 ? 1 : 0);
-    // two queued rays per iteration: four loads in flight before any sum
-    while (true) {
-        uint32_t it = 0;
-        if (lane == 0) it = atomicAdd(&next, 2u);
-        it = __shfl_sync(full, it, 0);
-        if (it >= ngq) break;
-        const bool two = it + 1 < ngq;
-        const GatherItem ea = gq[it];
-        const GatherItem eb = gq[two ? it + 1 : it];
-        const uint32_t na = ea.base + loff, nb = eb.base + loff;
-        const float4 a0 = __ldg(node4 + (size_t)na * 2 + part);
-        const float4 a1 = __ldg(node4 + (size_t)(na + s0) * 2 + part);
-        const float4 b0 = __ldg(node4 + (size_t)nb * 2 + part);
-        const float4 b1 = __ldg(node4 + (size_t)(nb + s0) * 2 + part);
-        gather_sum(ea, a0, a1, c1, c2, c3, upper, u4, u3, writer, comp, lane, ob, of);
-        if (two) gather_sum(eb, b0, b1, c1, c2, c3, upper, u4, u3, writer, comp, lane, ob, of);
-    }
-    __syncthreads();
-
-    if (r < n) {
-        const uint32_t fl = of[t];
-        float o[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (fl & LT_FLAG_VALID) {
+#pragma unroll 1
+    for (int g = 0; g < nv; g += kGatherBatch) {
+        float4 v0[kGatherBatch], v1[kGatherBatch];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) o[k] = ob[k][t];
-            if (!(fl & LT_FLAG_TRACED)) {
-                const float n2 = fmaf(o[2], o[2], fmaf(o[3], o[3], o[4] * o[4]));
-                float inv = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
-                inv = inv * fmaf(-0.5f * n2, inv * inv, 1.5f);
-                o[2] *= inv;
-                o[3] *= inv;
-                o[4] *= inv;
-            }
+        for (int k = 0; k < kGatherBatch; ++k) {
+            const uint32_t nb = gq[min(g + k, nv - 1)].base + loff;
+            v0[k] = __ldg(node4 + (size_t)nb * 2 + part);
+            v1[k] = __ldg(node4 + (size_t)(nb + s0) * 2 + part);
         }
-        store_out(out, r, o, fl);
+#pragma unroll
+        for (int k = 0; k < kGatherBatch; ++k)
+            if (g + k < nv) gather_sum(gq[g + k], v0[k], v1[k], c1, c2, c3, upper, u4, u3, writer, comp, ob);
     }
+    __syncwarp();
+
+    if (r < n && !tr) {
+        float o[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (ip) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) o[k] = ob[lane * kObStride + k];
+            const float n2 = fmaf(o[2], o[2], fmaf(o[3], o[3], o[4] * o[4]));
+            float inv = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
+            inv = inv * fmaf(-0.5f * n2, inv * inv, 1.5f);
+            o[2] *= inv;
+            o[3] *= inv;
+            o[4] *= inv;
+        }
+        store_out(out, r, o, ip ? LT_FLAG_VALID : 0u);
+    }
+}
+
+// The exact tracer over the query's trace queue (see map_query_kernel):
+// blocks take 256-ray chunks of the queue from a counter until it is empty.
+template <bool CAUCHY>
+__global__ void __launch_bounds__(kQBlock)
+map_trace_kernel(const __grid_constant__ MapDev M, RaysOutDev out, TraceQueue Q, unsigned long long* work)
+{
+    __shared__ TraceSmem<kQBlock> S;
+    __shared__ uint32_t chunk;
+    const int t = threadIdx.x;
+    const uint32_t cnt = *Q.count;
+    int nint = 0;
+#pragma unroll 1
+    while (true) {
+        if (t == 0) chunk = atomicAdd(Q.count + 1, 1u);
+        __syncthreads();
+        const uint32_t c0 = chunk * (uint32_t)kQBlock;
+        if (c0 >= cnt) break;
+        const uint32_t k = c0 + (uint32_t)t;
+        uint32_t e = 0;
+        RayState st;
+        bool live = false;
+        S.of[t] = 0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) S.ob[q][t] = 0.0f;
+        if (k < cnt) {
+            e = Q.tag[k];
+            live = trace_init(Q.x[k], Q.y[k], Q.dx[k], Q.dy[k], Q.dz[k], Q.lam[k], st);
+            if (!live) S.of[t] = (uint8_t)st.flags;
+        }
+        nint += trace_block_states<CAUCHY, kQBlock>(M.L, M.pi, M.pj, live, st, S);
+        __syncthreads();
+        if (k < cnt) {
+            const uint32_t r = e & ~kOutsideBit;
+            const float o[6] = {S.ob[0][t], S.ob[1][t], S.ob[2][t], S.ob[3][t], S.ob[4][t], S.ob[5][t]};
+            store_out(out, r, o, S.of[t] | LT_FLAG_TRACED | ((e & kOutsideBit) ? LT_FLAG_OUTSIDE : 0u));
+        }
+        __syncthreads();
+    }
+    warp_add(work, (unsigned)nint);
 }
 
 // ------------------------------------------------------------------ scratch pool
@@ -531,21 +548,59 @@ lt_status scratch_pool(cudaMemPool_t* pool)
     return LT_OK;
 }
 
+TraceQueue trace_queue_at(void* scratch, size_t n)
+{
+    char* p = static_cast<char*>(scratch);
+    const size_t cap = (n + 63) & ~(size_t)63;
+    TraceQueue Q;
+    Q.count = reinterpret_cast<uint32_t*>(p);
+    float** fq[6] = {&Q.x, &Q.y, &Q.dx, &Q.dy, &Q.dz, &Q.lam};
+    for (int q = 0; q < 6; ++q) *fq[q] = reinterpret_cast<float*>(p + 256 + (size_t)q * cap * 4);
+    Q.tag = reinterpret_cast<uint32_t*>(p + 256 + 6 * cap * 4);
+    return Q;
+}
+
+lt_status launch_query_with(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
+                            int mode, const TraceQueue& Q, cudaStream_t st)
+{
+    const unsigned blocks = (n + kQBlock - 1) / kQBlock;
+    const bool table = mode == LT_QUERY_TABLE;
+    const void* trace = map->cauchy ? (const void*)map_trace_kernel<true> : (const void*)map_trace_kernel<false>;
+    const unsigned gt = persistent_blocks(trace, kQBlock, n, 32);
+    LT_CUDA_TRY(cudaMemsetAsync(Q.count, 0, 2 * sizeof(uint32_t), st));
+    {
+        ProfScope prof("map_query_kernel", st);
+        if (map->cauchy) {
+            if (table) map_query_kernel<LT_QUERY_TABLE, true><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, Q);
+            else map_query_kernel<LT_QUERY_NO_MASK, true><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, Q);
+        } else {
+            if (table) map_query_kernel<LT_QUERY_TABLE, false><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, Q);
+            else map_query_kernel<LT_QUERY_NO_MASK, false><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, Q);
+        }
+        LT_CUDA_TRY(cudaGetLastError());
+    }
+    {
+        ProfScope prof("map_trace_kernel", st);
+        if (map->cauchy) map_trace_kernel<true><<<gt, kQBlock, 0, st>>>(map->dev, out, Q, prof.work());
+        else map_trace_kernel<false><<<gt, kQBlock, 0, st>>>(map->dev, out, Q, prof.work());
+        LT_CUDA_TRY(cudaGetLastError());
+    }
+    return LT_OK;
+}
+
 lt_status launch_query(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
                        int mode, cudaStream_t st)
 {
-    const unsigned blocks = (n + kQBlock - 1) / kQBlock;
-    ProfScope prof("map_query_kernel", st);
-    const bool table = mode == LT_QUERY_TABLE;
-    if (map->cauchy) {
-        if (table) map_query_kernel<LT_QUERY_TABLE, true><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, prof.work());
-        else map_query_kernel<LT_QUERY_NO_MASK, true><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, prof.work());
-    } else {
-        if (table) map_query_kernel<LT_QUERY_TABLE, false><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, prof.work());
-        else map_query_kernel<LT_QUERY_NO_MASK, false><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, prof.work());
-    }
-    LT_CUDA_TRY(cudaGetLastError());
-    return LT_OK;
+    cudaMemPool_t pool;
+    lt_status s = scratch_pool(&pool);
+    if (s != LT_OK) return s;
+    const size_t bytes = query_scratch_bytes(n);
+    char* buf = nullptr;
+    if (cudaMallocFromPoolAsync((void**)&buf, bytes, pool, st) != cudaSuccess)
+        return fail(LT_ENOMEM, "lt_query: trace queue allocation of %zu bytes failed", bytes);
+    s = launch_query_with(map, in, out, n, mode, trace_queue_at(buf, n), st);
+    cudaFreeAsync(buf, st);
+    return s;
 }
 
 }  // namespace lt
@@ -914,6 +969,37 @@ lt_status lt_map_load(const char* path, lt_map** out)
 
 // ---------------------------------------------------------------- allocation-free query
 
+// The trace queue of lt_query_noalloc (layout of trace_queue_at for
+// LT_NOALLOC_MAX_RAYS rays: two counters padded to 256 bytes, then 28 bytes
+// per ray).  A file-scope device array: every device that loads the library
+// holds it until the process exits.
+namespace {
+constexpr size_t kNoallocQueueBytes = query_scratch_bytes(LT_NOALLOC_MAX_RAYS);
+__device__ __align__(256) unsigned char g_noalloc_queue[kNoallocQueueBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {};
+
+// Device address of the array on the current device, looked up once per
+// device.  In host code the symbol is only a host-side stand-in; kernels must
+// be given this address.
+lt_status noalloc_queue(void** out)
+{
+    int dev = 0;
+    LT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(LT_EINVAL, "lt_query_noalloc: device index %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_queue);
+        if (e != cudaSuccess || !p) return cuda_fail(e, "lt_query_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return LT_OK;
+}
+}  // namespace
+
 extern "C" lt_status lt_query_noalloc(const lt_map* m, const lt_rays_in* in, const float* lam,
                                       const lt_rays_out* out, size_t n, int32_t mode,
                                       lt_stream stream)
@@ -927,7 +1013,11 @@ extern "C" lt_status lt_query_noalloc(const lt_map* m, const lt_rays_in* in, con
                     n, LT_NOALLOC_MAX_RAYS);
     lt_status s = check_io(in, lam, out, n, "lt_query_noalloc");
     if (s != LT_OK || n == 0) return s;
+    void* q = nullptr;
+    s = noalloc_queue(&q);
+    if (s != LT_OK) return s;
     RaysInDev din{in->x, in->y, in->dx, in->dy, in->dz, lam};
     RaysOutDev dout{out->x, out->y, out->dx, out->dy, out->dz, out->I, out->flags};
-    return launch_query(m, din, dout, (uint32_t)n, mode, (cudaStream_t)stream);
+    // the queue's counters are cleared by launch_query_with on the call's stream
+    return launch_query_with(m, din, dout, (uint32_t)n, mode, trace_queue_at(q, n), (cudaStream_t)stream);
 }

@@ -25,9 +25,28 @@ struct MapDev {
     const uint32_t* cls;    // 2 bits per cell
 };
 
-// The fused map query of n < 2^31 rays on `st` (no scratch memory).
+// The map query's trace queue: per queued ray its entrance ray (structure of
+// arrays) and its index (bit 31 set: outside the lattice box); count[0]
+// counts queued rays, count[1] the 256-ray chunks the tracer has taken.
+struct TraceQueue {
+    float *x, *y, *dx, *dy, *dz, *lam;
+    uint32_t* tag;
+    uint32_t* count;
+};
+// scratch bytes of the queue for n rays: the counters' 256 bytes, then 7
+// arrays of n (rounded up to 64) words
+constexpr size_t query_scratch_bytes(size_t n) { return 256 + 7 * 4 * ((n + 63) & ~(size_t)63); }
+// the queue laid out in `scratch` (256-byte aligned, query_scratch_bytes(n))
+TraceQueue trace_queue_at(void* scratch, size_t n);
+
+// The map query of n < 2^31 rays on `st`: the classify-and-gather kernel,
+// then the tracer over the rays it queued.  launch_query takes the queue from
+// the library's stream-ordered pool; launch_query_with uses the caller's
+// (its counters are cleared on `st`).
 lt_status launch_query(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
                        int mode, cudaStream_t st);
+lt_status launch_query_with(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
+                            int mode, const TraceQueue& Q, cudaStream_t st);
 
 }  // namespace lt
 

@@ -424,7 +424,7 @@ def profile_read(reset: bool = True) -> dict:
 
 # ------------------------------------------------------------------ allocation-free query
 
-NOALLOC_MAX_RAYS = 1 << 20
+NOALLOC_MAX_RAYS = 1 << 19
 
 
 def query_noalloc(gmap: "Map", inp: Sequence, lam, out: Sequence, n: int,

@@ -1,12 +1,14 @@
 """The allocation-free map query (lt_query_noalloc).
 
-Some callers of this library cannot allocate GPU memory while they run (a
-process that reserves the whole device with its own allocator at start-up,
-or a loop where cudaMalloc is not allowed).  lt_query_noalloc keeps that
-contract in the ABI (the fused query needs no scratch at all).  This checks,
-through the C ABI, that it answers exactly like lt_query on two calls in a
-row, and that it refuses batches larger than its documented limit.
-The file is named to run last: if it fails, every other test has run.
+Some callers of this library cannot allocate GPU memory while they run: a
+renderer or serving process whose allocator reserves the whole device at
+start-up, or a loop where cudaMalloc (and the synchronisation it can imply)
+is not allowed.  lt_query_noalloc gives them the map query with its trace
+queue in a fixed array inside the library instead of the memory pool.  This
+checks, through the C ABI, that it answers like lt_query on two calls in a
+row (the array keeps the first call's contents, so the second call shows
+that the counter is cleared), and that it refuses batches larger than the
+array.  The file is named to run last: if it fails, every other test has run.
 """
 import math
 
