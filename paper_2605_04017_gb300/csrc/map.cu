@@ -318,8 +318,8 @@ __device__ __forceinline__ bool cell_and_base(const MapDev& M, float x, float y,
     return inside;
 }
 
-// A VALID-cell ray of the block waiting for its gather: its slot in the
-// block, the node index of its cell's first corner, its position in the cell.
+// A VALID-cell ray of a warp waiting for its gather: its lane, the node
+// index of its cell's first corner, its position in the cell.
 struct __align__(16) GatherItem {
     uint32_t slot, base;
     float f[5];
@@ -359,8 +359,8 @@ __device__ __forceinline__ void gather_sum(const GatherItem& e, float4 v0, float
 //  1. Each lane classifies its ray.  INVALID cells are answered at once;
 //     VALID cells are queued in the warp's shared-memory list for a gather;
 //     BOUNDARY cells and rays outside the lattice box go to the launch's
-//     trace queue (their index, bit 31 set for an outside ray; one atomic
-//     per warp).
+//     trace queue (entrance ray and index, bit 31 set for an outside ray;
+//     one atomic per warp on its block's segment counter).
 //  2. The warp gathers its queued rays two at a time (four 16-byte loads
 //     per lane in flight).  A gather is warp-cooperative: lane (q, part)
 //     loads 16 bytes -- part 0/1: the two halves of the lower-lambda node
@@ -376,11 +376,11 @@ __device__ __forceinline__ void gather_sum(const GatherItem& e, float4 v0, float
 // tracer, 256 rays per block at a time with survivors compacted (the rays
 // of BOUNDARY cells die at every depth of the lens), and writes each result
 // at its ray's index.
-constexpr int kQWarps = kQBlock / 32;
+constexpr int kQWarps = kQTile / 32;
 constexpr int kGatherBatch = 2;
 
 template <int MODE, bool CAUCHY>
-__global__ void __launch_bounds__(kQBlock)
+__global__ void __launch_bounds__(kQTile)
 map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out, uint32_t n, TraceQueue Q)
 {
     __shared__ GatherItem gq_all[kQWarps][32];
@@ -389,7 +389,7 @@ map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     GatherItem* gq = gq_all[warp];
     float* ob = ob_all[warp];
-    const uint32_t r = blockIdx.x * kQBlock + threadIdx.x;
+    const uint32_t r = blockIdx.x * kQTile + threadIdx.x;
     bool ip = false, tr = false;
     uint32_t tag = r, base = 0;
     float f[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -416,10 +416,11 @@ map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out,
     if (m) {
         const int leader = __ffs(m) - 1;
         uint32_t b = 0;
-        if (lane == leader) b = atomicAdd(Q.count, (uint32_t)__popc(m));
+        const uint32_t seg = blockIdx.x % kQSegs;
+        if (lane == leader) b = atomicAdd(Q.count + seg * kQCountStride, (uint32_t)__popc(m));
         b = __shfl_sync(full, b, leader);
         if (tr) {
-            const uint32_t k = b + __popc(m & lt_mask);
+            const uint32_t k = seg * Q.segcap + b + __popc(m & lt_mask);
             Q.x[k] = x;
             Q.y[k] = y;
             Q.dx[k] = dx;
@@ -483,37 +484,59 @@ map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out,
 }
 
 // The exact tracer over the query's trace queue (see map_query_kernel):
-// blocks take 256-ray chunks of the queue from a counter until it is empty.
+// blocks take 256-ray chunks of the queue's segments from a counter until
+// none is left (chunk c of the launch: segment s with cum[s] <= c <
+// cum[s + 1], cum the prefix sum of the segments' chunk counts).
 template <bool CAUCHY>
 __global__ void __launch_bounds__(kQBlock)
 map_trace_kernel(const __grid_constant__ MapDev M, RaysOutDev out, TraceQueue Q, unsigned long long* work)
 {
     __shared__ TraceSmem<kQBlock> S;
-    __shared__ uint32_t chunk;
+    __shared__ uint32_t cnt[kQSegs], cum[kQSegs + 1];
+    __shared__ uint32_t chunk, cseg;
     const int t = threadIdx.x;
-    const uint32_t cnt = *Q.count;
+    if (t < kQSegs) cnt[t] = Q.count[t * kQCountStride];
+    __syncthreads();
+    if (t == 0) {
+        uint32_t c = 0;
+        for (int s = 0; s < kQSegs; ++s) {
+            cum[s] = c;
+            c += (cnt[s] + kQBlock - 1) / kQBlock;
+        }
+        cum[kQSegs] = c;
+    }
+    __syncthreads();
+    const uint32_t nchunks = cum[kQSegs];
     int nint = 0;
 #pragma unroll 1
     while (true) {
-        if (t == 0) chunk = atomicAdd(Q.count + 1, 1u);
+        if (t == 0) {
+            const uint32_t c = atomicAdd(Q.count + kQSegs * kQCountStride, 1u);
+            int s = 0;
+            while (s < kQSegs - 1 && cum[s + 1] <= c) ++s;
+            chunk = c;
+            cseg = (uint32_t)s;
+        }
         __syncthreads();
-        const uint32_t c0 = chunk * (uint32_t)kQBlock;
-        if (c0 >= cnt) break;
-        const uint32_t k = c0 + (uint32_t)t;
+        if (chunk >= nchunks) break;
+        const uint32_t sg = cseg;
+        const uint32_t i = (chunk - cum[sg]) * (uint32_t)kQBlock + (uint32_t)t;   // entry within the segment
+        const bool have = i < cnt[sg];
+        const uint32_t k = sg * Q.segcap + i;
         uint32_t e = 0;
         RayState st;
         bool live = false;
         S.of[t] = 0;
 #pragma unroll
         for (int q = 0; q < 6; ++q) S.ob[q][t] = 0.0f;
-        if (k < cnt) {
+        if (have) {
             e = Q.tag[k];
             live = trace_init(Q.x[k], Q.y[k], Q.dx[k], Q.dy[k], Q.dz[k], Q.lam[k], st);
             if (!live) S.of[t] = (uint8_t)st.flags;
         }
         nint += trace_block_states<CAUCHY, kQBlock>(M.L, M.pi, M.pj, live, st, S);
         __syncthreads();
-        if (k < cnt) {
+        if (have) {
             const uint32_t r = e & ~kOutsideBit;
             const float o[6] = {S.ob[0][t], S.ob[1][t], S.ob[2][t], S.ob[3][t], S.ob[4][t], S.ob[5][t]};
             store_out(out, r, o, S.of[t] | LT_FLAG_TRACED | ((e & kOutsideBit) ? LT_FLAG_OUTSIDE : 0u));
@@ -551,31 +574,32 @@ lt_status scratch_pool(cudaMemPool_t* pool)
 TraceQueue trace_queue_at(void* scratch, size_t n)
 {
     char* p = static_cast<char*>(scratch);
-    const size_t cap = (n + 63) & ~(size_t)63;
+    const size_t segcap = query_segcap(n), cap = (size_t)kQSegs * segcap;
     TraceQueue Q;
     Q.count = reinterpret_cast<uint32_t*>(p);
+    Q.segcap = (uint32_t)segcap;
     float** fq[6] = {&Q.x, &Q.y, &Q.dx, &Q.dy, &Q.dz, &Q.lam};
-    for (int q = 0; q < 6; ++q) *fq[q] = reinterpret_cast<float*>(p + 256 + (size_t)q * cap * 4);
-    Q.tag = reinterpret_cast<uint32_t*>(p + 256 + 6 * cap * 4);
+    for (int q = 0; q < 6; ++q) *fq[q] = reinterpret_cast<float*>(p + kQHeaderBytes + (size_t)q * cap * 4);
+    Q.tag = reinterpret_cast<uint32_t*>(p + kQHeaderBytes + 6 * cap * 4);
     return Q;
 }
 
 lt_status launch_query_with(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
                             int mode, const TraceQueue& Q, cudaStream_t st)
 {
-    const unsigned blocks = (n + kQBlock - 1) / kQBlock;
+    const unsigned blocks = (n + kQTile - 1) / kQTile;
     const bool table = mode == LT_QUERY_TABLE;
     const void* trace = map->cauchy ? (const void*)map_trace_kernel<true> : (const void*)map_trace_kernel<false>;
     const unsigned gt = persistent_blocks(trace, kQBlock, n, 32);
-    LT_CUDA_TRY(cudaMemsetAsync(Q.count, 0, 2 * sizeof(uint32_t), st));
+    LT_CUDA_TRY(cudaMemsetAsync(Q.count, 0, kQHeaderBytes, st));
     {
         ProfScope prof("map_query_kernel", st);
         if (map->cauchy) {
-            if (table) map_query_kernel<LT_QUERY_TABLE, true><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, Q);
-            else map_query_kernel<LT_QUERY_NO_MASK, true><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, Q);
+            if (table) map_query_kernel<LT_QUERY_TABLE, true><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, Q);
+            else map_query_kernel<LT_QUERY_NO_MASK, true><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, Q);
         } else {
-            if (table) map_query_kernel<LT_QUERY_TABLE, false><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, Q);
-            else map_query_kernel<LT_QUERY_NO_MASK, false><<<blocks, kQBlock, 0, st>>>(map->dev, in, out, n, Q);
+            if (table) map_query_kernel<LT_QUERY_TABLE, false><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, Q);
+            else map_query_kernel<LT_QUERY_NO_MASK, false><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, Q);
         }
         LT_CUDA_TRY(cudaGetLastError());
     }
@@ -970,8 +994,8 @@ lt_status lt_map_load(const char* path, lt_map** out)
 // ---------------------------------------------------------------- allocation-free query
 
 // The trace queue of lt_query_noalloc (layout of trace_queue_at for
-// LT_NOALLOC_MAX_RAYS rays: two counters padded to 256 bytes, then 28 bytes
-// per ray).  A file-scope device array: every device that loads the library
+// LT_NOALLOC_MAX_RAYS rays: 8,448 bytes of counters, then 28 bytes per
+// ray).  A file-scope device array: every device that loads the library
 // holds it until the process exits.
 namespace {
 constexpr size_t kNoallocQueueBytes = query_scratch_bytes(LT_NOALLOC_MAX_RAYS);

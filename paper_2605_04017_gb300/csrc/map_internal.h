@@ -11,7 +11,7 @@ enum { LT_CELL_INVALID = 0, LT_CELL_VALID = 1, LT_CELL_BOUNDARY = 2 };
 
 namespace lt {
 
-// The map as the kernels see it (a __grid_constant__ parameter, ~2 KB):
+// The map as the kernels see it (a __grid_constant__ parameter, ~3 KB):
 // the lens for the fallback tracer, the path, the FP32 lattice constants and
 // the device tables.  Node strides: (x, y, s_x, s_y, lambda) row-major,
 // lambda fastest; cell strides likewise over res - 1.
@@ -26,16 +26,27 @@ struct MapDev {
 };
 
 // The map query's trace queue: per queued ray its entrance ray (structure of
-// arrays) and its index (bit 31 set: outside the lattice box); count[0]
-// counts queued rays, count[1] the 256-ray chunks the tracer has taken.
+// arrays) and its index (bit 31 set: outside the lattice box).  The queue is
+// split into kQSegs segments of segcap entries, block b of the query kernel
+// appending to segment b % kQSegs, so that the appends' atomics spread over
+// kQSegs counters in separate 128-byte lines instead of one hot address:
+// count[s * kQCountStride] counts segment s, count[kQSegs * kQCountStride]
+// the 256-ray chunks the tracer has taken.
+constexpr int kQSegs = 64;
+constexpr int kQCountStride = 32;
+constexpr size_t kQHeaderBytes = (kQSegs + 1) * kQCountStride * 4 + 128;   // 8,448 bytes
 struct TraceQueue {
     float *x, *y, *dx, *dy, *dz, *lam;
     uint32_t* tag;
     uint32_t* count;
+    uint32_t segcap;
 };
-// scratch bytes of the queue for n rays: the counters' 256 bytes, then 7
-// arrays of n (rounded up to 64) words
-constexpr size_t query_scratch_bytes(size_t n) { return 256 + 7 * 4 * ((n + 63) & ~(size_t)63); }
+constexpr int kQTile = 256;   // rays per block of the query kernel
+// entries per segment for n rays
+constexpr size_t query_segcap(size_t n) { return ((n + kQTile - 1) / kQTile + kQSegs - 1) / kQSegs * kQTile; }
+// scratch bytes of the queue for n rays: the counters, then 7 arrays of
+// kQSegs * segcap words
+constexpr size_t query_scratch_bytes(size_t n) { return kQHeaderBytes + 7 * 4 * kQSegs * query_segcap(n); }
 // the queue laid out in `scratch` (256-byte aligned, query_scratch_bytes(n))
 TraceQueue trace_queue_at(void* scratch, size_t n);
 
