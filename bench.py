@@ -175,24 +175,27 @@ def timed_steps(step, steps, warmup, flush, stream, on_timed_start=None):
     return [a.elapsed_time(b) for a, b in evs]
 
 
-def kernel_roofline(name, prof, peaks, units_bytes=None, flops_per_work=None):
+def kernel_roofline(name, prof, peaks, steps, units_bytes=None, flops_per_work=None):
+    """Roofline of one kernel over the timed steps: `units_bytes` (or the
+    counted work x flops_per_work) of one step over the kernel's summed
+    CUDA-event time per step (a step may launch it several times)."""
     launches, ms, work = prof[name]
-    avg_s = ms / launches * 1e-3
+    step_s = ms / steps * 1e-3
+    base = {"kernel": name, "launches_per_step": round(launches / steps, 2),
+            "kernel_ms_per_step": round(ms / steps, 5)}
     if units_bytes is not None:
-        ach = units_bytes / avg_s / 1e9
-        return {"kernel": name, "bound": "hbm", "achieved": round(ach, 1),
+        ach = units_bytes / step_s / 1e9
+        return {**base, "bound": "hbm", "achieved": round(ach, 1),
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4),
                 "peak_src": peaks["src"] + " (hbm_gbs, burst copy)",
-                "algorithmic_bytes_per_launch": int(units_bytes),
-                "avg_launch_ms": round(ms / launches, 5)}
-    flops = work / launches * flops_per_work
-    ach = flops / avg_s / 1e12
+                "algorithmic_bytes_per_step": int(units_bytes)}
+    flops = work / steps * flops_per_work
+    ach = flops / step_s / 1e12
     peak = fp32_peak_tflops(peaks["sm_max_mhz"])
-    return {"kernel": name, "bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 1),
+    return {**base, "bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 1),
             "unit": "TFLOP/s", "frac": round(ach / peak, 4),
             "peak_src": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % peaks["sm_max_mhz"],
-            "interactions_per_launch": int(work / launches),
-            "flops_per_interaction": flops_per_work, "avg_launch_ms": round(ms / launches, 5)}
+            "interactions_per_step": int(work / steps), "flops_per_interaction": flops_per_work}
 
 
 def run_ours(args):
@@ -279,15 +282,15 @@ def run_ours(args):
     table_bytes = mstats["n_nodes"] * 24 + (mstats["n_cells"] + 15) // 16 * 4
     q_bytes = n * 24 + (n - n_fb) * 25 + n_fb * 4 + table_bytes
     kernels = {
-        "map_query_kernel": kernel_roofline("map_query_kernel", pq, peaks, units_bytes=q_bytes),
-        "map_trace_kernel": kernel_roofline("map_trace_kernel", pq, peaks,
+        "map_query_kernel": kernel_roofline("map_query_kernel", pq, peaks, args.steps, units_bytes=q_bytes),
+        "map_trace_kernel": kernel_roofline("map_trace_kernel", pq, peaks, args.steps,
                                             flops_per_work=FLOPS_PER_INTERACTION),
-        "trace_kernel": kernel_roofline("trace_kernel", pt, peaks,
+        "trace_kernel": kernel_roofline("trace_kernel", pt, peaks, args.steps,
                                         flops_per_work=FLOPS_PER_INTERACTION),
     }
-    kernels["map_trace_kernel"]["traced_rays_per_launch"] = n_fb
+    kernels["map_trace_kernel"]["traced_rays_per_step"] = n_fb
     # the roofline reported is that of the step's longer kernel
-    dom = max(("map_query_kernel", "map_trace_kernel"), key=lambda k: kernels[k]["avg_launch_ms"])
+    dom = max(("map_query_kernel", "map_trace_kernel"), key=lambda k: kernels[k]["kernel_ms_per_step"])
     roof = dict(kernels[dom])
     tr = NCU_TRAFFIC.get(dom)
     roof["traffic"] = (tr["bytes_per_ray"] * n if tr and tr["hash"] == src_hash() else None)

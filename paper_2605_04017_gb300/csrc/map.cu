@@ -326,32 +326,9 @@ struct __align__(16) GatherItem {
     float pad;
 };
 
-// One gather's weighted sum: lane (q, part) weights its 16-byte pieces of the
-// lower (v0) and upper (v1) dimension-0 corner by the product of its corner's
-// factors; lanes differing in bit 4 swap halves of the four sums, bit 3
-// swaps quarters, bits 2 and 1 are summed as they are, leaving component c
-// in lanes whose bits 1-2 are clear, which write it to ob[e.slot * kObStride
-// + c] (a stride of 7 words puts the six writers in six banks).
+// Row stride (words) of a warp's result rows in shared memory: 7 puts a
+// ray's six outputs, and the rows of eight rays, in distinct banks.
 constexpr int kObStride = 7;
-__device__ __forceinline__ void gather_sum(const GatherItem& e, float4 v0, float4 v1, bool c1, bool c2,
-                                           bool c3, bool upper, bool u4, bool u3, bool writer, int comp,
-                                           float* ob)
-{
-    const unsigned full = 0xffffffffu;
-    const float w = ((c1 ? e.f[1] : 1.0f - e.f[1]) * (c2 ? e.f[2] : 1.0f - e.f[2])) *
-                    ((c3 ? e.f[3] : 1.0f - e.f[3]) * (upper ? e.f[4] : 1.0f - e.f[4]));
-    const float w1 = w * e.f[0], w0 = w * (1.0f - e.f[0]);
-    const float ax = fmaf(w1, v1.x, w0 * v0.x), ay = fmaf(w1, v1.y, w0 * v0.y);
-    const float az = fmaf(w1, v1.z, w0 * v0.z), aw = fmaf(w1, v1.w, w0 * v0.w);
-    float k0 = u4 ? az : ax, k1 = u4 ? aw : ay;
-    k0 += __shfl_xor_sync(full, u4 ? ax : az, 16);
-    k1 += __shfl_xor_sync(full, u4 ? ay : aw, 16);
-    float kk = u3 ? k1 : k0;
-    kk += __shfl_xor_sync(full, u3 ? k0 : k1, 8);
-    kk += __shfl_xor_sync(full, kk, 4);
-    kk += __shfl_xor_sync(full, kk, 2);
-    if (writer) ob[e.slot * kObStride + comp] = kk;
-}
 
 // The map query runs as two kernels.
 // map_query_kernel: each warp answers 32 consecutive rays on its own (no
@@ -361,15 +338,12 @@ __device__ __forceinline__ void gather_sum(const GatherItem& e, float4 v0, float
 //     BOUNDARY cells and rays outside the lattice box go to the launch's
 //     trace queue (entrance ray and index, bit 31 set for an outside ray;
 //     one atomic per warp on its block's segment counter).
-//  2. The warp gathers its queued rays two at a time (four 16-byte loads
-//     per lane in flight).  A gather is warp-cooperative: lane (q, part)
-//     loads 16 bytes -- part 0/1: the two halves of the lower-lambda node
-//     record, 2/3: of the upper one -- of corner pair q (q = the corner bits
-//     of dimensions 1-3) for dimension-0 corner 0 and 1, so each warp load
-//     reads eight whole 64-byte pairs.  Each lane weights its own values
-//     (the lambda factor included), and a transposed butterfly (5 shuffles)
-//     leaves component c of the sum in lane 8c (x, y, dx, dy) or 8c + 1
-//     (dz, I).
+//  2. The warp gathers its queued rays eight at a time, a quad of lanes per
+//     ray: each lane loads its 16-byte piece of the cell's 16 lambda pairs
+//     (one 64-byte pair per quad and warp load, so each load instruction
+//     reads eight whole pairs), weights it by the corner's multilinear
+//     factor (the lambda factor included) and sums in registers; one
+//     shuffle stage adds the quad's lower- and upper-lambda halves.
 //  3. Each lane writes its own ray (coalesced) unless it was queued for the
 //     tracer; interpolated directions are renormalised there.
 // map_trace_kernel, a persistent grid, then traces the queue with the exact
@@ -377,7 +351,6 @@ __device__ __forceinline__ void gather_sum(const GatherItem& e, float4 v0, float
 // of BOUNDARY cells die at every depth of the lens), and writes each result
 // at its ray's index.
 constexpr int kQWarps = kQTile / 32;
-constexpr int kGatherBatch = 2;
 
 template <int MODE, bool CAUCHY>
 __global__ void __launch_bounds__(kQTile)
@@ -443,27 +416,54 @@ map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out,
     }
     __syncwarp();
 
-    // warp-cooperative gathers, kGatherBatch at a time
-    const int part = lane & 3, q = lane >> 2;
-    const bool c1 = (q >> 2) & 1, c2 = (q >> 1) & 1, c3 = q & 1, upper = (part & 2) != 0;
-    const uint32_t loff = (c1 ? M.stride[1] : 0u) + (c2 ? M.stride[2] : 0u) + (c3 ? M.stride[3] : 0u);
-    const uint32_t s0 = M.stride[0];
+    // gathers, eight at a time: quad g of lanes (lane >> 2) interpolates
+    // queued ray g0 + g, lane part (lane & 3) its 16-byte piece of every
+    // lambda pair (0/1: the halves of the lower-lambda record, 2/3: of the
+    // upper one), summing the 16 pairs of (x, y, s_x, s_y) corners in
+    // registers; a shuffle adds the lower and upper halves.
+    const int part = lane & 3;
+    const bool upper = (part & 2) != 0;
+    const uint32_t s0 = M.stride[0], s1 = M.stride[1], s2 = M.stride[2], s3 = M.stride[3];
     const float4* __restrict__ node4 = reinterpret_cast<const float4*>(M.node);
-    const bool u4 = (lane & 16) != 0, u3 = (lane & 8) != 0;
-    const bool writer = (lane & 6) == 0 && !((lane & 1) && u4);
-    const int comp = (lane & 1) ? 4 + (u3 ? 1 : 0) : (u4 ? 2 : 0) + (u3 ? 1 : 0);
 #pragma unroll 1
-    for (int g = 0; g < nv; g += kGatherBatch) {
-        float4 v0[kGatherBatch], v1[kGatherBatch];
+    for (int g0 = 0; g0 < nv; g0 += 8) {
+        const int gi = g0 + (lane >> 2);
+        const bool act = gi < nv;
+        const GatherItem e = gq[min(gi, nv - 1)];
+        const float fl = upper ? e.f[4] : 1.0f - e.f[4];
+        const float w1a = e.f[0], w0a = 1.0f - e.f[0];
+        const float4* __restrict__ p = node4 + (size_t)e.base * 2 + part;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (act) {
 #pragma unroll
-        for (int k = 0; k < kGatherBatch; ++k) {
-            const uint32_t nb = gq[min(g + k, nv - 1)].base + loff;
-            v0[k] = __ldg(node4 + (size_t)nb * 2 + part);
-            v1[k] = __ldg(node4 + (size_t)(nb + s0) * 2 + part);
+            for (int qq = 0; qq < 8; ++qq) {
+                const uint32_t off = ((qq & 4) ? s1 : 0u) + ((qq & 2) ? s2 : 0u) + ((qq & 1) ? s3 : 0u);
+                const float4 a = __ldg(p + (size_t)off * 2);
+                const float4 b = __ldg(p + (size_t)(off + s0) * 2);
+                const float wq = (((qq & 4) ? e.f[1] : 1.0f - e.f[1]) * ((qq & 2) ? e.f[2] : 1.0f - e.f[2])) *
+                                 (((qq & 1) ? e.f[3] : 1.0f - e.f[3]) * fl);
+                const float w1 = wq * w1a, w0 = wq * w0a;
+                acc.x = fmaf(w1, b.x, fmaf(w0, a.x, acc.x));
+                acc.y = fmaf(w1, b.y, fmaf(w0, a.y, acc.y));
+                acc.z = fmaf(w1, b.z, fmaf(w0, a.z, acc.z));
+                acc.w = fmaf(w1, b.w, fmaf(w0, a.w, acc.w));
+            }
         }
-#pragma unroll
-        for (int k = 0; k < kGatherBatch; ++k)
-            if (g + k < nv) gather_sum(gq[g + k], v0[k], v1[k], c1, c2, c3, upper, u4, u3, writer, comp, ob);
+        acc.x += __shfl_xor_sync(full, acc.x, 2);
+        acc.y += __shfl_xor_sync(full, acc.y, 2);
+        acc.z += __shfl_xor_sync(full, acc.z, 2);
+        acc.w += __shfl_xor_sync(full, acc.w, 2);
+        if (act && part == 0) {
+            float* o = ob + e.slot * kObStride;
+            o[0] = acc.x;
+            o[1] = acc.y;
+            o[2] = acc.z;
+            o[3] = acc.w;
+        } else if (act && part == 1) {
+            float* o = ob + e.slot * kObStride;
+            o[4] = acc.x;
+            o[5] = acc.y;
+        }
     }
     __syncwarp();
 
@@ -584,32 +584,46 @@ TraceQueue trace_queue_at(void* scratch, size_t n)
     return Q;
 }
 
-lt_status launch_query_with(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
-                            int mode, const TraceQueue& Q, cudaStream_t st)
+// the classify-and-gather kernel on `st` (the queue's counters already cleared)
+static lt_status launch_classify(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
+                                 int mode, const TraceQueue& Q, cudaStream_t st)
 {
     const unsigned blocks = (n + kQTile - 1) / kQTile;
     const bool table = mode == LT_QUERY_TABLE;
-    const void* trace = map->cauchy ? (const void*)map_trace_kernel<true> : (const void*)map_trace_kernel<false>;
-    const unsigned gt = persistent_blocks(trace, kQBlock, n, 32);
-    LT_CUDA_TRY(cudaMemsetAsync(Q.count, 0, kQHeaderBytes, st));
-    {
-        ProfScope prof("map_query_kernel", st);
-        if (map->cauchy) {
-            if (table) map_query_kernel<LT_QUERY_TABLE, true><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, Q);
-            else map_query_kernel<LT_QUERY_NO_MASK, true><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, Q);
-        } else {
-            if (table) map_query_kernel<LT_QUERY_TABLE, false><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, Q);
-            else map_query_kernel<LT_QUERY_NO_MASK, false><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, Q);
-        }
-        LT_CUDA_TRY(cudaGetLastError());
+    ProfScope prof("map_query_kernel", st);
+    if (map->cauchy) {
+        if (table) map_query_kernel<LT_QUERY_TABLE, true><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, Q);
+        else map_query_kernel<LT_QUERY_NO_MASK, true><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, Q);
+    } else {
+        if (table) map_query_kernel<LT_QUERY_TABLE, false><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, Q);
+        else map_query_kernel<LT_QUERY_NO_MASK, false><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, Q);
     }
-    {
-        ProfScope prof("map_trace_kernel", st);
-        if (map->cauchy) map_trace_kernel<true><<<gt, kQBlock, 0, st>>>(map->dev, out, Q, prof.work());
-        else map_trace_kernel<false><<<gt, kQBlock, 0, st>>>(map->dev, out, Q, prof.work());
-        LT_CUDA_TRY(cudaGetLastError());
-    }
+    LT_CUDA_TRY(cudaGetLastError());
     return LT_OK;
+}
+
+// the tracer over the queue of a classify launch of n rays, on `st`
+static lt_status launch_queue_trace(const lt_map* map, const RaysOutDev& out, uint32_t n, const TraceQueue& Q,
+                                    cudaStream_t st)
+{
+    const void* trace = map->cauchy ? (const void*)map_trace_kernel<true> : (const void*)map_trace_kernel<false>;
+    // resident blocks, but no more than a quarter of the rays could keep busy
+    // (blocks take chunks from a counter, so any grid traces the whole queue)
+    const unsigned gt = persistent_blocks(trace, kQBlock, ((size_t)n + 3) / 4, 32);
+    ProfScope prof("map_trace_kernel", st);
+    if (map->cauchy) map_trace_kernel<true><<<gt, kQBlock, 0, st>>>(map->dev, out, Q, prof.work());
+    else map_trace_kernel<false><<<gt, kQBlock, 0, st>>>(map->dev, out, Q, prof.work());
+    LT_CUDA_TRY(cudaGetLastError());
+    return LT_OK;
+}
+
+lt_status launch_query_with(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
+                            int mode, const TraceQueue& Q, cudaStream_t st)
+{
+    LT_CUDA_TRY(cudaMemsetAsync(Q.count, 0, kQHeaderBytes, st));
+    lt_status s = launch_classify(map, in, out, n, mode, Q, st);
+    if (s != LT_OK) return s;
+    return launch_queue_trace(map, out, n, Q, st);
 }
 
 lt_status launch_query(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,

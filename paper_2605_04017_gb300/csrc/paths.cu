@@ -190,8 +190,9 @@ extern "C" lt_status lt_trace_paths(const lt_lens* L, const lt_rays_in* in, cons
     ProfScope prof("trace_paths_kernel", st);
     for (int p0 = 0; p0 < n_paths && s == LT_OK; p0 += per_wave) {
         const int np = std::min(per_wave, n_paths - p0);
-        if (cudaMemsetAsync(Q.count, 0, 4, st) != cudaSuccess) {
-            s = cuda_fail(cudaGetLastError(), "lt_trace_paths: memset");
+        const cudaError_t em = cudaMemsetAsync(Q.count, 0, 4, st);
+        if (em != cudaSuccess) {
+            s = cuda_fail(em, "lt_trace_paths: memset");
             break;
         }
         const dim3 grid((unsigned)((n + kPathsBlock - 1) / kPathsBlock), (unsigned)np);
@@ -203,7 +204,8 @@ extern "C" lt_status lt_trace_paths(const lt_lens* L, const lt_rays_in* in, cons
             paths_front_kernel<false><<<grid, kPathsBlock, 0, st>>>(L->dev, P, p0, din, lam_stride, dout, nn, Q, prof.work());
             paths_rest_kernel<false><<<gr, kPathsBlock, 0, st>>>(L->dev, P, Q, dout, prof.work());
         }
-        if (cudaGetLastError() != cudaSuccess) s = cuda_fail(cudaGetLastError(), "lt_trace_paths: launch");
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) s = cuda_fail(e, "lt_trace_paths: launch");
     }
     cudaFreeAsync(buf, st);
     return s;

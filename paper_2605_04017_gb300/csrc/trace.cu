@@ -167,7 +167,8 @@ lt_status launch_trace(const lt_lens* L, int pi, int pj, const RaysInDev& in,
         RaysOutDev b{out.x + off, out.y + off, out.dx + off, out.dy + off, out.dz + off,
                      out.I + off, out.flags + off};
         ProfScope prof("trace_kernel", st);
-        if (cudaMemsetAsync(Q.count, 0, 4, st) != cudaSuccess) { s = cuda_fail(cudaGetLastError(), "lt_trace: memset"); break; }
+        const cudaError_t em = cudaMemsetAsync(Q.count, 0, 4, st);
+        if (em != cudaSuccess) { s = cuda_fail(em, "lt_trace: memset"); break; }
         const unsigned g = (m + kTraceBlock - 1) / kTraceBlock;
         // the rest kernel's grid: resident blocks, no more than the wave could need
         const unsigned gr = persistent_blocks(rest, kTraceBlock, m, 32);
@@ -178,7 +179,8 @@ lt_status launch_trace(const lt_lens* L, int pi, int pj, const RaysInDev& in,
             trace_front_kernel<false><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, Q, prof.work());
             trace_rest_kernel<false><<<gr, kTraceBlock, 0, st>>>(L->dev, pi, pj, Q, b, prof.work());
         }
-        if (cudaGetLastError() != cudaSuccess) s = cuda_fail(cudaGetLastError(), "lt_trace: launch");
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) s = cuda_fail(e, "lt_trace: launch");
     }
     cudaFreeAsync(buf, st);
     return s;
