@@ -507,6 +507,16 @@ def bench_flares(args, stream, flush, peaks):
     avg_s = ms / launches * 1e-3
     useful = work / launches * FLOPS_PER_INTERACTION / avg_s / 1e12
     peak = fp32_peak_tflops(peaks["sm_max_mhz"])
+    del po
+    torch.cuda.empty_cache()
+    # forward light tracing of the same rays onto a 24 mm, 512 x 512 sensor
+    # (Eq. 8; per-sample average): the same trace with the deposits fused in
+    W = 512
+    img = torch.zeros((1, W, W), dtype=torch.float32, device="cuda")
+    rs, prof_s = time_kernel(lambda: lt.splat_paths(lens, d.inp, lam, n, ids, n, W, W, 24.0 / W, img,
+                                                    weight=1.0 / n, stream=stream),
+                             "splat", args, flush, stream, n * P, lt)
+    sl, sms, swork = prof_s["splat_paths_kernel"]
     return {"workload": "11-surface lens, 56 paths (main + 55 ghosts) x 1,048,576 rays, lambda per path",
             "rays_per_s": r["rays_per_s"], "ms_per_step": r["ms_per_step"], "p99_batch_ms": r["p99_batch_ms"],
             "valid_rays_per_launch": int(counts.sum()),
@@ -514,7 +524,12 @@ def bench_flares(args, stream, flush, peaks):
             "roofline": {"kernel": "trace_paths_kernel", "bound": "alu", "achieved": round(useful, 2),
                          "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(useful / peak, 4),
                          "interactions_per_launch": int(work / launches),
-                         "note": "useful FP32 flop: interactions actually executed x 89"}}
+                         "note": "useful FP32 flop: interactions actually executed x 89"},
+            "splat": {"workload": "the same 56 x 1,048,576 rays traced and splatted onto a 24 mm 512 x 512 "
+                                  "sensor (tent filter, G = exit d_z, weight 1/n)",
+                      "rays_per_s": rs["rays_per_s"], "ms_per_step": rs["ms_per_step"],
+                      "p99_batch_ms": rs["p99_batch_ms"],
+                      "useful_tflops": round(swork / sl * FLOPS_PER_INTERACTION / (sms / sl * 1e-3) / 1e12, 2)}}
 
 
 def bench_serving(args, peaks, seconds=10.0, warm=1.0, rate=2000.0):

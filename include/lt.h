@@ -199,6 +199,34 @@ lt_status lt_trace_paths(const lt_lens* lens, const lt_rays_in* in, const float*
                          size_t lambda_stride, const int32_t* path_ids, int32_t n_paths,
                          const lt_paths_out* out, size_t n, lt_stream stream);
 
+/* The sensor of forward light tracing: a width x height grid of square
+ * pixels of side pixel_mm on the image plane, centred on the axis (pixel
+ * (i, j) has its centre at ((i + 0.5 - width / 2) pixel_mm,
+ * (j + 0.5 - height / 2) pixel_mm)), row-major images of floats. */
+typedef struct {
+    int32_t width, height;       /* pixels, 1..65536 */
+    double pixel_mm;             /* pixel side, > 0 */
+    float weight;                /* factor on every deposit (1 / n: the per-sample average) */
+    int32_t per_path;            /* 0: one image, all paths summed; 1: one image per path */
+} lt_sensor;
+
+/* Forward light tracing onto the sensor (Sec. 3, Eq. 8): trace the n
+ * entrance rays along n_paths paths exactly as lt_trace_paths does (same
+ * waves, kernels and per-ray arithmetic) and add, for every ray that reaches
+ * the image plane, I_out * G * h(x_out - c) * weight to each pixel c, with
+ * G = d_z of the exit direction (its cosine to the sensor normal) and h the
+ * tent (bilinear) pixel filter of one pixel radius -- the paper names no
+ * filter.  Deposits are FP32 atomic adds (their order, and so the last bits
+ * of a pixel, varies between runs).  image: DEVICE float[per_path ? n_paths
+ * : 1][height][width], 16-byte aligned, accumulated into (the caller clears
+ * it).  path_ids, lambda_nm and lambda_stride as lt_trace_paths.  Rays that
+ * land outside the sensor deposit nothing there.  Errors: LT_EINVAL (NULL or
+ * misaligned pointer, bad sensor, n_paths < 1 or > 1024, bad path id,
+ * n >= 2^32), LT_ENOMEM (queue allocation), LT_ECUDA. */
+lt_status lt_splat_paths(const lt_lens* lens, const lt_rays_in* in, const float* lambda_nm,
+                         size_t lambda_stride, const int32_t* path_ids, int32_t n_paths, size_t n,
+                         const lt_sensor* sensor, float* image, lt_stream stream);
+
 /* ------------------------------------------------------------------ maps */
 
 /*

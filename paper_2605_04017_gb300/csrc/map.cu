@@ -487,8 +487,10 @@ map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out,
 // blocks take 256-ray chunks of the queue's segments from a counter until
 // none is left (chunk c of the launch: segment s with cum[s] <= c <
 // cum[s + 1], cum the prefix sum of the segments' chunk counts).
+// Six resident blocks per SM (40 registers, a few spilled): measured faster
+// than four at 60 registers or five at 48.
 template <bool CAUCHY>
-__global__ void __launch_bounds__(kQBlock)
+__global__ void __launch_bounds__(kQBlock, 6)
 map_trace_kernel(const __grid_constant__ MapDev M, RaysOutDev out, TraceQueue Q, unsigned long long* work)
 {
     __shared__ TraceSmem<kQBlock> S;

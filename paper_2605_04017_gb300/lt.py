@@ -266,6 +266,30 @@ def trace_paths(lens: Lens, inp: Sequence, lam, lam_stride: int, path_ids, out, 
                                _stream_handle(stream)))
 
 
+class c_sensor(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("pixel_mm", ctypes.c_double),
+                ("weight", ctypes.c_float), ("per_path", ctypes.c_int32)]
+
+
+def splat_paths(lens: Lens, inp: Sequence, lam, lam_stride: int, path_ids, n: int, width: int,
+                height: int, pixel_mm: float, image, weight: float = 1.0, per_path: bool = False,
+                stream=None) -> None:
+    """lt_splat_paths: forward light tracing of n rays along the given paths
+    onto a sensor image (device float tensor [n_images, height, width],
+    accumulated into)."""
+    import numpy as np
+    L = lib()
+    L.lt_splat_paths.restype = ctypes.c_int
+    L.lt_splat_paths.argtypes = [ctypes.c_void_p, ctypes.POINTER(c_rays_in), ctypes.c_void_p, ctypes.c_size_t,
+                                 ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t, ctypes.POINTER(c_sensor),
+                                 ctypes.c_void_p, ctypes.c_void_p]
+    ids = np.ascontiguousarray(path_ids, np.int32)
+    ri = rays_in(*inp)
+    sen = c_sensor(width, height, pixel_mm, weight, 1 if per_path else 0)
+    check(L.lt_splat_paths(lens.handle, ctypes.byref(ri), _ptr(lam), lam_stride, ids.ctypes.data, len(ids), n,
+                           ctypes.byref(sen), _ptr(image), _stream_handle(stream)))
+
+
 # ------------------------------------------------------------------ maps
 
 QUERY_TABLE = 0

@@ -138,6 +138,29 @@ def test_trace_paths_argument_errors_without_gpu():
     assert f(L.handle, ctypes.byref(ri), None, 0, ids, 2, ctypes.byref(po), 0, None) == lt.LT_EINVAL
 
 
+def test_splat_paths_argument_errors_without_gpu():
+    L = lt.Lens(w.singlet_lens())
+    ri = lt.c_rays_in()
+    ids = (ctypes.c_int32 * 2)(0, 1)
+    sen = lt.c_sensor(64, 48, 0.05, 1.0, 0)
+    f = lt.lib().lt_splat_paths
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(lt.c_rays_in), ctypes.c_void_p, ctypes.c_size_t,
+                  ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t, ctypes.POINTER(lt.c_sensor),
+                  ctypes.c_void_p, ctypes.c_void_p]
+    img = 256
+    assert f(L.handle, ctypes.byref(ri), None, 0, ids, 2, 0, None, img, None) == lt.LT_EINVAL
+    bad = lt.c_sensor(0, 48, 0.05, 1.0, 0)
+    assert f(L.handle, ctypes.byref(ri), None, 0, ids, 2, 0, ctypes.byref(bad), img, None) == lt.LT_EINVAL
+    assert "sensor" in lt.last_error()
+    bad = lt.c_sensor(64, 48, 0.0, 1.0, 0)
+    assert f(L.handle, ctypes.byref(ri), None, 0, ids, 2, 0, ctypes.byref(bad), img, None) == lt.LT_EINVAL
+    nopath = (ctypes.c_int32 * 1)(2)          # the singlet has paths 0 and 1 only
+    assert f(L.handle, ctypes.byref(ri), None, 0, nopath, 1, 0, ctypes.byref(sen), img, None) == lt.LT_EINVAL
+    # n = 0 deposits nothing and succeeds without touching the device
+    assert f(L.handle, ctypes.byref(ri), None, 0, ids, 2, 0, ctypes.byref(sen), img, None) == lt.LT_OK
+
+
 def test_server_entry_points_without_gpu():
     import torch
     t = ctypes.c_uint64()
