@@ -301,6 +301,8 @@ enum {
  * carry LT_FLAG_TRACED) and writes their results.  The queue (28 bytes per
  * ray) comes from the library's stream-ordered memory pool, which keeps
  * freed blocks for reuse, so steady-state calls do not reach cudaMalloc.
+ * Batches of at most 2^18 rays run as one kernel whose blocks trace their
+ * own queued rays (no queue, no pool); the results are the same either way.
  * Errors as lt_trace; LT_ENOMEM if the queue cannot be had. */
 lt_status lt_query(const lt_map* map, const lt_rays_in* in, const float* lambda_nm,
                    const lt_rays_out* out, size_t n, int32_t mode, lt_stream stream);

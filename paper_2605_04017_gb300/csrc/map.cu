@@ -352,75 +352,70 @@ constexpr int kObStride = 7;
 // at its ray's index.
 constexpr int kQWarps = kQTile / 32;
 
-template <int MODE, bool CAUCHY>
-__global__ void __launch_bounds__(kQTile)
-map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out, uint32_t n, TraceQueue Q)
+// A lane's ray after classification (step 1 of map_query_kernel).
+struct Classified {
+    bool ip, tr;                // VALID cell (to interpolate); BOUNDARY or outside (to trace)
+    uint32_t tag, base;         // ray index (| kOutsideBit); node index of the cell's first corner
+    float f[5];                 // position in the cell
+    float x, y, dx, dy, dz, lam;
+};
+
+// Step 1: load ray r (if r < n) and classify it.
+template <int MODE>
+__device__ __forceinline__ Classified classify_ray(const MapDev& M, const RaysInDev& in, uint32_t n, uint32_t r)
 {
-    __shared__ GatherItem gq_all[kQWarps][32];
-    __shared__ float ob_all[kQWarps][32 * kObStride];
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    GatherItem* gq = gq_all[warp];
-    float* ob = ob_all[warp];
-    const uint32_t r = blockIdx.x * kQTile + threadIdx.x;
-    bool ip = false, tr = false;
-    uint32_t tag = r, base = 0;
-    float f[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    float x = 0.f, y = 0.f, dx = 0.f, dy = 0.f, dz = 0.f, lam = 0.f;
+    Classified c;
+    c.ip = false;
+    c.tr = false;
+    c.tag = r;
+    c.base = 0;
+#pragma unroll
+    for (int d = 0; d < 5; ++d) c.f[d] = 0.0f;
+    c.x = c.y = c.dx = c.dy = c.dz = c.lam = 0.0f;
     if (r < n) {
-        x = __ldg(in.x + r);
-        y = __ldg(in.y + r);
-        dx = __ldg(in.dx + r);
-        dy = __ldg(in.dy + r);
-        dz = __ldg(in.dz + r);
-        lam = __ldg(in.lam + r);
+        c.x = __ldg(in.x + r);
+        c.y = __ldg(in.y + r);
+        c.dx = __ldg(in.dx + r);
+        c.dy = __ldg(in.dy + r);
+        c.dz = __ldg(in.dz + r);
+        c.lam = __ldg(in.lam + r);
         uint32_t cid = 0;
-        if (!cell_and_base(M, x, y, dx, dy, dz, lam, cid, base, f)) {
-            tr = true;
-            tag |= kOutsideBit;
+        if (!cell_and_base(M, c.x, c.y, c.dx, c.dy, c.dz, c.lam, cid, c.base, c.f)) {
+            c.tr = true;
+            c.tag |= kOutsideBit;
         } else {
-            const uint32_t c = MODE == LT_QUERY_TABLE ? cell_class(M, cid) : (uint32_t)LT_CELL_VALID;
-            ip = c == LT_CELL_VALID;
-            tr = c != LT_CELL_VALID && c != LT_CELL_INVALID;
+            const uint32_t k = MODE == LT_QUERY_TABLE ? cell_class(M, cid) : (uint32_t)LT_CELL_VALID;
+            c.ip = k == LT_CELL_VALID;
+            c.tr = k != LT_CELL_VALID && k != LT_CELL_INVALID;
         }
     }
-    const unsigned lt_mask = (1u << lane) - 1u;
-    unsigned m = __ballot_sync(full, tr);
-    if (m) {
-        const int leader = __ffs(m) - 1;
-        uint32_t b = 0;
-        const uint32_t seg = blockIdx.x % kQSegs;
-        if (lane == leader) b = atomicAdd(Q.count + seg * kQCountStride, (uint32_t)__popc(m));
-        b = __shfl_sync(full, b, leader);
-        if (tr) {
-            const uint32_t k = seg * Q.segcap + b + __popc(m & lt_mask);
-            Q.x[k] = x;
-            Q.y[k] = y;
-            Q.dx[k] = dx;
-            Q.dy[k] = dy;
-            Q.dz[k] = dz;
-            Q.lam[k] = lam;
-            Q.tag[k] = tag;
-        }
-    }
-    const unsigned mv = __ballot_sync(full, ip);
+    return c;
+}
+
+// Steps 2 and 3 for a warp (all 32 lanes call it; gq and ob are the warp's
+// shared-memory list and result rows): gather the warp's VALID rays eight at
+// a time -- quad g of lanes (lane >> 2) interpolates listed ray g0 + g, lane
+// part (lane & 3) its 16-byte piece of every lambda pair (0/1: the halves of
+// the lower-lambda record, 2/3: of the upper one), summing the 16 pairs of
+// (x, y, s_x, s_y) corners in registers; a shuffle adds the lower and upper
+// halves -- then write every ray of the warp that is not to be traced.
+__device__ __forceinline__ void gather_and_write(const MapDev& M, const RaysOutDev& out, uint32_t n, uint32_t r,
+                                                 const Classified& c, GatherItem* gq, float* ob)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned mv = __ballot_sync(full, c.ip);
     const int nv = __popc(mv);
-    if (ip) {
+    if (c.ip) {
         GatherItem e;
         e.slot = (uint32_t)lane;
-        e.base = base;
+        e.base = c.base;
 #pragma unroll
-        for (int d = 0; d < 5; ++d) e.f[d] = f[d];
+        for (int d = 0; d < 5; ++d) e.f[d] = c.f[d];
         e.pad = 0.0f;
-        gq[__popc(mv & lt_mask)] = e;
+        gq[__popc(mv & ((1u << lane) - 1u))] = e;
     }
     __syncwarp();
-
-    // gathers, eight at a time: quad g of lanes (lane >> 2) interpolates
-    // queued ray g0 + g, lane part (lane & 3) its 16-byte piece of every
-    // lambda pair (0/1: the halves of the lower-lambda record, 2/3: of the
-    // upper one), summing the 16 pairs of (x, y, s_x, s_y) corners in
-    // registers; a shuffle adds the lower and upper halves.
     const int part = lane & 3;
     const bool upper = (part & 2) != 0;
     const uint32_t s0 = M.stride[0], s1 = M.stride[1], s2 = M.stride[2], s3 = M.stride[3];
@@ -466,10 +461,9 @@ map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out,
         }
     }
     __syncwarp();
-
-    if (r < n && !tr) {
+    if (r < n && !c.tr) {
         float o[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (ip) {
+        if (c.ip) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) o[k] = ob[lane * kObStride + k];
             const float n2 = fmaf(o[2], o[2], fmaf(o[3], o[3], o[4] * o[4]));
@@ -479,8 +473,97 @@ map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out,
             o[3] *= inv;
             o[4] *= inv;
         }
-        store_out(out, r, o, ip ? LT_FLAG_VALID : 0u);
+        store_out(out, r, o, c.ip ? LT_FLAG_VALID : 0u);
     }
+}
+
+template <int MODE, bool CAUCHY>
+__global__ void __launch_bounds__(kQTile)
+map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out, uint32_t n, TraceQueue Q)
+{
+    __shared__ GatherItem gq_all[kQWarps][32];
+    __shared__ float ob_all[kQWarps][32 * kObStride];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t r = blockIdx.x * kQTile + threadIdx.x;
+    const Classified c = classify_ray<MODE>(M, in, n, r);
+    const unsigned m = __ballot_sync(full, c.tr);
+    if (m) {
+        const int leader = __ffs(m) - 1;
+        uint32_t b = 0;
+        const uint32_t seg = blockIdx.x % kQSegs;
+        if (lane == leader) b = atomicAdd(Q.count + seg * kQCountStride, (uint32_t)__popc(m));
+        b = __shfl_sync(full, b, leader);
+        if (c.tr) {
+            const uint32_t k = seg * Q.segcap + b + __popc(m & ((1u << lane) - 1u));
+            Q.x[k] = c.x;
+            Q.y[k] = c.y;
+            Q.dx[k] = c.dx;
+            Q.dy[k] = c.dy;
+            Q.dz[k] = c.dz;
+            Q.lam[k] = c.lam;
+            Q.tag[k] = c.tag;
+        }
+    }
+    gather_and_write(M, out, n, r, c, gq_all[warp], ob_all[warp]);
+}
+
+// The whole query in one kernel, for small batches (fewer blocks than the
+// GPU holds at once, where the second launch and its queue cost more than
+// they save): each block classifies and gathers as map_query_kernel does,
+// lists its BOUNDARY and outside rays in shared memory, and traces them
+// itself with survivor compaction (trace_block_states).
+template <int MODE, bool CAUCHY>
+__global__ void __launch_bounds__(kQTile)
+map_query_fused_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out, uint32_t n,
+                       unsigned long long* work)
+{
+    __shared__ GatherItem gq_all[kQWarps][32];
+    __shared__ float ob_all[kQWarps][32 * kObStride];
+    __shared__ TraceSmem<kQTile> S;
+    __shared__ uint32_t tlist[kQTile];
+    __shared__ uint32_t tcount;
+    const unsigned full = 0xffffffffu;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) tcount = 0;
+    __syncthreads();
+    const uint32_t r0 = blockIdx.x * kQTile;
+    const uint32_t r = r0 + t;
+    const Classified c = classify_ray<MODE>(M, in, n, r);
+    const unsigned m = __ballot_sync(full, c.tr);
+    if (m) {
+        const int leader = __ffs(m) - 1;
+        uint32_t b = 0;
+        if (lane == leader) b = atomicAdd(&tcount, (uint32_t)__popc(m));
+        b = __shfl_sync(full, b, leader);
+        if (c.tr) tlist[b + __popc(m & ((1u << lane) - 1u))] = (uint32_t)t | (c.tag & kOutsideBit);
+    }
+    gather_and_write(M, out, n, r, c, gq_all[warp], ob_all[warp]);
+    __syncthreads();
+    const uint32_t nt = tcount;
+    if (nt == 0) return;
+    // trace the listed rays, thread k taking entry k
+    RayState st;
+    bool live = false;
+    uint32_t e = 0;
+    S.of[t] = 0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) S.ob[q][t] = 0.0f;
+    if ((uint32_t)t < nt) {
+        e = tlist[t];
+        const uint32_t rr = r0 + (e & ~kOutsideBit);
+        live = trace_init(__ldg(in.x + rr), __ldg(in.y + rr), __ldg(in.dx + rr), __ldg(in.dy + rr),
+                          __ldg(in.dz + rr), __ldg(in.lam + rr), st);
+        if (!live) S.of[t] = (uint8_t)st.flags;
+    }
+    const int nint = trace_block_states<CAUCHY, kQTile>(M.L, M.pi, M.pj, live, st, S);
+    __syncthreads();
+    if ((uint32_t)t < nt) {
+        const uint32_t rr = r0 + (e & ~kOutsideBit);
+        const float o[6] = {S.ob[0][t], S.ob[1][t], S.ob[2][t], S.ob[3][t], S.ob[4][t], S.ob[5][t]};
+        store_out(out, rr, o, S.of[t] | LT_FLAG_TRACED | ((e & kOutsideBit) ? LT_FLAG_OUTSIDE : 0u));
+    }
+    warp_add(work, (unsigned)nint);
 }
 
 // The exact tracer over the query's trace queue (see map_query_kernel):
@@ -628,9 +711,26 @@ lt_status launch_query_with(const lt_map* map, const RaysInDev& in, const RaysOu
     return launch_queue_trace(map, out, n, Q, st);
 }
 
+// Batches up to this size run as the one fused kernel.
+constexpr uint32_t kFusedMaxRays = 1u << 18;
+
 lt_status launch_query(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
                        int mode, cudaStream_t st)
 {
+    if (n <= kFusedMaxRays) {
+        const unsigned blocks = (n + kQTile - 1) / kQTile;
+        const bool table = mode == LT_QUERY_TABLE;
+        ProfScope prof("map_query_fused_kernel", st);
+        if (map->cauchy) {
+            if (table) map_query_fused_kernel<LT_QUERY_TABLE, true><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, prof.work());
+            else map_query_fused_kernel<LT_QUERY_NO_MASK, true><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, prof.work());
+        } else {
+            if (table) map_query_fused_kernel<LT_QUERY_TABLE, false><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, prof.work());
+            else map_query_fused_kernel<LT_QUERY_NO_MASK, false><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, prof.work());
+        }
+        LT_CUDA_TRY(cudaGetLastError());
+        return LT_OK;
+    }
     cudaMemPool_t pool;
     lt_status s = scratch_pool(&pool);
     if (s != LT_OK) return s;

@@ -52,8 +52,9 @@ TraceQueue trace_queue_at(void* scratch, size_t n);
 
 // The map query of n < 2^31 rays on `st`: the classify-and-gather kernel,
 // then the tracer over the rays it queued.  launch_query takes the queue from
-// the library's stream-ordered pool; launch_query_with uses the caller's
-// (its counters are cleared on `st`).
+// the library's stream-ordered pool (small batches run as one fused kernel
+// that needs no queue); launch_query_with always runs the two kernels, on the
+// caller's queue (its counters are cleared on `st`).
 lt_status launch_query(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
                        int mode, cudaStream_t st);
 lt_status launch_query_with(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
