@@ -109,6 +109,27 @@ typedef struct lt_lens lt_lens;
 lt_status lt_create_lens(const lt_prescription* p, lt_lens** out);
 void lt_destroy_lens(lt_lens* lens);
 
+/* The lens seen from its image side, for backward path tracing (Sec. 3,
+ * Eq. 9: rays leave the sensor, cross the lens in reverse along the full
+ * transmission path and go on into the scene).  The backward transport of
+ * the lens is the forward transport of its mirror image about the sensor
+ * plane z = sensor_z (absolute z of the forward lens): surface j of the new
+ * lens is forward surface S + 1 - j with negated curvature, the same clear
+ * aperture and the media shifted; the stop keeps its plane; the new lens's
+ * entrance plane is the sensor and its image plane (LT_IMAGE_ABS) the
+ * forward plane z = out_z in front of surface 1.  In its frame z' =
+ * sensor_z - z, a ray leaving the sensor at (x, y) along the forward
+ * direction (dx, dy, -dz), dz > 0, is the entrance ray (x, y, dx, dy, dz),
+ * and an exit ray (x', y', dx', dy', dz') is the forward ray at z = out_z
+ * along (dx', dy', -dz').  Every other call (lt_trace, lt_build_map,
+ * lt_mlp_train, ...) applies to the result unchanged, so the backward map of
+ * the paper's depth-of-field rendering is a map of the reversed lens.  Moving
+ * sensor_z refocuses (the paper's manual focusing).
+ * Errors: LT_EINVAL (NULL, a sensor plane not behind the last surface's cap,
+ * an output plane behind the first surface's cap, or a stop outside the two
+ * planes), or those of lt_create_lens.  The caller owns *out. */
+lt_status lt_reverse_lens(const lt_lens* lens, double sensor_z, double out_z, lt_lens** out);
+
 /* Paraxial data of a lens at lambda_nm (host, FP64): effective focal length,
  * back focal distance, and the image-plane z in use.  Any output may be NULL. */
 lt_status lt_lens_paraxial(const lt_lens* lens, double lambda_nm, double* efl, double* bfd,

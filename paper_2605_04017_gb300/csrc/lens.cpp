@@ -5,6 +5,7 @@
 // (y, n*u) marginal-ray trace in FP64: refraction n'u' = n u - y (n' - n) c,
 // transfer y' = y + t u'.  With air on both sides EFL = -y_1 / u'_S and the
 // back focal distance BFD = -y_S / u'_S.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -254,5 +255,48 @@ lt_status lt_create_lens(const lt_prescription* p, lt_lens** out)
 }
 
 void lt_destroy_lens(lt_lens* L) { delete L; }
+
+lt_status lt_reverse_lens(const lt_lens* F, double sensor_z, double out_z, lt_lens** out)
+{
+    clear_error();
+    if (!F || !out) return fail(LT_EINVAL, "lt_reverse_lens: NULL argument");
+    *out = nullptr;
+    const int S = F->S;
+    if (!std::isfinite(sensor_z) || !std::isfinite(out_z))
+        return fail(LT_EINVAL, "lt_reverse_lens: planes must be finite");
+    // the sensor lies behind the last surface's cap, the output plane in front of the first's
+    auto sag = [](double c, double a) { return c * a * a / (1.0 + std::sqrt(std::max(0.0, 1.0 - c * c * a * a))); };
+    const lt_surface& last = F->surf[S - 1];
+    const lt_surface& first = F->surf[0];
+    if (!(sensor_z > F->zv[S] + std::max(0.0, sag(last.curvature, last.aperture_r))))
+        return fail(LT_EINVAL, "lt_reverse_lens: the sensor plane must lie behind the last surface");
+    if (!(out_z <= F->zv[1] + std::min(0.0, sag(first.curvature, first.aperture_r))))
+        return fail(LT_EINVAL, "lt_reverse_lens: the output plane must lie in front of the first surface");
+    const lt_prescription& P = F->presc;
+    if (P.stop_r > 0.0 && !(F->z_stop < sensor_z && F->z_stop >= out_z))
+        return fail(LT_EINVAL, "lt_reverse_lens: the stop must lie between the output plane and the sensor");
+    lt_surface surf[LT_MAX_SURFACES];
+    for (int j = 1; j <= S; ++j) {
+        const int k = S + 1 - j;               // forward surface
+        const lt_surface& s = F->surf[k - 1];
+        surf[j - 1].curvature = -s.curvature;
+        surf[j - 1].aperture_r = s.aperture_r;
+        surf[j - 1].thickness = k >= 2 ? F->zv[k] - F->zv[k - 1] : 0.0;
+        surf[j - 1].glass_after = k >= 2 ? F->surf[k - 2].glass_after : -1;
+    }
+    lt_prescription R = P;
+    R.surfaces = surf;
+    R.glasses = F->glass;
+    R.n_glasses = F->n_glass;
+    R.entrance_gap = sensor_z - F->zv[S];
+    if (P.stop_r > 0.0) {
+        const int g = P.stop_after;            // forward gap between vertex g and g + 1
+        R.stop_after = S - g;
+        R.stop_offset = R.stop_after == 0 ? sensor_z - F->z_stop : F->zv[g + 1] - F->z_stop;
+    }
+    R.image_mode = LT_IMAGE_ABS;
+    R.image_z = sensor_z - out_z;
+    return lt_create_lens(&R, out);
+}
 
 }  // extern "C"

@@ -208,6 +208,21 @@ class Lens:
     def n_paths(self) -> int:
         return int(lib().lt_lens_n_paths(self.handle))
 
+    def reversed(self, sensor_z: float, out_z: float) -> "Lens":
+        """lt_reverse_lens: this lens seen from its image side (backward path
+        tracing), entrance plane at the forward plane z = sensor_z, image
+        plane at the forward plane z = out_z."""
+        L = lib()
+        L.lt_reverse_lens.restype = ctypes.c_int
+        L.lt_reverse_lens.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_void_p]
+        h = ctypes.c_void_p()
+        check(L.lt_reverse_lens(self.handle, sensor_z, out_z, ctypes.byref(h)))
+        r = Lens.__new__(Lens)
+        r.handle = h
+        r.S = self.S
+        r.presc = None
+        return r
+
     def paraxial(self, lam_nm: float):
         e, b, z = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         check(lib().lt_lens_paraxial(self.handle, lam_nm, ctypes.byref(e), ctypes.byref(b),

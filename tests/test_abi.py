@@ -161,6 +161,40 @@ def test_splat_paths_argument_errors_without_gpu():
     assert f(L.handle, ctypes.byref(ri), None, 0, ids, 2, 0, ctypes.byref(sen), img, None) == lt.LT_OK
 
 
+@pytest.mark.parametrize("which", ["singlet", "eleven"])
+def test_reversed_lens_matches_oracle_reversal(which):
+    """lt_reverse_lens (host code) against the oracle's own reversal: focal
+    length and image plane, for the in-focus and a refocused sensor."""
+    from oracle import reverse as R
+    p = w.singlet_lens() if which == "singlet" else w.eleven_surface_lens(oracle_accept)
+    L = lt.Lens(p)
+    zi = L.paraxial(587.6)[2]
+    for sensor_z, out_z in ((zi, 0.0), (zi + 0.6, -2.0)):
+        back = L.reversed(sensor_z, out_z)
+        ob = oracle.Lens(R.reverse_prescription(p, sensor_z, out_z, w.IMAGE_ABS))
+        for lam in (400.0, 587.6, 760.0):
+            e, b, z = back.paraxial(lam)
+            oe, obf = ob.paraxial(lam)
+            assert e == pytest.approx(oe, rel=1e-12) and b == pytest.approx(obf, rel=1e-12)
+        assert z == pytest.approx(ob.z_image(), abs=1e-12)
+        assert back.paraxial(587.6)[0] == pytest.approx(L.paraxial(587.6)[0], rel=1e-12)
+
+
+def test_reverse_lens_argument_errors():
+    L = lt.Lens(w.singlet_lens())
+    zi = L.paraxial(587.6)[2]
+    f = lt.lib().lt_reverse_lens
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_void_p]
+    h = ctypes.c_void_p()
+    assert f(None, zi, 0.0, ctypes.byref(h)) == lt.LT_EINVAL
+    assert f(L.handle, 4.0, 0.0, ctypes.byref(h)) == lt.LT_EINVAL        # sensor inside the lens
+    assert "sensor" in lt.last_error()
+    assert f(L.handle, zi, 1.0, ctypes.byref(h)) == lt.LT_EINVAL         # output plane behind surface 1
+    assert f(L.handle, zi, float("nan"), ctypes.byref(h)) == lt.LT_EINVAL
+    assert not h.value
+
+
 def test_server_entry_points_without_gpu():
     import torch
     t = ctypes.c_uint64()

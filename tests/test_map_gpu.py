@@ -53,10 +53,12 @@ def gpu_query(gmap, rays, mode=lt.QUERY_TABLE):
     return o.numpy()
 
 
-def check_map(presc, rho, fit, queries, res=RES, label=""):
-    lens = lt.Lens(presc)
-    ol = oracle.Lens(presc)
-    lo, hi = box(rho)
+def check_map(presc, rho, fit, queries, res=RES, label="", lens=None, ol=None, smax=SMAX):
+    """lens / ol: the library's and the oracle's lens when they are not built
+    from `presc` (the reversed lens of the backward map)."""
+    lens = lens or lt.Lens(presc)
+    ol = ol or oracle.Lens(presc)
+    lo, hi = [-rho, -rho, -smax, -smax, 380.0], [rho, rho, smax, smax, 780.0]
     dfit = batch.DeviceRays(fit)
     gmap = lt.Map.build(lens, 0, res, lo, hi, fit=dfit)
     st = gmap.stats()
