@@ -340,7 +340,7 @@ def run_ours(args):
     if world == 1 and not args.skip_extra:
         extra = {}
         for key, fn in (("singlet_65k", bench_singlet), ("precision_16M", bench_precision),
-                        ("flares_56x1M", bench_flares)):
+                        ("flares_56x1M", bench_flares), ("mcmc_ghost", bench_mcmc)):
             extra[key] = fn(args, stream, flush, peaks)
             torch.cuda.empty_cache()
         extra["serving"] = bench_serving(args, peaks, seconds=args.serve_seconds)
@@ -532,6 +532,49 @@ def bench_flares(args, stream, flush, peaks):
                       "useful_tflops": round(swork / sl * FLOPS_PER_INTERACTION / (sms / sl * 1e-3) / 1e12, 2)}}
 
 
+def bench_mcmc(args, stream, flush, peaks):
+    """The valid-region sampler (Sec. 5.1) on a ghost path of the 11-surface
+    lens: 65,536 chains x 64 steps, against uniform draws of the same box."""
+    import numpy as np
+    import torch
+    from paper_2605_04017_gb300 import batch, lt, workloads as w
+    presc = w.eleven_surface_lens(lib_accept)
+    lens = lt.Lens(presc)
+    rho = w.eleven_rho(presc)
+    lo, hi = map_box(rho)
+    pid, chains, steps = 20, 65536, 64
+    box = [(a, b) for a, b in zip(lo, hi)]
+    res = {}
+
+    def step():
+        res["out"] = lt.mcmc_sample(lens, pid, lo, hi, 20260510, chains, steps, 0.03, 0.05, 64, stream)
+
+    r, prof = time_kernel(step, "mcmc", args, flush, stream, chains * steps, lt)
+    f, flags, acc = res["out"]
+    started = float((flags[:chains] != 0).float().mean())
+    a = acc.cpu().numpy()
+    launches, ms, work = prof["mcmc_kernel"]
+    # uniform draws of the same box through the tracer: the valid fraction they would give
+    u = np.random.default_rng(20260511)
+    n = 1 << 22
+    cols = [u.uniform(b[0], b[1], n) for b in box]
+    s = np.sqrt(cols[2] ** 2 + cols[3] ** 2 + 1.0)
+    rays = w.Rays(*(np.asarray(c, np.float32) for c in (cols[0], cols[1], cols[2] / s, cols[3] / s, 1.0 / s, cols[4])))
+    d = batch.DeviceRays(rays)
+    o = batch.DeviceOut(n)
+    lt.trace(lens, d.inp, d.lam, pid, o.out, n, stream)
+    torch.cuda.synchronize()
+    uniform_valid = float(((o.flags & 1) != 0).float().mean())
+    useful = work / launches * FLOPS_PER_INTERACTION / (ms / launches * 1e-3) / 1e12
+    return {"workload": "11-surface lens, ghost path 20, 65,536 chains x 64 steps (small 0.03, p_large 0.05, "
+                        "64 start draws)",
+            "samples_per_s": r["rays_per_s"], "ms_per_step": r["ms_per_step"], "p99_batch_ms": r["p99_batch_ms"],
+            "chains_started": round(started, 4),
+            "acceptance": round(float(a[a > 0].mean()) / steps, 4) if (a > 0).any() else 0.0,
+            "valid_fraction_of_uniform_draws": round(uniform_valid, 5),
+            "useful_tflops": round(useful, 2)}
+
+
 def bench_serving(args, peaks, seconds=10.0, warm=1.0, rate=2000.0):
     """8 seeded lenses (S ~ U{4..22}); Poisson arrivals; sizes log-uniform on
     [1,024, 4,194,304]; lens uniform; main path (its resident table map) with
@@ -642,7 +685,7 @@ def run_only(args):
     def flush():
         flush_buf.fill_(1)
 
-    fns = {"singlet": bench_singlet, "precision": bench_precision, "flares": bench_flares}
+    fns = {"singlet": bench_singlet, "precision": bench_precision, "flares": bench_flares, "mcmc": bench_mcmc}
     if args.only == "serving":
         out = bench_serving(args, peaks, seconds=args.serve_seconds)
     else:
@@ -714,7 +757,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-extra", action="store_true", help="headline workload only")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
-    ap.add_argument("--only", choices=["singlet", "precision", "flares", "serving"],
+    ap.add_argument("--only", choices=["singlet", "precision", "flares", "mcmc", "serving"],
                     help="run one of the other workloads alone and print its object")
     ap.add_argument("--rays", type=int, default=0, help="headline batch size (default 4,194,304)")
     ap.add_argument("--precision-rays", type=int, default=0)

@@ -248,6 +248,49 @@ lt_status lt_splat_paths(const lt_lens* lens, const lt_rays_in* in, const float*
                          size_t lambda_stride, const int32_t* path_ids, int32_t n_paths, size_t n,
                          const lt_sensor* sensor, float* image, lt_stream stream);
 
+/* ------------------------------------------------------------------ valid-region sampling */
+
+/*
+ * The sampler the paper uses to gather training rays (Sec. 5.1, data
+ * collection): for most paths only a small fraction of the input space gives
+ * valid rays, so Markov chains with the path's binary visibility as target
+ * draw rays uniformly over the valid region.  A chain lives in the box
+ * [lo, hi] over (x, y, s_x, s_y, lambda); its ray is (x, y) with direction
+ * normalize(s_x, s_y, 1).  It starts at the first valid independent uniform
+ * draw (at most init_tries; a chain that finds none never starts), then
+ * each step proposes, with probability p_large, an independent uniform
+ * point, else a uniform point of the box of half-width small * (hi - lo)
+ * around its state, and moves iff the proposal is in the box and its ray is
+ * valid (the exact FP32 tracer decides).  Random numbers are counter-based:
+ * u(chain, i, k) = top 24 bits of SplitMix64(seed + (chain << 32 | i << 3 |
+ * k)) * 2^-24, i the init try t or init_tries + step, k 0 for the step kind
+ * and 1..5 for the dimensions; every proposal is computed in FP32 with one
+ * rounding per operation, so the samples are a pure function of the options.
+ */
+typedef struct {
+    int32_t path_id;
+    double lo[5], hi[5];          /* the box over (x, y, s_x, s_y, lambda) */
+    uint64_t seed;
+    int32_t chains, steps;        /* chains x steps samples, < 2^32 */
+    double small;                 /* small-step half-width, as a fraction of the box */
+    double p_large;               /* probability of an independent step, in [0, 1] */
+    int32_t init_tries;           /* >= 1; init_tries + steps < 2^29 */
+} lt_mcmc_opts;
+
+typedef struct {
+    float *x, *y, *dx, *dy, *dz;  /* device, chains x steps: the entrance ray of sample */
+    float* lambda_nm;             /* (step s, chain c) at index s * chains + c */
+    uint8_t* flags;               /* LT_FLAG_VALID for a started chain's samples; 0 (and zero rays) otherwise */
+    uint32_t* accepted;           /* device, per chain: proposals accepted (may be NULL) */
+} lt_samples_out;
+
+/* Run the chains (one GPU thread per chain) and write every chain's state
+ * after every step.  The samples feed lt_build_map (fit rays) or
+ * lt_mlp_train like any rays.  Errors: LT_EINVAL (NULL or misaligned array,
+ * bad path id, empty box, counts out of range), LT_ECUDA. */
+lt_status lt_mcmc_sample(const lt_lens* lens, const lt_mcmc_opts* opts, const lt_samples_out* out,
+                         lt_stream stream);
+
 /* ------------------------------------------------------------------ maps */
 
 /*

@@ -305,6 +305,37 @@ def splat_paths(lens: Lens, inp: Sequence, lam, lam_stride: int, path_ids, n: in
                            ctypes.byref(sen), _ptr(image), _stream_handle(stream)))
 
 
+class c_mcmc_opts(ctypes.Structure):
+    _fields_ = [("path_id", ctypes.c_int32), ("lo", ctypes.c_double * 5), ("hi", ctypes.c_double * 5),
+                ("seed", ctypes.c_uint64), ("chains", ctypes.c_int32), ("steps", ctypes.c_int32),
+                ("small", ctypes.c_double), ("p_large", ctypes.c_double), ("init_tries", ctypes.c_int32)]
+
+
+class c_samples_out(ctypes.Structure):
+    _fields_ = [("x", _fptr), ("y", _fptr), ("dx", _fptr), ("dy", _fptr), ("dz", _fptr),
+                ("lambda_nm", _fptr), ("flags", ctypes.c_void_p), ("accepted", ctypes.c_void_p)]
+
+
+def mcmc_sample(lens: Lens, path_id: int, lo, hi, seed: int, chains: int, steps: int, small: float,
+                p_large: float, init_tries: int, stream=None):
+    """lt_mcmc_sample: returns (device tensors [x, y, dx, dy, dz, lambda] of
+    chains * steps samples, flags, accepted per chain)."""
+    import torch
+    L = lib()
+    L.lt_mcmc_sample.restype = ctypes.c_int
+    L.lt_mcmc_sample.argtypes = [ctypes.c_void_p, ctypes.POINTER(c_mcmc_opts), ctypes.POINTER(c_samples_out),
+                                 ctypes.c_void_p]
+    n = chains * steps
+    f = [torch.empty(max(n, 1), dtype=torch.float32, device="cuda") for _ in range(6)]
+    flags = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
+    acc = torch.empty(max(chains, 1), dtype=torch.int32, device="cuda")
+    o = c_mcmc_opts(path_id, (ctypes.c_double * 5)(*lo), (ctypes.c_double * 5)(*hi), seed, chains, steps,
+                    small, p_large, init_tries)
+    out = c_samples_out(*[_ptr(t) for t in f], _ptr(flags), _ptr(acc))
+    check(L.lt_mcmc_sample(lens.handle, ctypes.byref(o), ctypes.byref(out), _stream_handle(stream)))
+    return f, flags, acc
+
+
 # ------------------------------------------------------------------ maps
 
 QUERY_TABLE = 0
