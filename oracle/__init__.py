@@ -75,6 +75,8 @@ def _declare(L: ctypes.CDLL) -> None:
     L.or_lens_init.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp, _dp, _ip, ctypes.c_int, _ip,
                                _dp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    L.or_lens_set_asphere.restype = ctypes.c_int
+    L.or_lens_set_asphere.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp]
     L.or_lens_get.restype = ctypes.c_double
     L.or_lens_get.argtypes = [ctypes.c_void_p, ctypes.c_int]
     L.or_index.restype = ctypes.c_double
@@ -161,6 +163,12 @@ class Lens:
                             presc.image_mode, presc.image_z, presc.lambda_ref_nm)
         if rc != 0:
             raise ValueError("oracle: bad prescription (or back focal distance <= 0)")
+        for k, s in enumerate(presc.surfaces):
+            kappa = float(getattr(s, "conic", 0.0))
+            a = np.array(list(getattr(s, "asph", (0.0, 0.0, 0.0, 0.0))), np.float64)
+            on = 1 if (kappa != 0.0 or np.any(a != 0.0) or getattr(s, "force_asphere", False)) else 0
+            if on and L.or_lens_set_asphere(self._buf, k + 1, on, kappa, _ptr(a, _dp)) != 0:
+                raise ValueError(f"oracle: asphere {k + 1}: aperture beyond the conic's domain")
         self.S = S
         self.presc = presc
 

@@ -27,6 +27,9 @@ typedef struct {
     double zv[OR_MAXS + 2];         /* vertex z of surface k (1..S) */
     double c[OR_MAXS + 2];          /* curvature 1/R of surface k, 0 = plane */
     double ap[OR_MAXS + 2];         /* clear aperture radius of surface k */
+    int asph[OR_MAXS + 2];          /* surface k is an even asphere (conic and polynomial below) */
+    double conic[OR_MAXS + 2];      /* conic constant kappa of surface k */
+    double a4[OR_MAXS + 2][4];      /* A4, A6, A8, A10 of surface k */
     int med[OR_MAXS + 2];           /* glass of medium m (0..S), -1 = air; m = k is after surface k */
     int n_glass;
     int gkind[OR_MAXG];

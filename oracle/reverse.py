@@ -6,8 +6,9 @@ transmission path and continue into the scene).  Reading: the backward
 transport of a lens is the forward transport of its mirror image about the
 sensor plane.  With z' = sensor_z - z:
   - surface j of the reversed lens is forward surface k = S + 1 - j, at
-    z'_j = sensor_z - z_k, with curvature -c_k (mirroring flips the sag) and
-    the same clear aperture;
+    z'_j = sensor_z - z_k, with curvature -c_k and, for an even asphere,
+    polynomial coefficients -A_k (mirroring flips the sag; the conic
+    constant stays), and the same clear aperture;
   - the medium after reversed surface j is the forward medium in front of
     surface k (air for k = 1);
   - the reversed entrance plane (z' = 0) is the sensor, and its output
@@ -54,8 +55,11 @@ def reverse_prescription(presc, sensor_z: float, out_z: float, image_abs_mode: i
         s = presc.surfaces[k - 1]
         thick = zv[k - 1] - zv[k - 2] if k >= 2 else 0.0
         glass = presc.surfaces[k - 2].glass_after if k >= 2 else -1
+        # mirroring negates the sag: the curvature and the polynomial terms change
+        # sign, the conic constant does not
         surfs.append(surf_t(curvature=-s.curvature, thickness=thick, aperture_r=s.aperture_r,
-                            glass_after=glass))
+                            glass_after=glass, conic=getattr(s, "conic", 0.0),
+                            asph=tuple(-a for a in getattr(s, "asph", (0.0, 0.0, 0.0, 0.0)))))
     stop_after, stop_offset = 0, 0.0
     if presc.stop_r > 0.0:
         g = presc.stop_after               # forward gap between vertex g and g + 1 (vertex 0: z = 0)

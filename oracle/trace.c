@@ -135,6 +135,63 @@ int or_lens_init(or_lens* L, int S, const double* curv, const double* thick, con
 }
 
 /*
+ * Make surface k (1..S) an even asphere (the circularly symmetric surfaces
+ * the paper's model admits, Sec. 4.1): sag
+ *   z(r) = c r^2 / (1 + sqrt(1 - (1 + kappa) c^2 r^2)) + A4 r^4 + A6 r^6 + A8 r^8 + A10 r^10
+ * in the vertex frame.  on = 0 restores the sphere.  Returns 0, or -1 for a
+ * bad k or a clear aperture beyond the conic's domain.
+ */
+int or_lens_set_asphere(or_lens* L, int k, int on, double kappa, const double* a)
+{
+    if (k < 1 || k > L->S) return -1;
+    L->asph[k] = on;
+    L->conic[k] = kappa;
+    for (int i = 0; i < 4; ++i) L->a4[k][i] = a ? a[i] : 0.0;
+    if (on && 1.0 - (1.0 + kappa) * L->c[k] * L->c[k] * L->ap[k] * L->ap[k] < 0.0) return -1;
+    return 0;
+}
+
+/* sag of an even asphere and its derivative with respect to s = r^2; -1 if
+ * s lies beyond the conic's domain */
+static int asph_sag(const or_lens* L, int k, double s, double* z, double* dz_ds)
+{
+    double c = L->c[k];
+    double q2 = 1.0 - (1.0 + L->conic[k]) * c * c * s;
+    if (q2 < 0.0) return -1;
+    double q = sqrt(q2);
+    const double* A = L->a4[k];
+    double poly = s * s * (A[0] + s * (A[1] + s * (A[2] + s * A[3])));
+    double dpoly = s * (2.0 * A[0] + s * (3.0 * A[1] + s * (4.0 * A[2] + s * 5.0 * A[3])));
+    *z = c * s / (1.0 + q) + poly;
+    /* d/ds [c s / (1 + q)] = c / (2 q) */
+    *dz_ds = (q > 0.0 ? c / (2.0 * q) : INFINITY) + dpoly;
+    return 0;
+}
+
+/*
+ * Hit of an even asphere by the ray o + t d (vertex frame): Newton's method
+ * on g(t) = o_z + t d_z - z(s(t)), s(t) = |(o + t d)_xy|^2, from t0 (the base
+ * sphere's near-cap root, or the vertex plane's).  Returns 0 with *t, or -1
+ * (no root the iteration reaches, or a point beyond the conic's domain).
+ */
+static int asph_hit(const or_lens* L, int k, const double* o, const double* d, double t0, double* t)
+{
+    double tt = t0;
+    for (int it = 0; it < 60; ++it) {
+        double px = o[0] + tt * d[0], py = o[1] + tt * d[1];
+        double z, zs;
+        if (asph_sag(L, k, px * px + py * py, &z, &zs) != 0) return -1;
+        double g = o[2] + tt * d[2] - z;
+        double gp = d[2] - zs * 2.0 * (px * d[0] + py * d[1]);
+        if (gp == 0.0 || !isfinite(gp)) return -1;
+        double step = g / gp;
+        tt -= step;
+        if (fabs(step) <= 1e-14 * (1.0 + fabs(tt))) { *t = tt; return 0; }
+    }
+    return -1;
+}
+
+/*
  * Unpolarised Fresnel reflectance at an interface n1 -> n2 for an incidence
  * cosine cos_i > 0.  Returns 1 for total internal reflection (Rs = Rp = 1).
  */
@@ -272,13 +329,24 @@ static int trace_impl(const or_lens* L, int pi, int pj, double x, double y, doub
             double b = c * (o[0] * d[0] + o[1] * d[1] + o[2] * d[2]) - d[2];
             double C = c * (o[0] * o[0] + o[1] * o[1] + o[2] * o[2]) - 2.0 * o[2];
             double disc = b * b - c * C;
-            if (disc < 0.0) return 0;
-            double q = -b - copysign(sqrt(disc), b);
-            if (q == 0.0) return 0;
-            t = C / q;
-            /* t = 0 is a hit at the start point (the singlet's entrance plane
-             * touches its front vertex); only a surface behind the ray misses */
-            if (!(t >= 0.0)) return 0;
+            if (L->asph[s]) {
+                /* start from the base sphere's near cap, or the vertex plane */
+                double t0 = -o[2] / d[2];
+                if (disc >= 0.0) {
+                    double q0 = -b - copysign(sqrt(disc), b);
+                    if (q0 != 0.0) t0 = C / q0;
+                }
+                if (asph_hit(L, s, o, d, t0, &t) != 0) return 0;
+                if (!(t >= 0.0)) return 0;
+            } else {
+                if (disc < 0.0) return 0;
+                double q = -b - copysign(sqrt(disc), b);
+                if (q == 0.0) return 0;
+                t = C / q;
+                /* t = 0 is a hit at the start point (the singlet's entrance plane
+                 * touches its front vertex); only a surface behind the ray misses */
+                if (!(t >= 0.0)) return 0;
+            }
         } else {
             if (!(d[2] > 0.0)) return 0;
             t = (L->z_image - p[2]) / d[2];
@@ -306,9 +374,18 @@ static int trace_impl(const or_lens* L, int pi, int pj, double x, double y, doub
         if (e < *edge) *edge = e;
         if (r2 > L->ap[s] * L->ap[s]) return 0;
 
-        /* unit normal of c|p|^2 - 2 p_z = 0 at the hit, facing the incoming ray */
+        /* unit normal at the hit, facing the incoming ray: of c|p|^2 - 2 p_z = 0
+         * for a sphere, of p_z - z(s) = 0 (gradient (-2x z'(s), -2y z'(s), 1))
+         * for an asphere */
         double c = L->c[s];
         double nv[3] = {c * p[0], c * p[1], c * (p[2] - L->zv[s]) - 1.0};
+        if (L->asph[s]) {
+            double z, zs;
+            if (asph_sag(L, s, r2, &z, &zs) != 0) return 0;
+            nv[0] = -2.0 * p[0] * zs;
+            nv[1] = -2.0 * p[1] * zs;
+            nv[2] = 1.0;
+        }
         double nn = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
         for (int a = 0; a < 3; ++a) nv[a] /= nn;
         double dn = nv[0] * d[0] + nv[1] * d[1] + nv[2] * d[2];

@@ -50,6 +50,8 @@ class Surface:
     thickness: float      # vertex-to-next-vertex distance in mm
     aperture_r: float     # clear aperture radius in mm
     glass_after: int      # index into Prescription.glasses of the medium after this surface, -1 = air
+    conic: float = 0.0    # even asphere: conic constant kappa (0 with zero asph: a sphere)
+    asph: tuple = (0.0, 0.0, 0.0, 0.0)   # even asphere: A4, A6, A8, A10 (mm^-3, mm^-5, ...)
 
 
 @dataclasses.dataclass
