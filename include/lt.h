@@ -79,6 +79,13 @@ typedef struct {
     double thickness;    /* vertex to next vertex (mm); ignored for the last surface */
     double aperture_r;   /* clear aperture radius (mm): a hit with x^2+y^2 > r^2 is absorbed */
     int glass_after;     /* index into glasses[] of the medium after this surface; -1 = air */
+    /* Even asphere (the circularly symmetric surfaces Sec. 4.1 admits): sag
+     * z(r) = c r^2 / (1 + sqrt(1 - (1 + conic) c^2 r^2)) + A4 r^4 + A6 r^6 + A8 r^8
+     * + A10 r^10 in the vertex frame; all zero: the sphere (or plane).  A lens
+     * with an asphere is traced by Newton's method on the sag (FP32) from the
+     * base sphere's hit, on the tracer's general instantiation. */
+    double conic;
+    double asph[4];      /* A4, A6, A8, A10 (1/mm^3, 1/mm^5, ...) */
 } lt_surface;
 
 typedef struct {

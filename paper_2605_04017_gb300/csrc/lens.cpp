@@ -160,6 +160,10 @@ lt_status lt_create_lens(const lt_prescription* p, lt_lens** out)
         if (!(s.aperture_r > 0.0) || !std::isfinite(s.curvature) ||
             !(std::fabs(s.curvature) * s.aperture_r < 1.0))
             return fail(LT_EBADLENS, "surface %d: aperture must be positive and smaller than |R|", k + 1);
+        if (!std::isfinite(s.conic) || !std::isfinite(s.asph[0]) || !std::isfinite(s.asph[1]) ||
+            !std::isfinite(s.asph[2]) || !std::isfinite(s.asph[3]) ||
+            !(1.0 - (1.0 + s.conic) * s.curvature * s.curvature * s.aperture_r * s.aperture_r > 0.0))
+            return fail(LT_EBADLENS, "surface %d: the clear aperture reaches beyond the conic", k + 1);
         if (k + 1 < S && !(s.thickness >= 0.0))
             return fail(LT_EBADLENS, "surface %d: negative thickness", k + 1);
     }
@@ -235,6 +239,12 @@ lt_status lt_create_lens(const lt_prescription* p, lt_lens** out)
         r.B_after = ga < 0 ? 0.0f : D.gB[ga];
         r.g_before = (float)gb;
         r.g_after = (float)ga;
+        const lt_surface& sf = L->surf[k - 1];
+        r.kc = (float)sf.conic;
+        r.a4 = (float)sf.asph[0];
+        r.a6 = (float)sf.asph[1];
+        r.a8 = (float)sf.asph[2];
+        r.a10 = (float)sf.asph[3];
     }
     if (p->stop_r > 0.0) {
         const int g = p->stop_after;
@@ -283,6 +293,9 @@ lt_status lt_reverse_lens(const lt_lens* F, double sensor_z, double out_z, lt_le
         surf[j - 1].aperture_r = s.aperture_r;
         surf[j - 1].thickness = k >= 2 ? F->zv[k] - F->zv[k - 1] : 0.0;
         surf[j - 1].glass_after = k >= 2 ? F->surf[k - 2].glass_after : -1;
+        // mirroring negates the sag: the polynomial terms change sign, the conic does not
+        surf[j - 1].conic = s.conic;
+        for (int q = 0; q < 4; ++q) surf[j - 1].asph[q] = -s.asph[q];
     }
     lt_prescription R = P;
     R.surfaces = surf;

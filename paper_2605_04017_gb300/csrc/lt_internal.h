@@ -24,12 +24,13 @@ void clear_error();
 constexpr int kMaxS = LT_MAX_SURFACES;
 constexpr int kMaxG = LT_MAX_GLASSES;
 
-// One surface as the tracer reads it (48 bytes): both neighbouring media are
+// One surface as the tracer reads it (64 bytes): both neighbouring media are
 // resolved, so an interaction evaluates one dispersion formula.
 struct __align__(16) SurfRec {
     float c, th_before, th_after, ap2;          // curvature, vertex gaps to s-1 and s+1, aperture^2
     float eps2a, A_before, B_before, A_after;   // near-edge band on r^2; Cauchy (A, B) of media s-1, s
-    float B_after, g_before, g_after, pad;      // glass ids of media s-1, s (as float; -1 air)
+    float B_after, g_before, g_after, kc;       // glass ids of media s-1, s (as float; -1 air); conic
+    float a4, a6, a8, a10;                      // even-asphere polynomial (all zero with kc: a sphere)
 };
 
 // The lens as the kernels see it: FP32, passed by value as a __grid_constant__

@@ -987,7 +987,7 @@ lt_status lt_map_save(const lt_map* m, const char* path)
     MapFileHeader h;
     std::memset(&h, 0, sizeof h);
     std::memcpy(h.magic, "LTMAP01", 8);
-    h.version = 1;
+    h.version = 2;   // 2: surface records carry the even-asphere terms
     h.path_id = m->path_id;
     for (int d = 0; d < 5; ++d) { h.res[d] = m->res[d]; h.lo[d] = m->lo[d]; h.hi[d] = m->hi[d]; }
     h.S = m->lens.S;
@@ -1025,7 +1025,7 @@ lt_status lt_map_load(const char* path, lt_map** out)
     lt_prescription p;
     lt_map_stats stats;
     bool ok = std::fread(&h, sizeof h, 1, f) == 1 && std::memcmp(h.magic, "LTMAP01", 8) == 0 &&
-              h.S >= 1 && h.S <= LT_MAX_SURFACES && h.n_glass >= 0 && h.n_glass <= LT_MAX_GLASSES;
+              h.version == 2 && h.S >= 1 && h.S <= LT_MAX_SURFACES && h.n_glass >= 0 && h.n_glass <= LT_MAX_GLASSES;
     ok = ok && std::fread(surf, sizeof(lt_surface), h.S, f) == (size_t)h.S;
     ok = ok && (h.n_glass == 0 || std::fread(glass, sizeof(lt_glass), h.n_glass, f) == (size_t)h.n_glass);
     ok = ok && std::fread(&p, sizeof p, 1, f) == 1 && std::fread(&stats, sizeof stats, 1, f) == 1;

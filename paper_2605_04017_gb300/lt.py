@@ -48,7 +48,8 @@ class c_glass(ctypes.Structure):
 
 class c_surface(ctypes.Structure):
     _fields_ = [("curvature", ctypes.c_double), ("thickness", ctypes.c_double),
-                ("aperture_r", ctypes.c_double), ("glass_after", ctypes.c_int)]
+                ("aperture_r", ctypes.c_double), ("glass_after", ctypes.c_int),
+                ("conic", ctypes.c_double), ("asph", ctypes.c_double * 4)]
 
 
 class c_prescription(ctypes.Structure):
@@ -177,7 +178,9 @@ class Lens:
         S = len(presc.surfaces)
         self._surfs = (c_surface * max(S, 1))()
         for k, s in enumerate(presc.surfaces):
-            self._surfs[k] = c_surface(s.curvature, s.thickness, s.aperture_r, s.glass_after)
+            self._surfs[k] = c_surface(s.curvature, s.thickness, s.aperture_r, s.glass_after,
+                                       float(getattr(s, "conic", 0.0)),
+                                       (ctypes.c_double * 4)(*getattr(s, "asph", (0.0, 0.0, 0.0, 0.0))))
         ng = len(presc.glasses)
         self._glasses = (c_glass * max(ng, 1))()
         for g, G in enumerate(presc.glasses):
