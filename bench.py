@@ -46,7 +46,12 @@ FLOPS_PER_INTERACTION = 89
 # ncu DRAM traffic per ray of each kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch / rays in it) with the hash of the
 # kernel sources it was measured on; stale hashes report traffic = null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, one launch of the
+    # 4,194,304-ray query of the 11-surface lens: 332,017,920 + 106,102,272 bytes
+    "map_query_kernel": {"bytes_per_ray": 438120192 / 4194304, "hash": "786fd7ef57aad82b"},
+    "map_trace_kernel": {"bytes_per_ray": 105677056 / 4194304, "hash": "786fd7ef57aad82b"},
+}
 
 KERNEL_SRCS = ["paper_2605_04017_gb300/csrc/trace.cu", "paper_2605_04017_gb300/csrc/tracer.cuh",
                "paper_2605_04017_gb300/csrc/map.cu", "paper_2605_04017_gb300/csrc/lt_internal.h",
@@ -175,6 +180,18 @@ def timed_steps(step, steps, warmup, flush, stream, on_timed_start=None):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def combine_ranks(step_ms, world, n, steps, dist=None, device="cpu"):
+    """Whole-job numbers of the replicas: for each timed arm (a list of per-step
+    ms), the maximum over ranks of its summed time, and the aggregate rays/s
+    world * n * steps / that time (every rank processed n rays per step)."""
+    import torch
+    tt = torch.tensor([sum(x) for x in step_ms], device=device, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    totals = [float(v) for v in tt.cpu()]
+    return totals, [world * n * steps / (t * 1e-3) for t in totals]
+
+
 def kernel_roofline(name, prof, peaks, steps, units_bytes=None, flops_per_work=None):
     """Roofline of one kernel over the timed steps: `units_bytes` (or the
     counted work x flops_per_work) of one step over the kernel's summed
@@ -247,13 +264,19 @@ def run_ours(args):
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
-    lt.profile_enable(True)
+    # the steps are timed twice: once as they run (the headline numbers), and
+    # once with the library's per-kernel CUDA events on (their records add
+    # about 3 us per kernel boundary) for the kernels' durations and work
     reset = lambda: lt.profile_read(reset=True)  # noqa: E731
-    t_query = timed_steps(query_step, args.steps, args.warmup, flush, stream, reset)
+    lt.profile_enable(False)
+    t_query = timed_steps(query_step, args.steps, args.warmup, flush, stream)
+    t_trace = timed_steps(trace_step, args.steps, args.warmup, flush, stream)
+    lt.profile_enable(True)
+    tp_query = timed_steps(query_step, args.steps, args.warmup, flush, stream, reset)
     pq = lt.profile_read(reset=True)
     qflags = o.flags.cpu().numpy()
     qout = torch.stack(o.f, 1).cpu().numpy()
-    t_trace = timed_steps(trace_step, args.steps, args.warmup, flush, stream, reset)
+    tp_trace = timed_steps(trace_step, args.steps, args.warmup, flush, stream, reset)
     pt = lt.profile_read(reset=True)
     lt.profile_enable(False)
     clocks = sampler.stop()
@@ -263,12 +286,8 @@ def run_ours(args):
         dist.barrier()
 
     # max over ranks of the summed step time
-    tt = torch.tensor([sum(t_query), sum(t_trace)], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    q_total_ms, t_total_ms = float(tt[0]), float(tt[1])
-    value = world * n * args.steps / (q_total_ms * 1e-3)
-    trace_value = world * n * args.steps / (t_total_ms * 1e-3)
+    (q_total_ms, t_total_ms), (value, trace_value) = combine_ranks(
+        [t_query, t_trace], world, n, args.steps, dist if world > 1 else None, "cuda")
 
     traced = (qflags & lt.FLAG_TRACED) != 0
     n_fb = int(traced.sum())
@@ -321,7 +340,9 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "p99_batch_ms": round(float(np.percentile(t_query, 99)), 4),
         "trace": {"rays_per_s": round(trace_value, 1), "ms_per_step": round(statistics.mean(t_trace), 4),
-                  "p99_batch_ms": round(float(np.percentile(t_trace, 99)), 4)},
+                  "p99_batch_ms": round(float(np.percentile(t_trace, 99)), 4),
+                  "ms_per_step_profiled": round(statistics.mean(tp_trace), 4)},
+        "ms_per_step_profiled": round(statistics.mean(tp_query), 4),
         "map_over_trace": round(value / trace_value, 3),
         "query_mix": {"mask_only": round(1 - (n_fb + n_interp) / n, 4),
                       "interpolated": round(n_interp / n, 4), "traced": round(n_fb / n, 4)},
@@ -734,7 +755,7 @@ def run_reference(args):
         om.query(rays)
     dt = time.perf_counter() - t0
     value = args.steps * len(rays) / dt
-    line = {"metric": METRIC, "value": round(value, 1), "unit": "rays/s", "n_gpus": 1,
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "rays/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

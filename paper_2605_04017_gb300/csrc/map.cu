@@ -20,7 +20,7 @@
 
 namespace lt {
 
-constexpr int kQBlock = 256;
+constexpr int kQBlock = 128;   // rays per chunk (and threads per block) of the trace kernel
 constexpr uint32_t kOutsideBit = 0x80000000u;
 
 // ------------------------------------------------------------------ lattice (FP32 rule)
@@ -347,7 +347,7 @@ constexpr int kObStride = 7;
 //  3. Each lane writes its own ray (coalesced) unless it was queued for the
 //     tracer; interpolated directions are renormalised there.
 // map_trace_kernel, a persistent grid, then traces the queue with the exact
-// tracer, 256 rays per block at a time with survivors compacted (the rays
+// tracer, 128 rays per block at a time with survivors compacted (the rays
 // of BOUNDARY cells die at every depth of the lens), and writes each result
 // at its ray's index.
 constexpr int kQWarps = kQTile / 32;
@@ -567,19 +567,23 @@ map_query_fused_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDe
 }
 
 // The exact tracer over the query's trace queue (see map_query_kernel):
-// blocks take 256-ray chunks of the queue's segments from a counter until
+// blocks take kQBlock-ray chunks of the queue's segments from a counter until
 // none is left (chunk c of the launch: segment s with cum[s] <= c <
 // cum[s + 1], cum the prefix sum of the segments' chunk counts).
-// Six resident blocks per SM (40 registers, a few spilled): measured faster
-// than four at 60 registers or five at 48.
+// Twelve resident 128-thread blocks per SM (40 registers, a few spilled):
+// measured faster than 256-ray chunks, or fewer blocks at 48 or 60
+// registers.  Launched as a programmatic dependent of map_query_kernel: its
+// blocks may become resident while that kernel drains, and wait for it to
+// complete (griddepcontrol.wait) before reading the queue.
 template <bool CAUCHY>
-__global__ void __launch_bounds__(kQBlock, 6)
+__global__ void __launch_bounds__(kQBlock, 12)
 map_trace_kernel(const __grid_constant__ MapDev M, RaysOutDev out, TraceQueue Q, unsigned long long* work)
 {
     __shared__ TraceSmem<kQBlock> S;
     __shared__ uint32_t cnt[kQSegs], cum[kQSegs + 1];
     __shared__ uint32_t chunk, cseg;
     const int t = threadIdx.x;
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
     if (t < kQSegs) cnt[t] = Q.count[t * kQCountStride];
     __syncthreads();
     if (t == 0) {
@@ -696,9 +700,19 @@ static lt_status launch_queue_trace(const lt_map* map, const RaysOutDev& out, ui
     // (blocks take chunks from a counter, so any grid traces the whole queue)
     const unsigned gt = persistent_blocks(trace, kQBlock, ((size_t)n + 3) / 4, 32);
     ProfScope prof("map_trace_kernel", st);
-    if (map->cauchy) map_trace_kernel<true><<<gt, kQBlock, 0, st>>>(map->dev, out, Q, prof.work());
-    else map_trace_kernel<false><<<gt, kQBlock, 0, st>>>(map->dev, out, Q, prof.work());
-    LT_CUDA_TRY(cudaGetLastError());
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(gt);
+    cfg.blockDim = dim3(kQBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    unsigned long long* w = prof.work();
+    if (map->cauchy) LT_CUDA_TRY(cudaLaunchKernelEx(&cfg, map_trace_kernel<true>, map->dev, out, Q, w));
+    else LT_CUDA_TRY(cudaLaunchKernelEx(&cfg, map_trace_kernel<false>, map->dev, out, Q, w));
     return LT_OK;
 }
 

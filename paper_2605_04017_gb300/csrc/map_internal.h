@@ -31,7 +31,7 @@ struct MapDev {
 // appending to segment b % kQSegs, so that the appends' atomics spread over
 // kQSegs counters in separate 128-byte lines instead of one hot address:
 // count[s * kQCountStride] counts segment s, count[kQSegs * kQCountStride]
-// the 256-ray chunks the tracer has taken.
+// the 128-ray chunks the tracer has taken.
 constexpr int kQSegs = 64;
 constexpr int kQCountStride = 32;
 constexpr size_t kQHeaderBytes = (kQSegs + 1) * kQCountStride * 4 + 128;   // 8,448 bytes
