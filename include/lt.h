@@ -190,9 +190,12 @@ typedef struct {
 lt_status lt_trace(const lt_lens* lens, const lt_rays_in* in, const float* lambda_nm,
                    int32_t path_id, const lt_rays_out* out, size_t n, lt_stream stream);
 
-/* Same, with HOST arrays (pageable or pinned): copies in, traces, copies out
- * in pipelined chunks on library streams and returns when the outputs are in
- * host memory.  Errors as lt_trace, plus LT_ENOMEM for staging buffers. */
+/* Same, with HOST arrays (pageable or pinned; pinned is faster): traces in
+ * pipelined chunks of at most 2^20 rays and returns when the outputs are in
+ * host memory.  Each chunk passes through three library streams (copy in,
+ * kernels, copy out), so one chunk's inputs copy in while an older chunk's
+ * outputs copy back.  Errors as lt_trace, plus LT_ENOMEM for staging
+ * buffers. */
 lt_status lt_trace_host(const lt_lens* lens, const lt_rays_in* in, const float* lambda_nm,
                         int32_t path_id, const lt_rays_out* out, size_t n);
 
@@ -377,7 +380,8 @@ enum {
  * Errors as lt_trace; LT_ENOMEM if the queue cannot be had. */
 lt_status lt_query(const lt_map* map, const lt_rays_in* in, const float* lambda_nm,
                    const lt_rays_out* out, size_t n, int32_t mode, lt_stream stream);
-/* Same with HOST arrays; returns when the results are in host memory. */
+/* Same with HOST arrays, in the pipelined chunks of lt_trace_host; returns
+ * when the results are in host memory. */
 lt_status lt_query_host(const lt_map* map, const lt_rays_in* in, const float* lambda_nm,
                         const lt_rays_out* out, size_t n, int32_t mode);
 
@@ -389,13 +393,13 @@ lt_status lt_query_host(const lt_map* map, const lt_rays_in* in, const float* la
  * counterpart: this is a deployment aid.
  * Same arguments, results and errors as lt_query, but its trace queue lives
  * in a fixed array inside the library (28 bytes per ray of
- * LT_NOALLOC_MAX_RAYS rays plus two counters: 14 MiB, held on every device
- * that loads the library until the process exits), so
+ * LT_NOALLOC_MAX_RAYS rays after 8,448 bytes of counters: 14 MiB, held on
+ * every device that loads the library until the process exits), so
  * n > LT_NOALLOC_MAX_RAYS is rejected with LT_EINVAL: split larger batches.
  *  - The first call on a device looks up the array's device address (a
  *    driver query, no allocation); make that first call before any stream
  *    capture.
- *  - Every call shares the one array, and its counter is cleared on the
+ *  - Every call shares the one array, and its counters are cleared on the
  *    call's stream: calls whose work overlaps on the GPU (different streams
  *    without an event between them) race and give wrong results.  Order
  *    them on one stream. */

@@ -200,6 +200,24 @@ def test_save_load_and_host_query_are_bitwise_equal():
     assert np.array_equal(h.flags.numpy(), rfl)
 
 
+@pytest.mark.parametrize("pin", [True, False, "mixed"])
+def test_host_query_in_chunks_is_bitwise_equal(pin):
+    # 600,001 rays: the device call runs the classify kernel and the queue
+    # tracer over the whole batch, the host call four chunks (the last one
+    # ragged) of the one-kernel query; pinned, pageable and mixed host arrays
+    p = w.singlet_lens()
+    rays = w.singlet_rays(600001)
+    lo, hi = box(12.0)
+    g = lt.Map.build(lt.Lens(p), 0, [9, 9, 9, 9, 4], lo, hi, fit=batch.DeviceRays(w.singlet_rays(20000)))
+    ref, rfl = gpu_query(g, rays)
+    h = batch.HostRays(rays, pin=(pin is True))
+    if pin == "mixed":
+        h.inp[:3] = [t.pin_memory() for t in h.inp[:3]]
+    g.query_host(h.inp[:5], h.inp[5], h.out + [h.flags], len(rays))
+    assert np.array_equal(np.stack([t.numpy() for t in h.out], 1), ref)
+    assert np.array_equal(h.flags.numpy(), rfl)
+
+
 def test_query_zero_rays():
     p = w.singlet_lens()
     lo, hi = box(12.0)

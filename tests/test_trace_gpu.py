@@ -111,11 +111,14 @@ def test_bad_inputs_are_flagged():
     assert np.all(flags[:4] == lt.FLAG_BAD_INPUT)
 
 
-def test_host_entry_point_is_bitwise_equal(eleven):
+@pytest.mark.parametrize("pin", [True, False])
+def test_host_entry_point_is_bitwise_equal(eleven, pin):
+    # pinned and pageable host arrays; 300,001 rays run as four chunks of the
+    # three-stream pipeline, the last one ragged
     lens = lt.Lens(eleven)
     rays = w.eleven_rays(eleven, 300001)
     out_d, flags_d = run_gpu(lens, rays, 3)
-    h = batch.HostRays(rays)
+    h = batch.HostRays(rays, pin=pin)
     lt.trace_host(lens, h.inp[:5], h.inp[5], 3, h.out + [h.flags], len(rays))
     out_h = np.stack([t.numpy() for t in h.out], axis=1)
     assert np.array_equal(out_h, out_d)
