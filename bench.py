@@ -538,6 +538,8 @@ def bench_flares(args, stream, flush, peaks):
                                                     weight=1.0 / n, stream=stream),
                              "splat", args, flush, stream, n * P, lt)
     sl, sms, swork = prof_s["splat_paths_kernel"]
+    del img
+    bf16 = bench_flares_bf16_map(args, stream, flush, lens, presc, d, lam, n, P)
     return {"workload": "11-surface lens, 56 paths (main + 55 ghosts) x 1,048,576 rays, lambda per path",
             "rays_per_s": r["rays_per_s"], "ms_per_step": r["ms_per_step"], "p99_batch_ms": r["p99_batch_ms"],
             "valid_rays_per_launch": int(counts.sum()),
@@ -550,7 +552,68 @@ def bench_flares(args, stream, flush, peaks):
                                   "sensor (tent filter, G = exit d_z, weight 1/n)",
                       "rays_per_s": rs["rays_per_s"], "ms_per_step": rs["ms_per_step"],
                       "p99_batch_ms": rs["p99_batch_ms"],
-                      "useful_tflops": round(swork / sl * FLOPS_PER_INTERACTION / (sms / sl * 1e-3) / 1e12, 2)}}
+                      "useful_tflops": round(swork / sl * FLOPS_PER_INTERACTION / (sms / sl * 1e-3) / 1e12, 2)},
+            "bf16_map": bf16}
+
+
+def bench_flares_bf16_map(args, stream, flush, lens, presc, d, lam, n, P, m_err=65536):
+    """The BF16 map variant of the flare workload: one learned map per path
+    (classifier + regressor trained on the GPU from 262,144 traced rays of that
+    path, short schedule), all 56 queried in BF16 on tensor cores over the
+    same rays and wavelengths as the trace; error against the FP32 tracer on
+    the first m_err rays of every path."""
+    import numpy as np
+    import torch
+    from paper_2605_04017_gb300 import batch, lt, workloads as w
+    rho = w.eleven_rho(presc)
+    rng = np.random.Generator(np.random.PCG64(w.SEED_BASE + 4 + 1000))
+    fit = batch.DeviceRays(w.entrance_rays(1 << 18, w.SEED_BASE + 4 + 1001, rho))
+    t0 = time.perf_counter()
+    maps = [lt.Mlp.train(lens, lt.mlp_frame(p, rho, 0.2421), fit, xavier_flat(MLP_REG_SIZES, rng),
+                         xavier_flat(MLP_CLS_SIZES, rng), reg_steps=1500, reg_batch=8192, cls_steps=1500,
+                         cls_batch=8192, lr=1e-3, lr_decay=0.95, decay_every=500, seed=100 + p)
+            for p in range(P)]
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del fit
+    o = batch.DeviceOut(n)
+
+    def step():
+        for p in range(P):
+            maps[p].query(d.inp, lam[p * n:(p + 1) * n], o.out, n, lt.MLP_BF16, stream)
+
+    r, _ = time_kernel(step, "flares_bf16", args, flush, stream, n * P, lt)
+    # error against the FP32 tracer, path by path, on the first m_err rays
+    m = min(m_err, n)
+    sub = [t[:m] for t in d.inp]
+    tq, qq = batch.DeviceOut(m), batch.DeviceOut(m)
+    agree, rms, p99, nboth = [], [], [], 0
+    for p in range(P):
+        lp = lam[p * n:p * n + m]
+        lt.trace(lens, sub, lp, p, tq.out, m, stream)
+        maps[p].query(sub, lp, qq.out, m, lt.MLP_BF16, stream)
+        torch.cuda.synchronize()
+        to, tf = tq.numpy()
+        qo, qf = qq.numpy()
+        tv, qv = (tf & lt.FLAG_VALID) != 0, (qf & lt.FLAG_VALID) != 0
+        agree.append(float((tv == qv).mean()))
+        both = tv & qv
+        if both.sum() >= 10:
+            e = np.hypot(qo[both, 0] - to[both, 0], qo[both, 1] - to[both, 1])
+            rms.append(float(np.sqrt((e ** 2).mean())))
+            p99.append(float(np.percentile(e, 99)))
+            nboth += int(both.sum())
+    return {"workload": "one learned map per path (classifier 4-32-32-1 + regressor 4-(32x5)-6, "
+                        "1,500 + 1,500 Adam steps of 8,192 on 262,144 traced rays of the path), "
+                        "56 BF16 tensor-core queries of 1,048,576 rays each",
+            "train_s": round(train_s, 2), "rays_per_s": r["rays_per_s"], "ms_per_step": r["ms_per_step"],
+            "p99_batch_ms": r["p99_batch_ms"],
+            "err_vs_fp32_trace": {"rays_per_path": m, "valid_agreement_mean": round(float(np.mean(agree)), 5),
+                                  "valid_agreement_min": round(float(np.min(agree)), 5),
+                                  "pos_rms_mm_median_over_paths": round(float(np.median(rms)), 5) if rms else None,
+                                  "pos_rms_mm_main_path": round(rms[0], 5) if rms else None,
+                                  "pos_p99_mm_max_over_paths": round(float(np.max(p99)), 5) if p99 else None,
+                                  "paths_compared": len(rms), "rays_valid_in_both": nboth}}
 
 
 def bench_mcmc(args, stream, flush, peaks):

@@ -249,3 +249,53 @@ def test_learned_map_gain(singlet, trained):
     both = ((f_c & 1) != 0) & truth
     e = np.hypot(o_c[both, 0] - ex[both, 0], o_c[both, 1] - ex[both, 1])
     print("learned map position error rms / p99 (mm)", np.sqrt((e ** 2).mean()), np.percentile(e, 99))
+
+
+@pytest.fixture(scope="module")
+def precision_batch():
+    return w.precision_rays()
+
+
+@pytest.mark.parametrize("precision", [lt.MLP_F32, lt.MLP_BF16, lt.MLP_F16])
+def test_full_size_precision_queries_sampled(singlet, trained, precision_batch, precision):
+    """The precision workload as the bench runs it: the trained networks
+    answer all 16,777,216 rays in one launch; 4,098 rays spread over the batch
+    (the first and last included) are checked against the oracle's forward,
+    FP32 within the tolerance of the small FP32 test, BF16 / FP16 within the
+    bounds of the half-precision error report."""
+    p, lens, ol = singlet
+    m, _, _ = trained
+    rays = precision_batch
+    n = len(rays)
+    assert n == 16777216
+    out, flags = run_query(m, rays, precision)
+    rng = np.random.Generator(np.random.PCG64(91))
+    idx = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, 4096)]))
+    sample = rays.subset(idx)
+    out, flags = out[idx], flags[idx]
+    st = m.stats()
+    t_mean, t_std = np.array(st["t_mean"]), np.array(st["t_std"])
+    reg_f, cls_f = m.params()
+    gv = (flags & 1) != 0
+    if precision == lt.MLP_F32:
+        oo, ov, logit = mlp.query_with(as64(cls_f, "cls"), as64(reg_f, "reg"), sample, RHO, WMAX,
+                                       t_mean, t_std, mlp.tanh_lambert)
+        clear = np.abs(logit) > 1e-3
+        assert np.array_equal(gv[clear], ov[clear])
+        both = gv & ov
+        err = np.abs(out[both].astype(np.float64) - oo[both])
+        tol = 3e-5 * t_std + 2 * 2.0 ** -23 * np.abs(oo[both])
+        for q in (0, 1, 5):
+            assert np.all(err[:, q] <= tol[:, q]), q
+        assert err[:, 2:5].max() < 3e-5
+    else:
+        bound = 3e-2 if precision == lt.MLP_BF16 else 4e-3
+        oo, ov, logit = mlp.query(as64(cls_f, "cls"), as64(reg_f, "reg"), sample, RHO, WMAX, t_mean, t_std)
+        clear = np.abs(logit) > 0.05
+        assert (gv == ov)[clear].mean() > 0.99
+        both = gv & ov
+        scaled = np.abs(out[both].astype(np.float64) - oo[both]) / np.array([t_std[0], t_std[1], 1, 1, 1, t_std[5]])
+        pos_rms = float(np.sqrt((scaled[:, :2] ** 2).mean()))
+        print("full-size precision", precision, "pos_rms_std", pos_rms, "dir_max", float(scaled[:, 2:5].max()))
+        assert pos_rms < bound and scaled[:, 2:5].max() < 10 * bound
+    assert np.all(out[~gv] == 0)
