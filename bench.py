@@ -48,9 +48,9 @@ FLOPS_PER_INTERACTION = 89
 # kernel sources it was measured on; stale hashes report traffic = null.
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, one launch of the
-    # 4,194,304-ray query of the 11-surface lens: 332,017,920 + 106,102,272 bytes
-    "map_query_kernel": {"bytes_per_ray": 438120192 / 4194304, "hash": "786fd7ef57aad82b"},
-    "map_trace_kernel": {"bytes_per_ray": 105677056 / 4194304, "hash": "786fd7ef57aad82b"},
+    # 4,194,304-ray query of the 11-surface lens: 253,714,432 + 103,454,464 bytes
+    "map_query_kernel": {"bytes_per_ray": 357168896 / 4194304, "hash": "5ad6cd3877613a36"},
+    "map_trace_kernel": {"bytes_per_ray": 108173824 / 4194304, "hash": "5ad6cd3877613a36"},
 }
 
 KERNEL_SRCS = ["paper_2605_04017_gb300/csrc/trace.cu", "paper_2605_04017_gb300/csrc/tracer.cuh",
@@ -539,7 +539,7 @@ def bench_flares(args, stream, flush, peaks):
                              "splat", args, flush, stream, n * P, lt)
     sl, sms, swork = prof_s["splat_paths_kernel"]
     del img
-    bf16 = bench_flares_bf16_map(args, stream, flush, lens, presc, d, lam, n, P)
+    bf16 = None if args.no_flare_map else bench_flares_bf16_map(args, stream, flush, lens, presc, d, lam, n, P)
     return {"workload": "11-surface lens, 56 paths (main + 55 ghosts) x 1,048,576 rays, lambda per path",
             "rays_per_s": r["rays_per_s"], "ms_per_step": r["ms_per_step"], "p99_batch_ms": r["p99_batch_ms"],
             "valid_rays_per_launch": int(counts.sum()),
@@ -864,6 +864,8 @@ def main():
     ap.add_argument("--rays", type=int, default=0, help="headline batch size (default 4,194,304)")
     ap.add_argument("--precision-rays", type=int, default=0)
     ap.add_argument("--flare-rays", type=int, default=0, help="rays per flare path")
+    ap.add_argument("--no-flare-map", action="store_true",
+                    help="leave out the flare workload's BF16 learned-map variant (56 trainings)")
     ap.add_argument("--untrained", action="store_true",
                     help="precision workload with random networks (no training launches)")
     args = ap.parse_args()

@@ -344,8 +344,9 @@ constexpr int kObStride = 7;
 //     reads eight whole pairs), weights it by the corner's multilinear
 //     factor (the lambda factor included) and sums in registers; one
 //     shuffle stage adds the quad's lower- and upper-lambda halves.
-//  3. Each lane writes its own ray (coalesced) unless it was queued for the
-//     tracer; interpolated directions are renormalised there.
+//  3. Each lane writes its own ray (coalesced; a queued ray's row gets a
+//     placeholder the tracer overwrites); interpolated directions are
+//     renormalised there.
 // map_trace_kernel, a persistent grid, then traces the queue with the exact
 // tracer, 128 rays per block at a time with survivors compacted (the rays
 // of BOUNDARY cells die at every depth of the lens), and writes each result
@@ -398,7 +399,8 @@ __device__ __forceinline__ Classified classify_ray(const MapDev& M, const RaysIn
 // part (lane & 3) its 16-byte piece of every lambda pair (0/1: the halves of
 // the lower-lambda record, 2/3: of the upper one), summing the 16 pairs of
 // (x, y, s_x, s_y) corners in registers; a shuffle adds the lower and upper
-// halves -- then write every ray of the warp that is not to be traced.
+// halves -- then write every ray of the warp (a placeholder row for a ray to be
+// traced).
 __device__ __forceinline__ void gather_and_write(const MapDev& M, const RaysOutDev& out, uint32_t n, uint32_t r,
                                                  const Classified& c, GatherItem* gq, float* ob)
 {
@@ -461,7 +463,10 @@ __device__ __forceinline__ void gather_and_write(const MapDev& M, const RaysOutD
         }
     }
     __syncwarp();
-    if (r < n && !c.tr) {
+    // Every row is written, a queued ray's as a placeholder that the tracer
+    // overwrites later: the warp's stores then cover whole sectors, which L2
+    // takes without merging partial lines.
+    if (r < n) {
         float o[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (c.ip) {
 #pragma unroll

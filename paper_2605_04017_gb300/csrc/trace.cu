@@ -15,8 +15,9 @@ constexpr int kTraceBlock = 256;
 // the rest go on to the image; one thread per ray would keep each warp
 // running to its longest ray with most lanes idle.
 //  - trace_front_kernel: one thread per ray through the first kFront
-//    interactions; finished rays are written at once, survivors' states go
-//    to a queue (warp-aggregated appends, structure of arrays).
+//    interactions; finished rays are written at once (survivors' rows get a
+//    placeholder), survivors' states go to a queue (warp-aggregated appends,
+//    structure of arrays).
 //  - trace_rest_kernel: a persistent grid traces the queue to the end with
 //    every lane busy and writes each result at its ray's index.
 // Per-ray arithmetic is that of trace_ray, bit for bit.
@@ -81,8 +82,11 @@ trace_front_kernel(const __grid_constant__ LensDev L, int pi, int pj, RaysInDev 
         if (res != STEP_GO) {
             if (live) nint = st.k + (res == STEP_DONE ? 1 : 0);
             live = false;
-            store_result(out, r, st, res);
         }
+        // Every output row is written here, a survivor's as a placeholder that
+        // the rest kernel overwrites: the warp's stores then cover whole
+        // sectors, which L2 takes without merging partial lines.
+        store_result(out, r, st, live ? STEP_DEAD : res);
     }
     queue_push(Q, live, st, r, 0);
     warp_add(work, (unsigned)nint);
