@@ -48,9 +48,9 @@ FLOPS_PER_INTERACTION = 89
 # kernel sources it was measured on; stale hashes report traffic = null.
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, one launch of the
-    # 4,194,304-ray query of the 11-surface lens: 253,714,432 + 103,454,464 bytes
-    "map_query_kernel": {"bytes_per_ray": 357168896 / 4194304, "hash": "5ad6cd3877613a36"},
-    "map_trace_kernel": {"bytes_per_ray": 108173824 / 4194304, "hash": "5ad6cd3877613a36"},
+    # 4,194,304-ray query of the 11-surface lens: 253,664,512 + 102,752,768 bytes
+    "map_query_kernel": {"bytes_per_ray": 356417280 / 4194304, "hash": "0d93c77d8ed7d194"},
+    "map_trace_kernel": {"bytes_per_ray": 105388544 / 4194304, "hash": "0d93c77d8ed7d194"},
 }
 
 KERNEL_SRCS = ["paper_2605_04017_gb300/csrc/trace.cu", "paper_2605_04017_gb300/csrc/tracer.cuh",

@@ -607,7 +607,8 @@ lt_status lt_server_stats_get(lt_server* server, lt_server_stats* out);
  * name, launches and summed milliseconds), sets *n to the number of kernel
  * names seen, and clears the record if `reset` is non-zero.  At most 65,536
  * launches are kept between resets.  While enabled, tracing kernels also
- * count their work (one 64-bit atomic per warp). */
+ * count their work (one 64-bit atomic per warp, spread over eight counters
+ * per launch so that the counting does not serialise on one address). */
 typedef struct {
     char name[48];
     int64_t launches;

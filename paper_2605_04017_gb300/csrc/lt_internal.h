@@ -71,6 +71,11 @@ struct lt_lens {
 };
 
 namespace lt {
+// The profiler's work counters (profile.cpp): record r's count is the sum of
+// kProfShards 64-bit counters at r + s * kProfMaxRecs, so that the kernels'
+// per-warp additions spread over that many L2 lines instead of one address.
+constexpr size_t kProfMaxRecs = 1 << 16;
+constexpr int kProfShards = 8;
 // Host FP64 paraxial ABCD data of a lens (defined in lens.cpp).
 int paraxial(const lt_lens* L, double lambda_nm, double* efl, double* bfd);
 bool path_ij(int S, int path_id, int* i, int* j);

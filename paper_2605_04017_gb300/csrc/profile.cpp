@@ -20,8 +20,10 @@ bool g_on = false;
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_free;
 unsigned long long g_dropped = 0;
-constexpr size_t kMaxRecs = 1 << 16;
-unsigned long long* g_work = nullptr;   // one device counter per record
+constexpr size_t kMaxRecs = kProfMaxRecs;
+// kProfShards device counters per record (record r, shard s at r + s * kMaxRecs),
+// zeroed when profiling is enabled and at every reset
+unsigned long long* g_work = nullptr;
 int g_work_dev = -1;
 size_t g_next_slot = 0;
 
@@ -53,7 +55,6 @@ ProfScope::ProfScope(const char* name, cudaStream_t st) : name_(name), st_(st)
     if (g_work && dev == g_work_dev && g_next_slot < kMaxRecs) {
         slot_ = (int)g_next_slot++;
         work_ = g_work + slot_;
-        cudaMemsetAsync(work_, 0, sizeof(unsigned long long), st_);
     }
     cudaEventRecord(a_, st_);
     active_ = true;
@@ -78,8 +79,10 @@ lt_status lt_profile_enable(int32_t on)
     std::lock_guard<std::mutex> lk(g_mu);
     g_on = on != 0;
     if (g_on && !g_work) {
-        if (cudaGetDevice(&g_work_dev) != cudaSuccess ||
-            cudaMalloc(&g_work, kMaxRecs * sizeof(unsigned long long)) != cudaSuccess) {
+        const size_t bytes = kMaxRecs * kProfShards * sizeof(unsigned long long);
+        if (cudaGetDevice(&g_work_dev) != cudaSuccess || cudaMalloc(&g_work, bytes) != cudaSuccess ||
+            cudaMemset(g_work, 0, bytes) != cudaSuccess) {
+            if (g_work) cudaFree(g_work);
             g_work = nullptr;
             g_work_dev = -1;   // timing still works; work counts read as 0
         }
@@ -96,9 +99,13 @@ lt_status lt_profile_read(lt_kernel_time* out, int32_t max, int32_t* n_out, int3
     std::vector<unsigned long long> work;
     for (const Rec& r : g_recs) LT_CUDA_TRY(cudaEventSynchronize(r.b));
     if (g_work && g_next_slot > 0) {
-        work.resize(g_next_slot);
-        LT_CUDA_TRY(cudaMemcpy(work.data(), g_work, work.size() * sizeof(unsigned long long),
-                               cudaMemcpyDeviceToHost));
+        work.assign(g_next_slot, 0);
+        std::vector<unsigned long long> shard(g_next_slot);
+        for (int s = 0; s < kProfShards; ++s) {
+            LT_CUDA_TRY(cudaMemcpy(shard.data(), g_work + (size_t)s * kMaxRecs,
+                                   shard.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+            for (size_t r = 0; r < shard.size(); ++r) work[r] += shard[r];
+        }
     }
     for (const Rec& r : g_recs) {
         float ms = 0.0f;
@@ -125,6 +132,17 @@ lt_status lt_profile_read(lt_kernel_time* out, int32_t max, int32_t* n_out, int3
             g_free.push_back(r.b);
         }
         g_recs.clear();
+        if (g_work && g_next_slot > 0) {
+            // clear the used slots of every shard on the counters' device
+            int cur = -1;
+            LT_CUDA_TRY(cudaGetDevice(&cur));
+            if (cur != g_work_dev) LT_CUDA_TRY(cudaSetDevice(g_work_dev));
+            cudaError_t e = cudaSuccess;
+            for (int s = 0; s < kProfShards && e == cudaSuccess; ++s)
+                e = cudaMemset(g_work + (size_t)s * kMaxRecs, 0, g_next_slot * sizeof(unsigned long long));
+            if (cur != g_work_dev) cudaSetDevice(cur);
+            if (e != cudaSuccess) return cuda_fail(e, "lt_profile_read: clearing the work counters");
+        }
         g_next_slot = 0;
         g_dropped = 0;
     }

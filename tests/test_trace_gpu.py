@@ -150,3 +150,37 @@ def test_near_edge_flag_band_is_tight():
     assert list(near) == [False, False, True, True, True, False, False]
     assert list((flags & 1) != 0)[:2] == [True, True]
     assert list((flags & 1) != 0)[-2:] == [False, False]
+
+
+@pytest.mark.parametrize("lens_kind", ["singlet", "eleven"])
+def test_profiler_counts_every_interaction(lens_kind, eleven):
+    """The profiler's work count (ray-surface interactions evaluated, the image
+    plane counting as one) is exact: near-axis rays that all pass the lens
+    count K + 1 each, and a count over the whole batch equals the counts of
+    its two halves traced separately."""
+    p = w.singlet_lens() if lens_kind == "singlet" else eleven
+    lens = lt.Lens(p)
+    S = p.n_surfaces
+    rays = w.entrance_rays(200003, 5, 1.0, half_angle_deg=0.5)
+    ol = oracle.Lens(p)
+    _, ev, _, _ = ol.trace(rays, oracle.path_ij(S, 0))
+    assert np.all(ev == 1)
+    d = batch.DeviceRays(rays)
+    o = batch.DeviceOut(len(rays))
+    n = len(rays)
+    lt.profile_enable(True)
+    try:
+        lt.profile_read(reset=True)
+        lt.trace(lens, d.inp, d.lam, 0, o.out, n)
+        whole = lt.profile_read(reset=True)["trace_kernel"]
+        assert whole[0] == 1 and whole[2] == (S + 1) * n
+        # a ghost path, where rays die at many depths: whole batch = sum of halves
+        lt.trace(lens, d.inp, d.lam, 1, o.out, n)
+        g = lt.profile_read(reset=True)["trace_kernel"][2]
+        h = (n // 2) & ~63          # keeps the second half's arrays 16-byte aligned
+        lt.trace(lens, [t[:h] for t in d.inp], d.lam[:h], 1, o.out, h)
+        lt.trace(lens, [t[h:] for t in d.inp], d.lam[h:], 1, [t[h:] for t in o.out], n - h)
+        halves = lt.profile_read(reset=True)["trace_kernel"]
+        assert halves[0] == 2 and halves[2] == g and g > 0
+    finally:
+        lt.profile_enable(False)
