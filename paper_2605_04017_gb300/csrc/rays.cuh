@@ -130,14 +130,9 @@ Staging& host_staging();
 // each chunk's inputs are copied to its device buffers, the kernels write its
 // outputs to device buffers, and those are copied back.
 template <class Launch>
-lt_status run_host_pipelined(const lt_rays_in* in, const float* lam, const lt_rays_out* out,
-                             size_t n, Launch&& launch)
+lt_status host_chunks(Staging& S, const lt_rays_in* in, const float* lam, const lt_rays_out* out, size_t n,
+                      size_t chunk, Launch&& launch)
 {
-    std::lock_guard<std::mutex> lock(host_staging().mu);
-    Staging& S = host_staging();
-    const size_t chunk = host_chunk(n);
-    lt_status s = S.reserve(chunk);
-    if (s != LT_OK) return s;
     const float* hin[6] = {in->x, in->y, in->dx, in->dy, in->dz, lam};
     float* hout[6] = {out->x, out->y, out->dx, out->dy, out->dz, out->I};
     for (size_t off = 0, c = 0; off < n; off += chunk, ++c) {
@@ -155,7 +150,7 @@ lt_status run_host_pipelined(const lt_rays_in* in, const float* lam, const lt_ra
         RaysInDev din{S.in[b][0], S.in[b][1], S.in[b][2], S.in[b][3], S.in[b][4], S.in[b][5]};
         RaysOutDev dout{S.out[b][0], S.out[b][1], S.out[b][2], S.out[b][3], S.out[b][4], S.out[b][5],
                         S.flags[b]};
-        s = launch(din, dout, m, S.s_k);
+        const lt_status s = launch(din, dout, m, S.s_k);
         if (s != LT_OK) return s;
         LT_CUDA_TRY(cudaEventRecord(S.k_done[b], S.s_k));
         LT_CUDA_TRY(cudaStreamWaitEvent(S.s_out, S.k_done[b], 0));
@@ -165,10 +160,27 @@ lt_status run_host_pipelined(const lt_rays_in* in, const float* lam, const lt_ra
         LT_CUDA_TRY(cudaMemcpyAsync(out->flags + off, S.flags[b], m, cudaMemcpyDeviceToHost, S.s_out));
         LT_CUDA_TRY(cudaEventRecord(S.out_done[b], S.s_out));
     }
-    LT_CUDA_TRY(cudaStreamSynchronize(S.s_out));
-    LT_CUDA_TRY(cudaStreamSynchronize(S.s_k));
-    LT_CUDA_TRY(cudaStreamSynchronize(S.s_in));
     return LT_OK;
+}
+
+template <class Launch>
+lt_status run_host_pipelined(const lt_rays_in* in, const float* lam, const lt_rays_out* out,
+                             size_t n, Launch&& launch)
+{
+    std::lock_guard<std::mutex> lock(host_staging().mu);
+    Staging& S = host_staging();
+    const size_t chunk = host_chunk(n);
+    lt_status s = S.reserve(chunk);
+    if (s != LT_OK) return s;
+    s = host_chunks(S, in, lam, out, n, chunk, launch);
+    // on success and on failure alike, wait for every stage queued so far:
+    // the caller's host arrays are in use until then
+    const cudaStream_t streams[3] = {S.s_out, S.s_k, S.s_in};
+    for (cudaStream_t q : streams) {
+        const cudaError_t e = cudaStreamSynchronize(q);
+        if (s == LT_OK && e != cudaSuccess) s = cuda_fail(e, "host pipeline: cudaStreamSynchronize");
+    }
+    return s;
 }
 
 }  // namespace lt
