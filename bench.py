@@ -679,6 +679,25 @@ def bench_serving(args, peaks, seconds=10.0, warm=1.0, rate=2000.0):
         maps.append(lt.Map.build(lenses[k], 0, RES, lo, hi, fit=fit))
         del fit
         inputs.append(batch.DeviceRays(w.entrance_rays(NMAX, w.SEED_BASE + 5 + 7 * k + 1, rho)))
+    # each resident map's error against the FP32 tracer on the first 65,536
+    # rays of its lens's requests (interpolated rays; traced ones are exact)
+    m_err = 1 << 16
+    eq, et = batch.DeviceOut(m_err), batch.DeviceOut(m_err)
+    map_err = []
+    for k in range(len(pres)):
+        sub = [t[:m_err] for t in inputs[k].inp]
+        lam = inputs[k].lam[:m_err]
+        maps[k].query(sub, lam, eq.out, m_err)
+        lt.trace(lenses[k], sub, lam, 0, et.out, m_err)
+        torch.cuda.synchronize()
+        qo, qf = eq.numpy()
+        to, tf = et.numpy()
+        interp = (qf & lt.FLAG_TRACED) == 0
+        e = pos_err(qo[interp], qf[interp], to[interp], tf[interp], lt.FLAG_VALID)
+        map_err.append({"surfaces": pres[k].n_surfaces, "rms_mm": round(e["rms_mm"], 6),
+                        "p99_mm": round(e["p99_mm"], 6), "valid_agreement": e["valid_agreement"],
+                        "traced_fraction": round(float((~interp).mean()), 4)})
+    del eq, et
     SLOTS = 48
     slots = [batch.DeviceOut(NMAX) for _ in range(SLOTS)]
     free = queue.Queue()
@@ -755,7 +774,8 @@ def bench_serving(args, peaks, seconds=10.0, warm=1.0, rate=2000.0):
             "p99_latency_ms": round(float(np.percentile(lat, 99)) / 1e3, 4) if lat.size else None,
             "rays_per_s": round(rays_done / meas, 1),
             "fused_launches": int(stats["fused_launches"]), "fused_requests": int(stats["fused_requests"]),
-            "launches": int(stats["launches"]), "client_slot_stalls": stalls[0]}
+            "launches": int(stats["launches"]), "client_slot_stalls": stalls[0],
+            "map_err_vs_fp32_trace": map_err}
 
 
 def run_only(args):
