@@ -1,5 +1,5 @@
 """Pins for the oracle's tabulated map (paper Sec. 4.2 factorised mask +
-regressor; the table is this build's regressor).  Checked against exact
+regressor; the table is this library's regressor).  Checked against exact
 properties of multilinear interpolation, the exact tracer it falls back to,
 and lens geometry that fixes a cell's class by inspection."""
 import math
