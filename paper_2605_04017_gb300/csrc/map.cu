@@ -1047,13 +1047,17 @@ lt_status lt_map_load(const char* path, lt_map** out)
               h.version == 2 && h.S >= 1 && h.S <= LT_MAX_SURFACES && h.n_glass >= 0 && h.n_glass <= LT_MAX_GLASSES;
     ok = ok && std::fread(surf, sizeof(lt_surface), h.S, f) == (size_t)h.S;
     ok = ok && (h.n_glass == 0 || std::fread(glass, sizeof(lt_glass), h.n_glass, f) == (size_t)h.n_glass);
-    ok = ok && std::fread(&p, sizeof p, 1, f) == 1 && std::fread(&stats, sizeof stats, 1, f) == 1;
+    ok = ok && std::fread(&p, sizeof p, 1, f) == 1 && std::fread(&stats, sizeof stats, 1, f) == 1 &&
+         p.n_surfaces == h.S && p.n_glasses == h.n_glass;
     uint64_t N = 1, NC = 1;
     for (int d = 0; ok && d < 5; ++d) {
-        ok = h.res[d] >= 2 && h.res[d] <= 4096;
+        ok = h.res[d] >= 2 && h.res[d] <= 4096 && std::isfinite(h.lo[d]) && std::isfinite(h.hi[d]) &&
+             h.hi[d] > h.lo[d];
         N *= (uint64_t)h.res[d];
         NC *= (uint64_t)(h.res[d] - 1);
     }
+    int pi = 0, pj = 0;
+    ok = ok && path_ij(h.S, h.path_id, &pi, &pj);
     ok = ok && N == h.n_nodes && NC == h.n_cells && N * kNodeFloats < (1ull << 32);
     if (!ok) { std::fclose(f); return fail(LT_EIO, "lt_map_load: %s is not a map file", path); }
     std::vector<float> node(N * 6);
@@ -1076,8 +1080,6 @@ lt_status lt_map_load(const char* path, lt_map** out)
     m->lens.presc.surfaces = m->lens.surf;
     m->lens.presc.glasses = m->lens.glass;
     lt_destroy_lens(lens);
-    int pi, pj;
-    path_ij(m->lens.S, h.path_id, &pi, &pj);
     m->path_id = h.path_id;
     m->n_nodes = N;
     m->n_cells = NC;

@@ -205,3 +205,19 @@ def test_server_entry_points_without_gpu():
     h = ctypes.c_void_p()
     rc = lt.lib().lt_server_create(None, ctypes.byref(h))
     assert rc != lt.LT_OK and not h.value
+
+
+def test_map_load_rejects_files_that_are_not_maps(tmp_path):
+    # missing, empty, wrong magic and truncated files are refused with
+    # LT_EIO before any device memory is touched
+    missing = tmp_path / "none.ltmap"
+    empty = tmp_path / "empty.ltmap"
+    empty.write_bytes(b"")
+    wrong = tmp_path / "wrong.ltmap"
+    wrong.write_bytes(b"NOTAMAP\0" + bytes(4096))
+    trunc = tmp_path / "trunc.ltmap"
+    trunc.write_bytes(b"LTMAP01\0" + (2).to_bytes(4, "little") + bytes(16))
+    for f in (missing, empty, wrong, trunc):
+        with pytest.raises(lt.LTError) as e:
+            lt.Map.load(str(f))
+        assert e.value.code == lt.LT_EIO, f
