@@ -368,7 +368,8 @@ def run_ours(args):
             torch.cuda.empty_cache()
         extra["serving"] = bench_serving(args, peaks, seconds=args.serve_seconds)
         line["configs"] = extra
-    if rank == 0 and not args.skip_cpu:
+    if world == 1 and not args.skip_cpu:
+        # the oracle baseline is taken at N = 1 only (the replicas' GPUs are not held for it)
         line["cpu_baseline"] = cpu_baseline(presc, rays)
     if rank == 0:
         print(json.dumps(line), flush=True)
