@@ -6,15 +6,24 @@ Sec. 5.1).  The tracer and the tabulated map are single-threaded FP64 C
 (``trace.c``, ``map.c``); the learned networks are FP64 numpy (``mlp.py``).
 
 Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's CPU
-baseline may import this package.  It shares no code with the CUDA library
-and never imports it.
+baseline (its ``cpu_baseline`` object and its ``--impl reference`` arm) may
+import this package.  It shares no code with the CUDA library and never
+imports it.
 
 Parity status per function (what pins it; see tests/test_oracle_*.py):
   or_trace       paraxial ABCD/lensmaker focal lengths, Fresnel closed forms,
                  plate closed form, Snell invariant, reversibility, symmetry,
-                 hand-enumerated tiny cases, the paper's path codes
+                 hand-enumerated tiny cases, the paper's path codes; even
+                 aspheres: the zero-asphere sphere, a Cartesian oval's
+                 perfect focus, a polynomial surface's hit and normal
   or_map_*       affine-field exactness, node reproduction, brute-force class
   mlp            finite differences, closed-form tiny networks, Adam step
+  splat          pixel-centre, pixel-corner and quarter-offset deposits,
+                 brute-force tent filter, conservation of weight, symmetry
+  mcmc           SplitMix64 reference outputs, the uniform stationary law
+                 over the valid region, chain invariants
+  reverse        a backward trace returns to the entrance ray, equal focal
+                 lengths from both sides, the stop keeps its plane
 """
 from __future__ import annotations
 
