@@ -402,7 +402,10 @@ lt_status lt_query_host(const lt_map* map, const lt_rays_in* in, const float* la
  *  - Every call shares the one array, and its counters are cleared on the
  *    call's stream: calls whose work overlaps on the GPU (different streams
  *    without an event between them) race and give wrong results.  Order
- *    them on one stream. */
+ *    them on one stream.
+ *  - While the library's profiler is on (lt_profile_enable), each launch
+ *    also records two CUDA events that the profiler creates; leave it off
+ *    where nothing may be created during the call. */
 #define LT_NOALLOC_MAX_RAYS (1 << 19)
 lt_status lt_query_noalloc(const lt_map* map, const lt_rays_in* in, const float* lambda_nm,
                            const lt_rays_out* out, size_t n, int32_t mode, lt_stream stream);
