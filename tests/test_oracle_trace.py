@@ -477,3 +477,56 @@ def test_path_sequence_counts():
                 assert surf[2 * j - i - 1] == i and typ[2 * j - i - 1] == 1
         ids = [oracle.path_ij(S, k) for k in range(1, S * (S - 1) // 2 + 1)]
         assert len(set(ids)) == S * (S - 1) // 2
+
+
+def test_throughput_is_the_amplitude_fresnel_product_along_paths(eleven):
+    """At every interface a traced ray meets, the oracle's throughput changes
+    by the transmittance (n2 cos t)/(n1 cos i) (t_s^2 + t_p^2)/2 or by the
+    reflectance (r_s^2 + r_p^2)/2 of the textbook amplitude coefficients
+    (Hecht, Optics, Sec. 4.6), recomputed here from the recorded hit, the
+    sphere's centre and Snell's law; the two add to 1 at each interface."""
+    L = oracle.Lens(eleven)
+    S = eleven.n_surfaces
+    zv = eleven.vertex_z()
+    rays = w.eleven_rays(eleven, 200)
+    checked = reflections = 0
+    for pid in [0, 5, 30, 54]:
+        path = oracle.path_ij(S, pid)
+        surf, typ, dirs = oracle.path_sequence(S, *path)
+        for r in range(len(rays)):
+            ray = [float(a[r]) for a in rays.arrays()]
+            v, out, st = L.trace_states(*ray, path=path)
+            lam = ray[5]
+            nmed = [L.index(m, lam) for m in range(S + 1)]
+            d_prev = np.array(ray[2:5], np.float64)
+            d_prev /= np.linalg.norm(d_prev)
+            I_prev = 1.0
+            for m in range(min(len(st), len(surf))):
+                s, t, dr = surf[m], typ[m], dirs[m]
+                p, dn, I = st[m, 0:3], st[m, 3:6], st[m, 6]
+                R = 1.0 / eleven.surfaces[s - 1].curvature
+                nv = (p - np.array([0.0, 0.0, zv[s - 1] + R])) / R
+                n1 = nmed[s - 1] if dr > 0 else nmed[s]
+                n2 = nmed[s] if dr > 0 else nmed[s - 1]
+                ci = abs(float(np.dot(d_prev, nv)))
+                sin_t = n1 / n2 * math.sqrt(max(0.0, 1.0 - ci * ci))
+                if sin_t >= 1.0:
+                    assert t == 1 and I == pytest.approx(I_prev, rel=1e-12)   # total reflection
+                else:
+                    ct = math.sqrt(1.0 - sin_t * sin_t)
+                    if t == 0:
+                        assert abs(float(np.dot(dn, nv))) == pytest.approx(ct, abs=1e-12)
+                    ts = 2 * n1 * ci / (n1 * ci + n2 * ct)
+                    tp = 2 * n1 * ci / (n2 * ci + n1 * ct)
+                    rs = (n1 * ci - n2 * ct) / (n1 * ci + n2 * ct)
+                    rp = (n2 * ci - n1 * ct) / (n2 * ci + n1 * ct)
+                    Tamp = n2 * ct / (n1 * ci) * 0.5 * (ts * ts + tp * tp)
+                    Ramp = 0.5 * (rs * rs + rp * rp)
+                    assert Tamp + Ramp == pytest.approx(1.0, abs=1e-12)
+                    assert I == pytest.approx(I_prev * (Tamp if t == 0 else Ramp), rel=1e-11)
+                reflections += t == 1
+                I_prev, d_prev = I, dn
+                checked += 1
+            if v == 1:
+                assert out[5] == pytest.approx(I_prev, rel=1e-12)
+    assert checked > 1000 and reflections > 50
