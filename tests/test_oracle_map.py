@@ -62,6 +62,40 @@ def test_affine_field_is_reproduced_exactly():
         assert np.allclose(out[2:5], dconst, atol=1e-15)
 
 
+def test_multilinear_field_is_reproduced_exactly():
+    """The interpolant is the tensor-product (multilinear) one, not just any
+    affine-exact scheme: a product of affine factors, one per coordinate
+    (x y s_x s_y lambda terms included), is reproduced exactly, which a
+    simplex or other piecewise-linear interpolant would not do."""
+    lo, hi = box()
+    lat = oracle.Lattice([6, 7, 5, 6, 4], lo, hi)
+    rng = np.random.default_rng(17)
+    a = rng.normal(size=5)
+    c = rng.normal(size=5) * 3.0
+    scale = np.array([1 / 12.0, 1 / 12.0, 1 / SMAX, 1 / SMAX, 1 / 400.0])
+
+    def field(q):
+        return float(np.prod(c + a * q * scale))
+
+    rays = w.entrance_rays(300, 8, 11.0)
+    worst = 0.0
+    for r in range(len(rays)):
+        ray = np.array([x[r] for x in rays.arrays()], np.float32)
+        cell = lat.cell_of(ray)
+        assert cell is not None
+        corner6 = np.zeros((32, 6))
+        for k in range(32):
+            q = np.array([node_coords(lat, d, cell[d] + ((k >> (4 - d)) & 1)) for d in range(5)],
+                         np.float64)
+            corner6[k] = [field(q), 0.0, 0.0, 0.0, 1.0, 0.0]
+        out, _ = lat.interpolate(corner6, ray)
+        v = np.array([ray[0], ray[1], ray[2] / np.float64(ray[4]), ray[3] / np.float64(ray[4]),
+                      ray[5]], np.float64)
+        want = field(v)
+        worst = max(worst, abs(out[0] - want) / (1 + abs(want)))
+    assert worst < 1e-11
+
+
 def test_query_at_a_node_returns_the_node_value():
     lo, hi = box()
     lat = oracle.Lattice([5, 5, 5, 5, 3], lo, hi)
