@@ -180,7 +180,7 @@ typedef struct {
 /* Brute-force FP32 trace of n rays along one path (Sec. 3, Eq. 6-7).
  * in/out/lambda_nm: device arrays of n entries.  Paths of more than 4
  * interactions run as two kernels per wave of at most 2^24 rays: one thread
- * per ray through the first two interactions (where most rays of a lens
+ * per ray through the first three interactions (where most rays of a lens
  * die), then the survivors, queued, in dense warps to the end; the queue
  * (54 B per ray of the wave) is taken stream-ordered from the library's
  * memory pool.  Shorter paths run as one kernel whose blocks compact their
@@ -221,7 +221,7 @@ typedef struct {
  * capacity after the stream synchronises.  Per-ray results are identical to
  * lt_trace of the same ray, path and wavelength.  The paths run in waves of
  * at most 2^24 (path, ray) pairs, each as two kernels: every ray through its
- * first two interactions, then the queued survivors to the end; the queue
+ * first three interactions, then the queued survivors to the end; the queue
  * (54 B per pair of a wave) comes stream-ordered from the library's pool.
  * Errors: LT_EINVAL (NULL pointer, misaligned array, n_paths < 1 or > 1024,
  * bad path id, capacity 0, n >= 2^32), LT_ENOMEM (queue allocation),
