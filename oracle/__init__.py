@@ -3,7 +3,8 @@
 Plain, slow, obviously-correct CPU reference for the lens-transport hot
 path (paper: Precomputed Lens Transport Maps, Sec. 3 Eq. 1-7, Sec. 4.2,
 Sec. 5.1).  The tracer and the tabulated map are single-threaded FP64 C
-(``trace.c``, ``map.c``); the learned networks are FP64 numpy (``mlp.py``).
+(``trace.c``, ``map.c``); the learned networks (``mlp.py``) and the
+polynomial-patch map (``poly.py``) are FP64 numpy.
 
 Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's CPU
 baseline (its ``cpu_baseline`` object and its ``--impl reference`` arm) may
@@ -17,6 +18,11 @@ Parity status per function (what pins it; see tests/test_oracle_*.py):
                  aspheres: the zero-asphere sphere, a Cartesian oval's
                  perfect focus, a polynomial surface's hit and normal
   or_map_*       affine-field exactness, node reproduction, brute-force class
+  poly           polynomial-patch map: exact reproduction of degree-<=D fields
+                 (and not of degree D + 1), the symmetry reduction's rotation
+                 invariance and round trip, unclipped = real lens on valid
+                 rays, brute-force classes, the exact trace within the
+                 certified residual
   mlp            finite differences, closed-form tiny networks, Adam step
   splat          pixel-centre, pixel-corner and quarter-offset deposits,
                  brute-force tent filter, conservation of weight, symmetry
