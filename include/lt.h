@@ -377,7 +377,9 @@ enum {
  * freed blocks for reuse, so steady-state calls do not reach cudaMalloc.
  * Batches of at most 2^18 rays run as one kernel whose blocks trace their
  * own queued rays (no queue, no pool); the results are the same either way.
- * Errors as lt_trace; LT_ENOMEM if the queue cannot be had. */
+ * Errors as lt_trace; LT_ENOMEM if the queue cannot be had; LT_EINVAL if the
+ * current device is not the one the map was built or loaded on (this holds
+ * for every call that takes a map). */
 lt_status lt_query(const lt_map* map, const lt_rays_in* in, const float* lambda_nm,
                    const lt_rays_out* out, size_t n, int32_t mode, lt_stream stream);
 /* Same with HOST arrays, in the pipelined chunks of lt_trace_host; returns
@@ -396,9 +398,11 @@ lt_status lt_query_host(const lt_map* map, const lt_rays_in* in, const float* la
  * LT_NOALLOC_MAX_RAYS rays after 8,448 bytes of counters: 14 MiB, held on
  * every device that loads the library until the process exits), so
  * n > LT_NOALLOC_MAX_RAYS is rejected with LT_EINVAL: split larger batches.
- *  - The first call on a device looks up the array's device address (a
- *    driver query, no allocation); make that first call before any stream
- *    capture.
+ *  - Every call looks up the array's device address on the current device
+ *    (a driver query, no allocation; the first one on a device may load the
+ *    library's device code there), so make the first call before any stream
+ *    capture.  The library's device arrays do not survive a device reset:
+ *    maps built before one must be rebuilt.
  *  - Every call shares the one array, and its counters are cleared on the
  *    call's stream: calls whose work overlaps on the GPU (different streams
  *    without an event between them) race and give wrong results.  Order
@@ -410,9 +414,95 @@ lt_status lt_query_host(const lt_map* map, const lt_rays_in* in, const float* la
 lt_status lt_query_noalloc(const lt_map* map, const lt_rays_in* in, const float* lambda_nm,
                            const lt_rays_out* out, size_t n, int32_t mode, lt_stream stream);
 
-/* Copy the map to host memory for inspection: node6 (n_nodes x 6 floats),
- * node_valid (n_nodes bytes, 1/0), cell_class (n_cells bytes: 0 INVALID,
- * 1 VALID, 2 BOUNDARY).  Any pointer may be NULL. */
+/*
+ * Polynomial-patch map of one path: the same factorised form (Sec. 4.2,
+ * Eq. 11), over the symmetry-reduced input of Sec. 4.1 (Eq. 10), with the
+ * regressor a least-squares polynomial per patch.
+ *   - Reduced input of an entrance ray (x, y, d) at lambda (nm): slopes
+ *     s = d_xy / d_z; r = |(x, y)|; (c, s') = (x, y) / r, or (1, 0) at r = 0;
+ *     p = c s_x + s' s_y, q' = c s_y - s' s_x, mirror m = -1 if q' < 0 else 1,
+ *     q = |q'|; w = (1000 / lambda)^2 (1/um^2, in which a Cauchy index is
+ *     affine).  u = (r, p, q, w) lies in the box [0, rho] x [-smax, smax] x
+ *     [0, smax] x [(1000/lam_hi)^2, (1000/lam_lo)^2]; the reduced ray is
+ *     (r, 0) with direction normalize(p, q, 1).
+ *   - Regressor: the box is split into patches[k] equal patches per axis; on
+ *     a patch the exit (x', y', d_x', d_y', I) of the reduced ray is a
+ *     polynomial of total degree `degree` in the patch-local xi = 2 (u - lo)
+ *     / h - 1, whose coefficients minimise the squared error over a tensor
+ *     grid of `samples` Chebyshev nodes cos(pi (k + 1/2) / samples) per axis,
+ *     traced (FP32) through the UNCLIPPED lens -- the same surfaces and path
+ *     with every clear aperture and the stop removed -- and solved by FP64
+ *     normal equations (FP64 reductions, Cholesky) on the GPU.  Apertures
+ *     decide only whether a ray passes, not where it goes, so this function
+ *     is smooth across the vignetting edge and the mask carries the occlusion.
+ *     A patch with fewer valid samples than terms, or a singular system, has
+ *     no fit (its cells are BOUNDARY).
+ *   - Mask: a class grid of patches[k] * cells[k] cells per axis whose nodes
+ *     are traced through the real lens: INVALID (16 corners invalid and no
+ *     valid fit ray inside), VALID (16 corners valid, the patch fitted, every
+ *     corner's and fit ray's exit position within max_residual_mm of the
+ *     polynomial's) or BOUNDARY, 2 bits per cell.
+ *   - Query (lt_query and every call that takes a map): VALID -> the
+ *     polynomial (FP32 Horner) at the ray's xi, d_z' = sqrt(1 - d_x'^2 -
+ *     d_y'^2), mirrored and rotated back; INVALID -> no output; BOUNDARY or
+ *     outside the box -> the exact tracer.  LT_QUERY_NO_MASK answers every ray
+ *     inside the box whose patch has a fit with the polynomial.
+ * The cell of a ray is decided in FP32 with correctly rounded operations in
+ * this order: i_z = 1 / d_z; s_x = d_x * i_z, s_y = d_y * i_z; r = sqrt(x*x +
+ * y*y); i_r = 1 / r; c = x * i_r, s' = y * i_r; p = c*s_x + s'*s_y; q' =
+ * c*s_y - s'*s_x; t = 1000 / lambda;
+ * w = t*t; g_k = (u_k - lo_k) * inv_k with lo_k, inv_k = C_k / (hi_k - lo_k)
+ * the FP32 roundings; cell_k = min(floor(g_k), C_k - 1); inside iff 0 <= g_k
+ * <= C_k.  Class-grid node i is the ray of v = lo + i * step (step_k the FP32
+ * rounding of (hi_k - lo_k) / C_k): x = v_r, y = 0, n2 = (p*p + q*q) + 1,
+ * len = sqrt(n2), d = (p / len, q / len, 1 / len), lambda = 1000 / sqrt(w).
+ */
+typedef struct {
+    int32_t path_id;
+    double rho;                  /* entrance radius bound (mm) */
+    double smax;                 /* slope bound: p in [-smax, smax], q in [0, smax] */
+    double lam_lo, lam_hi;       /* wavelength range (nm) */
+    int32_t degree;              /* total degree of every patch polynomial, 1..LT_POLY_MAX_DEGREE */
+    int32_t patches[4];          /* patches along (r, p, q, w), each >= 1 */
+    int32_t cells[4];            /* mask cells per patch along each axis, each >= 1 */
+    int32_t samples;             /* Chebyshev samples per axis and patch, degree + 1 .. 8 */
+    double max_residual_mm;      /* <= 0: no limit */
+    const float *fit_x, *fit_y, *fit_dx, *fit_dy, *fit_dz, *fit_lambda;  /* device; may be absent */
+    size_t n_fit;                /* extra traced rays that can only demote cells to BOUNDARY */
+} lt_poly_opts;
+
+#define LT_POLY_MAX_DEGREE 5
+
+typedef struct {
+    uint32_t patches, patches_fit, terms;
+    uint64_t samples_traced, samples_valid;
+    double sample_residual_max_mm;   /* largest |fit - traced| exit position over valid samples */
+    double corner_residual_max_mm;   /* over the corners of cells whose 16 corners are valid */
+} lt_poly_stats;
+
+/* Build a polynomial-patch map on the current device (see above).  Work runs
+ * on `stream`; the call returns when the map is complete.  lt_map_stats_get
+ * reports its mask (n_nodes: class-grid nodes; cells; fit rays, whose
+ * residuals are taken against the FP32 polynomial as queried), and
+ * lt_poly_stats_get the fit.  Errors: LT_EINVAL (bad option, empty box, bad
+ * path, misaligned fit arrays, more than 2^31 nodes), LT_ENOMEM, LT_ECUDA.
+ * The caller releases *out with lt_destroy_map. */
+lt_status lt_build_poly_map(const lt_lens* lens, const lt_poly_opts* opts, lt_map** out,
+                            lt_stream stream);
+/* LT_EINVAL for a table map. */
+lt_status lt_poly_stats_get(const lt_map* map, lt_poly_stats* out);
+/* Copy a polynomial-patch map's fit to host memory: coef (patches x terms x 5
+ * doubles, outputs x', y', d_x', d_y', I, patches row-major over (r, p, q, w)),
+ * exps (terms x 4 exponents of (xi_r, xi_p, xi_q, xi_w), in the order of
+ * coef's terms), patch_ok (patches bytes).  Any pointer may be NULL.
+ * LT_EINVAL for a table map. */
+lt_status lt_poly_export(const lt_map* map, double* coef, int32_t* exps, uint8_t* patch_ok);
+
+/* Copy the map to host memory for inspection: node6 (n_nodes x 6 floats; a
+ * table map only, NULL for a polynomial-patch map), node_valid (n_nodes
+ * bytes, 1/0), cell_class (n_cells bytes: 0 INVALID, 1 VALID, 2 BOUNDARY;
+ * cells and nodes row-major over the map's axes, the last fastest).  Any
+ * pointer may be NULL. */
 lt_status lt_map_export(const lt_map* map, float* node6, uint8_t* node_valid,
                         uint8_t* cell_class);
 

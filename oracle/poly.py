@@ -41,9 +41,10 @@ least-squares polynomial per patch fitted to traced rays:
 FP32 rule (shared by definition with the CUDA path, so both pick the same
 cell for a ray on a face): the reduced coordinates and the class-grid
 coordinate g_k = (u_k - lo_k) * inv_k are computed in FP32 with correctly
-rounded operations in the order written above (s = d/d_z; r2 = x*x + y*y;
-r = sqrt(r2); c = x / r; p = c*s_x + s_*s_y; q' = c*s_y - s_*s_x;
-t = 1000 / lambda; w = t*t); lo_k, step_k = (hi_k - lo_k) / C_k and
+rounded operations in this order: i_z = 1 / d_z; s = d_xy * i_z; r2 = x*x +
+y*y; r = sqrt(r2); i_r = 1 / r; c = x * i_r, s_ = y * i_r; p = c*s_x +
+s_*s_y; q' = c*s_y - s_*s_x; t = 1000 / lambda; w = t*t; lo_k, step_k =
+(hi_k - lo_k) / C_k and
 inv_k = C_k / (hi_k - lo_k) are the FP32 roundings of the FP64 values;
 cell_k = min(floor(g_k), C_k - 1), inside iff 0 <= g_k <= C_k.  Node rays:
 v = lo + i * step; x = v_r; y = 0; n2 = (p*p + q*q) + 1; len = sqrt(n2);
@@ -107,14 +108,15 @@ def reduce_f32(x, y, dx, dy, dz, lam):
     with np.errstate(all="ignore"):
         ok = (np.isfinite(x) & np.isfinite(y) & np.isfinite(dx) & np.isfinite(dy) & np.isfinite(dz)
               & np.isfinite(lam) & (dz > 0) & (lam > 0))
-        sx = dx / dz
-        sy = dy / dz
+        idz = F32(1) / dz
+        sx = dx * idz
+        sy = dy * idz
         r2 = x * x + y * y
         r = np.sqrt(r2)
         pos = r > 0
-        rs = np.where(pos, r, F32(1))
-        c = np.where(pos, x / rs, F32(1)).astype(F32)
-        s = np.where(pos, y / rs, F32(0)).astype(F32)
+        ir = F32(1) / np.where(pos, r, F32(1))
+        c = np.where(pos, x * ir, F32(1)).astype(F32)
+        s = np.where(pos, y * ir, F32(0)).astype(F32)
         p = c * sx + s * sy
         qq = c * sy - s * sx
         q = np.abs(qq)
@@ -153,8 +155,9 @@ class PolyGrid:
     """Box, patch grid and class grid, with the FP32 constants of the rule."""
 
     def __init__(self, rho, smax, lam_lo, lam_hi, patches, cells):
-        self.lo = np.array([0.0, -smax, 0.0, (1000.0 / lam_hi) ** 2], np.float64)
-        self.hi = np.array([rho, smax, smax, (1000.0 / lam_lo) ** 2], np.float64)
+        t_lo, t_hi = 1000.0 / lam_hi, 1000.0 / lam_lo
+        self.lo = np.array([0.0, -smax, 0.0, t_lo * t_lo], np.float64)
+        self.hi = np.array([rho, smax, smax, t_hi * t_hi], np.float64)
         self.P = np.asarray(patches, np.int64)
         self.m = np.asarray(cells, np.int64)
         self.C = self.P * self.m
@@ -212,11 +215,14 @@ class PolyMap:
 
     def __init__(self, presc, path, rho, smax, lam_lo, lam_hi, degree, patches, cells, samples,
                  tol: float = float("inf"), fit_rays=None,
-                 sample_fn: Optional[Callable] = None, node_fn: Optional[Callable] = None):
+                 sample_fn: Optional[Callable] = None, node_fn: Optional[Callable] = None,
+                 build_mask: bool = True):
         """sample_fn(u [n,4]) -> (values [n,5], valid [n]) replaces the
         unclipped trace of the fit samples, and node_fn(ray arrays) -> (out
         [n,6], valid [n]) the real trace of the class-grid nodes (the pins
-        feed known fields through them)."""
+        feed known fields through them).  build_mask False: no class table;
+        classes come from classify_fresh, cell by cell (for maps too large to
+        classify whole here)."""
         from oracle import Lens
         self.presc, self.path, self.tol, self.D = presc, tuple(path), float(tol), int(degree)
         self.lens = Lens(presc)
@@ -247,6 +253,9 @@ class PolyMap:
             self.coef[pid] = c
             self.patch_ok[pid] = True
             self.sample_res[pid] = float(np.abs(Av @ c - val[ok]).max())
+        self.fit_rays = fit_rays
+        if not build_mask:
+            return
         # mask: class-grid nodes through the real lens
         shape = G.node_shape()
         idx = np.array(list(np.ndindex(*shape)), np.int64)
@@ -341,6 +350,55 @@ class PolyMap:
             cls[tuple(cells.T)] = np.where(worst <= self.tol, CELL_VALID, CELL_BOUNDARY)
         return cls, res
 
+    def classify_fresh(self, cell):
+        """(class, largest residual) of one cell from its 16 corner rays traced
+        here and the map's fit rays that fall in it."""
+        G = self.grid
+        cell = np.asarray(cell, np.int64)
+        corners = np.array(list(itertools.product((0, 1), repeat=4)), np.int64)
+        arrs = G.node_rays_f32(cell + corners)
+        out, v, _, _ = self.lens.trace(_rays(arrs), self.path)
+        vs = v == 1
+        if not vs.any():
+            cls, res = CELL_INVALID, 0.0
+        elif not vs.all():
+            cls, res = CELL_BOUNDARY, 0.0
+        else:
+            P = cell // G.m
+            pid = int(np.ravel_multi_index(tuple(P), tuple(G.P)))
+            if not self.patch_ok[pid]:
+                cls, res = CELL_BOUNDARY, 0.0
+            else:
+                xi = 2.0 * (cell + corners - P * G.m) / G.m - 1.0
+                pred = self.evaluate(P, xi)
+                res = float(np.hypot(pred[:, 0] - out[:, 0], pred[:, 1] - out[:, 1]).max())
+                cls = CELL_VALID if res <= self.tol else CELL_BOUNDARY
+        if self.fit_rays is not None and len(self.fit_rays):
+            if not hasattr(self, "_fit_cells"):
+                u32, ok = reduce_f32(*self.fit_rays.arrays())
+                g, inside = G.grid_coords(u32)
+                self._fit_in = inside & ok
+                self._fit_cells = np.ravel_multi_index(tuple(G.cell_of(g).T), tuple(G.C))
+            cid = int(np.ravel_multi_index(tuple(cell), tuple(G.C)))
+            idx = np.nonzero(self._fit_in & (self._fit_cells == cid))[0]
+            if idx.size and cls != CELL_BOUNDARY:
+                sub = self.fit_rays.subset(idx)
+                o, v, _, _ = self.lens.trace(sub, self.path)
+                valid = v == 1
+                if cls == CELL_INVALID and valid.any():
+                    cls = CELL_BOUNDARY
+                elif cls == CELL_VALID:
+                    if not valid.all():
+                        cls = CELL_BOUNDARY
+                    else:
+                        pred = self.predict(sub, np.tile(cell, (idx.size, 1)), np.arange(idx.size))
+                        for j in range(idx.size):
+                            r = math.hypot(pred[j][0] - o[j, 0], pred[j][1] - o[j, 1])
+                            res = max(res, r)
+                        if res > self.tol:
+                            cls = CELL_BOUNDARY
+        return cls, res
+
     def _apply_fit_rays(self, rays):
         G = self.grid
         u32, ok = reduce_f32(*rays.arrays())
@@ -389,18 +447,25 @@ class PolyMap:
                         dzp, I], axis=1)
         return {int(r): out[j] for j, r in enumerate(idx)}
 
-    def query(self, rays, use_mask: bool = True):
+    def locate(self, rays):
+        """(inside [n], class-grid cells [n,4]) by the FP32 rule."""
+        u32, ok = reduce_f32(*rays.arrays())
+        g, inside = self.grid.grid_coords(u32)
+        return inside & ok, self.grid.cell_of(g)
+
+    def query(self, rays, use_mask: bool = True, classes=None):
         """(out [n,6], flags [n]): bit0 valid, bit3 bad input, bit4 answered by the
         exact tracer, bit5 outside the box.  use_mask False: every ray inside the
-        box whose patch has a fit gets the regressor's answer (Fig. 6 ablation)."""
+        box whose patch has a fit gets the regressor's answer (Fig. 6 ablation).
+        classes: the rays' cell classes when the map holds no class table."""
         G = self.grid
         n = len(rays)
-        u32, ok = reduce_f32(*rays.arrays())
-        g, inside = G.grid_coords(u32)
-        inside &= ok
-        cells = G.cell_of(g)
+        inside, cells = self.locate(rays)
         cls = np.full(n, CELL_BOUNDARY, np.uint8)
-        cls[inside] = self.cell_class[tuple(cells[inside].T)]
+        if classes is not None:
+            cls[inside] = np.asarray(classes, np.uint8)[inside]
+        else:
+            cls[inside] = self.cell_class[tuple(cells[inside].T)]
         if not use_mask:
             pid = np.ravel_multi_index(tuple((cells // G.m).T), tuple(G.P))
             cls[inside] = np.where(self.patch_ok[pid[inside]], CELL_VALID, CELL_BOUNDARY)

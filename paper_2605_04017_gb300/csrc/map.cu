@@ -21,7 +21,6 @@
 namespace lt {
 
 constexpr int kQBlock = 128;   // rays per chunk (and threads per block) of the trace kernel
-constexpr uint32_t kOutsideBit = 0x80000000u;
 
 // ------------------------------------------------------------------ lattice (FP32 rule)
 
@@ -697,8 +696,8 @@ static lt_status launch_classify(const lt_map* map, const RaysInDev& in, const R
 }
 
 // the tracer over the queue of a classify launch of n rays, on `st`
-static lt_status launch_queue_trace(const lt_map* map, const RaysOutDev& out, uint32_t n, const TraceQueue& Q,
-                                    cudaStream_t st)
+lt_status launch_queue_trace(const lt_map* map, const RaysOutDev& out, uint32_t n, const TraceQueue& Q,
+                             cudaStream_t st)
 {
     const void* trace = map->cauchy ? (const void*)map_trace_kernel<true> : (const void*)map_trace_kernel<false>;
     // resident blocks, but no more than a quarter of the rays could keep busy
@@ -724,18 +723,17 @@ static lt_status launch_queue_trace(const lt_map* map, const RaysOutDev& out, ui
 lt_status launch_query_with(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
                             int mode, const TraceQueue& Q, cudaStream_t st)
 {
+    if (map->kind == LT_MAP_KIND_POLY) return launch_poly_query(map, in, out, n, mode, &Q, st);
     LT_CUDA_TRY(cudaMemsetAsync(Q.count, 0, kQHeaderBytes, st));
     lt_status s = launch_classify(map, in, out, n, mode, Q, st);
     if (s != LT_OK) return s;
     return launch_queue_trace(map, out, n, Q, st);
 }
 
-// Batches up to this size run as the one fused kernel.
-constexpr uint32_t kFusedMaxRays = 1u << 18;
-
 lt_status launch_query(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
                        int mode, cudaStream_t st)
 {
+    if (map->kind == LT_MAP_KIND_POLY) return launch_poly_query(map, in, out, n, mode, nullptr, st);
     if (n <= kFusedMaxRays) {
         const unsigned blocks = (n + kQTile - 1) / kQTile;
         const bool table = mode == LT_QUERY_TABLE;
@@ -762,6 +760,30 @@ lt_status launch_query(const lt_map* map, const RaysInDev& in, const RaysOutDev&
     return s;
 }
 
+lt_status launch_map_classify(const uint8_t* corner_bits, const uint32_t* seen, const uint32_t* resmax,
+                              float tol, uint32_t* cls, uint32_t NC, unsigned long long* counts,
+                              cudaStream_t st)
+{
+    uint32_t tol_bits;
+    std::memcpy(&tol_bits, &tol, 4);
+    const uint32_t NW = (NC + 15) / 16;
+    map_classify_kernel<<<(NW + 255) / 256, 256, 0, st>>>(corner_bits, seen, resmax, tol_bits, cls, NC, counts);
+    LT_CUDA_TRY(cudaGetLastError());
+    return LT_OK;
+}
+
+// A map's tables live on the device it was built or loaded on; a call made
+// with another device current would launch there and read them across
+// devices.
+lt_status check_map_device(const lt_map* m, const char* who)
+{
+    int dev = 0;
+    LT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != m->device)
+        return fail(LT_EINVAL, "%s: the map lives on device %d but device %d is current", who, m->device, dev);
+    return LT_OK;
+}
+
 }  // namespace lt
 
 using namespace lt;
@@ -771,6 +793,10 @@ lt_map::~lt_map()
     if (node) cudaFree(node);
     if (node_valid) cudaFree(node_valid);
     if (cls) cudaFree(cls);
+    if (coef4) cudaFree(coef4);
+    if (coefI) cudaFree(coefI);
+    if (coef64) cudaFree(coef64);
+    if (patch_ok) cudaFree(patch_ok);
 }
 
 extern "C" {
@@ -936,6 +962,8 @@ lt_status lt_query(const lt_map* m, const lt_rays_in* in, const float* lam, cons
     if (mode != LT_QUERY_TABLE && mode != LT_QUERY_NO_MASK) return fail(LT_EINVAL, "lt_query: unknown mode %d", mode);
     lt_status s = check_io(in, lam, out, n, "lt_query");
     if (s != LT_OK || n == 0) return s;
+    s = check_map_device(m, "lt_query");
+    if (s != LT_OK) return s;
     if (n >= (1ull << 31)) return fail(LT_EINVAL, "lt_query: n must be < 2^31");
     RaysInDev din{in->x, in->y, in->dx, in->dy, in->dz, lam};
     RaysOutDev dout{out->x, out->y, out->dx, out->dy, out->dz, out->I, out->flags};
@@ -954,6 +982,8 @@ lt_status lt_query_host(const lt_map* m, const lt_rays_in* in, const float* lam,
                         out->dx, out->dy, out->dz, out->I, out->flags};
     for (const void* p : ps)
         if (!p) return fail(LT_EINVAL, "lt_query_host: NULL ray array");
+    lt_status sd = check_map_device(m, "lt_query_host");
+    if (sd != LT_OK) return sd;
     return run_host_pipelined(in, lam, out, n, [&](const RaysInDev& a, const RaysOutDev& b, size_t k, cudaStream_t st) {
         return launch_query(m, a, b, (uint32_t)k, mode, st);
     });
@@ -963,6 +993,8 @@ lt_status lt_map_export(const lt_map* m, float* node6, uint8_t* node_valid, uint
 {
     clear_error();
     if (!m) return fail(LT_EINVAL, "lt_map_export: NULL map");
+    if (node6 && m->kind != LT_MAP_KIND_TABLE)
+        return fail(LT_EINVAL, "lt_map_export: a polynomial-patch map has no node table (node6 must be NULL)");
     if (node6)
         LT_CUDA_TRY(cudaMemcpy2D(node6, 6 * sizeof(float), m->node, kNodeFloats * sizeof(float),
                                  6 * sizeof(float), m->n_nodes, cudaMemcpyDeviceToHost));
@@ -1138,25 +1170,16 @@ namespace {
 constexpr size_t kNoallocQueueBytes = query_scratch_bytes(LT_NOALLOC_MAX_RAYS);
 __device__ __align__(256) unsigned char g_noalloc_queue[kNoallocQueueBytes];
 
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[64] = {};
-
-// Device address of the array on the current device, looked up once per
-// device.  In host code the symbol is only a host-side stand-in; kernels must
-// be given this address.
+// Device address of the array on the current device.  In host code the
+// symbol is only a host-side stand-in; kernels must be given this address.
+// It is looked up on every call (a driver query that allocates nothing), so a
+// device reset by the host application leaves no stale address behind.
 lt_status noalloc_queue(void** out)
 {
-    int dev = 0;
-    LT_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return fail(LT_EINVAL, "lt_query_noalloc: device index %d out of range", dev);
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_queue);
-        if (e != cudaSuccess || !p) return cuda_fail(e, "lt_query_noalloc: cudaGetSymbolAddress");
-        g_noalloc_ptr[dev] = p;
-    }
-    *out = g_noalloc_ptr[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_queue);
+    if (e != cudaSuccess || !p) return cuda_fail(e, "lt_query_noalloc: cudaGetSymbolAddress");
+    *out = p;
     return LT_OK;
 }
 }  // namespace
@@ -1174,6 +1197,8 @@ extern "C" lt_status lt_query_noalloc(const lt_map* m, const lt_rays_in* in, con
                     n, LT_NOALLOC_MAX_RAYS);
     lt_status s = check_io(in, lam, out, n, "lt_query_noalloc");
     if (s != LT_OK || n == 0) return s;
+    s = check_map_device(m, "lt_query_noalloc");
+    if (s != LT_OK) return s;
     void* q = nullptr;
     s = noalloc_queue(&q);
     if (s != LT_OK) return s;

@@ -60,10 +60,51 @@ lt_status launch_query(const lt_map* map, const RaysInDev& in, const RaysOutDev&
 lt_status launch_query_with(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
                             int mode, const TraceQueue& Q, cudaStream_t st);
 
+// LT_EINVAL unless the current device is the one the map lives on.
+lt_status check_map_device(const lt_map* m, const char* who);
+
+// Pieces of the table map that the polynomial-patch map shares (map.cu).
+constexpr uint32_t kOutsideBit = 0x80000000u;   // queue tag bit: ray outside the box
+constexpr uint32_t kFusedMaxRays = 1u << 18;    // batches up to this size run as one fused kernel
+// the exact tracer over a query's queue (map_trace_kernel), on `st`
+lt_status launch_queue_trace(const lt_map* map, const RaysOutDev& out, uint32_t n, const TraceQueue& Q,
+                             cudaStream_t st);
+// the 2-bit classes from per-cell corner bits (bit0: class may be VALID, bit1:
+// every corner invalid), fit-ray sightings (2 bits per cell: valid / invalid
+// seen) and fit-ray residual maxima (FP32 bits; NULL: none); counts[0..2] +=
+// INVALID, VALID, BOUNDARY cells
+lt_status launch_map_classify(const uint8_t* corner_bits, const uint32_t* seen, const uint32_t* resmax,
+                              float tol, uint32_t* cls, uint32_t NC, unsigned long long* counts,
+                              cudaStream_t st);
+
+// The polynomial-patch map as its query kernels see it (a __grid_constant__
+// parameter): FP32 constants of the class grid over (r, p, q, w), the patch
+// structure and the device tables.
+struct PolyDev {
+    float lo[4], inv[4], cmax[4], two_over_m[4];
+    int C[4], m[4], P[4];
+    uint32_t mdiv[4];                   // ceil(2^32 / m): cell / m = umulhi(cell, mdiv) for cell < 2^16
+    uint32_t cstride[4], pstride[4];    // class-grid cell and patch strides (w fastest)
+    int T, degree, n_patches;
+    const float4* c4;                   // [patch][term]: x', y', d_x', d_y' coefficients
+    const float* cI;                    // [patch][term]: I coefficients
+    const uint8_t* patch_ok;            // [patch]: 1 if the patch has a fit
+    const uint32_t* cls;                // 2 bits per class-grid cell
+};
+
+// The polynomial-patch map's query on `st` (launch_query / launch_query_with
+// dispatch here for such maps); Q may be NULL: then batches of at most
+// kFusedMaxRays run as one kernel and larger ones take a queue from the pool.
+lt_status launch_poly_query(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
+                            int mode, const TraceQueue* Q, cudaStream_t st);
+
 }  // namespace lt
+
+enum { LT_MAP_KIND_TABLE = 0, LT_MAP_KIND_POLY = 1 };
 
 struct lt_map {
     lt_lens lens;             // copy of the lens the map was built on
+    int kind = LT_MAP_KIND_TABLE;
     int path_id = 0;
     int res[5] = {};
     double lo[5] = {}, hi[5] = {};
@@ -75,6 +116,14 @@ struct lt_map {
     int device = 0;
     bool cauchy = true;       // every glass of the lens is Cauchy (single-FMA dispersion)
     lt_map_stats stats = {};
-    lt::MapDev dev;
+    lt::MapDev dev;           // the lens and path (for the fallback tracer); table constants
+    // polynomial-patch maps
+    lt_poly_opts popts = {};  // the build options (fit arrays cleared)
+    lt_poly_stats pstats = {};
+    lt::PolyDev pdev = {};
+    float4* coef4 = nullptr;
+    float* coefI = nullptr;
+    double* coef64 = nullptr; // patches x terms x 5, the FP64 fit
+    uint8_t* patch_ok = nullptr;
     ~lt_map();
 };

@@ -1,0 +1,1226 @@
+// Polynomial-patch lens transport map: build (unclipped-lens samples, FP64
+// least-squares fit per patch, class-grid nodes through the real lens, cell
+// classes) and query (symmetry reduction, mask lookup, FP32 Horner
+// evaluation of the patch polynomial, exact-tracer fallback).
+//
+// The paper's factorisation (Sec. 4.2, Eq. 11) over its symmetry-reduced
+// input (Sec. 4.1, Eq. 10): the mask g is 2 bits per class-grid cell, the
+// regressor f a polynomial per patch fitted to traced rays.  The fit traces
+// the unclipped lens (apertures and stop removed): apertures only decide
+// whether a ray passes, so the function the valid rays follow is smooth
+// across the vignetting edge and a low-degree polynomial on a coarse patch
+// reproduces it to the FP32 tracer's own error, while the mask resolves the
+// occlusion on a finer grid.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "map_internal.h"
+#include "profile.h"
+#include "tracer.cuh"
+
+namespace lt {
+
+constexpr int kPolyTile = 256;        // rays per block of the query kernels
+constexpr int kMaxSamplesAxis = 8;
+
+__host__ __device__ constexpr int poly_terms(int D) { return (D + 1) * (D + 2) * (D + 3) * (D + 4) / 24; }
+
+// Exponents (a, b, c, e) of (xi_r, xi_p, xi_q, xi_w) in the order the Horner
+// evaluation consumes coefficients: a, then b, then c, then e, each
+// descending, over a + b + c + e <= D.
+static void horner_exponents(int D, std::vector<int32_t>& e)
+{
+    e.clear();
+    for (int a = D; a >= 0; --a)
+        for (int b = D - a; b >= 0; --b)
+            for (int c = D - a - b; c >= 0; --c)
+                for (int d = D - a - b - c; d >= 0; --d) {
+                    e.push_back(a);
+                    e.push_back(b);
+                    e.push_back(c);
+                    e.push_back(d);
+                }
+}
+
+// ------------------------------------------------------------------ evaluation
+
+// The five outputs of a patch polynomial: (x', y') and (d_x', d_y') as pairs
+// (packed FP32x2 FMAs: two IEEE FMAs per instruction, bit for bit the scalar
+// ones), I alone.
+struct Acc5 {
+    float2 p, d;
+    float I;
+};
+
+__device__ __forceinline__ void acc_load(Acc5& a, const float4 v, float vi)
+{
+    a.p = make_float2(v.x, v.y);
+    a.d = make_float2(v.z, v.w);
+    a.I = vi;
+}
+__device__ __forceinline__ void acc_step(Acc5& a, float t, const float4 v, float vi)
+{
+    const float2 tt = make_float2(t, t);
+    a.p = __ffma2_rn(a.p, tt, make_float2(v.x, v.y));
+    a.d = __ffma2_rn(a.d, tt, make_float2(v.z, v.w));
+    a.I = fmaf(a.I, t, vi);
+}
+__device__ __forceinline__ void acc_step(Acc5& a, float t, const Acc5& v)
+{
+    const float2 tt = make_float2(t, t);
+    a.p = __ffma2_rn(a.p, tt, v.p);
+    a.d = __ffma2_rn(a.d, tt, v.d);
+    a.I = fmaf(a.I, t, v.I);
+}
+
+// The patch polynomial at xi by nested Horner steps (T - 1 FMAs per output):
+// P = sum_a xi_r^a Q_a(xi_p, xi_q, xi_w), each Q_a likewise in the next
+// variable; coefficients are read in horner_exponents order.
+template <int D>
+__device__ __forceinline__ Acc5 poly_eval(const float4* __restrict__ C4, const float* __restrict__ CI,
+                                          const float xi[4])
+{
+    Acc5 A0;
+    int k = 0;
+#pragma unroll
+    for (int a = D; a >= 0; --a) {
+        Acc5 A1;
+#pragma unroll
+        for (int b = D - a; b >= 0; --b) {
+            Acc5 A2;
+#pragma unroll
+            for (int c = D - a - b; c >= 0; --c) {
+                Acc5 A3;
+#pragma unroll
+                for (int e = D - a - b - c; e >= 0; --e) {
+                    const float4 v = __ldg(C4 + k);
+                    const float vi = __ldg(CI + k);
+                    ++k;
+                    if (e == D - a - b - c) acc_load(A3, v, vi);
+                    else acc_step(A3, xi[3], v, vi);
+                }
+                if (c == D - a - b) A2 = A3;
+                else acc_step(A2, xi[2], A3);
+            }
+            if (b == D - a) A1 = A2;
+            else acc_step(A1, xi[1], A2);
+        }
+        if (a == D) A0 = A1;
+        else acc_step(A0, xi[0], A1);
+    }
+    return A0;
+}
+
+// The FP32 rule for the reduced coordinates (documented in lt.h): three
+// correctly rounded divisions (1 / d_z, 1 / r, 1000 / lambda), every other
+// operation a correctly rounded product, sum or square root; false for
+// unusable input (non-finite, d_z <= 0, lambda <= 0).
+__device__ __forceinline__ bool poly_reduce(float x, float y, float dx, float dy, float dz, float lam,
+                                            float u[4], float& c, float& s, float& m)
+{
+    const bool ok = isfinite(x) & isfinite(y) & isfinite(dx) & isfinite(dy) & isfinite(dz) &
+                    isfinite(lam) & (dz > 0.0f) & (lam > 0.0f);
+    if (!ok) return false;
+    const float idz = __frcp_rn(dz);
+    const float sx = __fmul_rn(dx, idz), sy = __fmul_rn(dy, idz);
+    const float r = __fsqrt_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)));
+    c = 1.0f;
+    s = 0.0f;
+    if (r > 0.0f) {
+        const float ir = __frcp_rn(r);
+        c = __fmul_rn(x, ir);
+        s = __fmul_rn(y, ir);
+    }
+    const float p = __fadd_rn(__fmul_rn(c, sx), __fmul_rn(s, sy));
+    const float qq = __fsub_rn(__fmul_rn(c, sy), __fmul_rn(s, sx));
+    m = qq < 0.0f ? -1.0f : 1.0f;
+    const float t = __fdiv_rn(1000.0f, lam);
+    u[0] = r;
+    u[1] = p;
+    u[2] = fabsf(qq);
+    u[3] = __fmul_rn(t, t);
+    return true;
+}
+
+// Read-once loads that leave L1 to the coefficient table: the rays' inputs
+// stream through once, and the class lookups are random 4-byte reads of an
+// L2-resident table that would otherwise each pull a 128-byte line into L1.
+__device__ __forceinline__ float ld_stream(const float* p)
+{
+    float v;
+    asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p)
+{
+    uint32_t v;
+    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t poly_patch_of(const PolyDev& P, int k, uint32_t cell)
+{
+    return P.m[k] == 1 ? cell : __umulhi(cell, P.mdiv[k]);
+}
+
+// Class-grid cell, patch and patch-local xi of reduced coordinates u; false
+// outside the box.
+__device__ __forceinline__ bool poly_locate(const PolyDev& P, const float u[4], uint32_t& cid, uint32_t& pid,
+                                            float xi[4])
+{
+    bool inside = true;
+    cid = 0;
+    pid = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float g = __fmul_rn(__fsub_rn(u[k], P.lo[k]), P.inv[k]);
+        inside &= (g >= 0.0f) & (g <= P.cmax[k]);
+        int cell = inside ? (int)floorf(g) : 0;
+        cell = min(max(cell, 0), P.C[k] - 1);
+        const uint32_t pk = poly_patch_of(P, k, (uint32_t)cell);
+        cid += (uint32_t)cell * P.cstride[k];
+        pid += pk * P.pstride[k];
+        xi[k] = fmaf(g - (float)(pk * (uint32_t)P.m[k]), P.two_over_m[k], -1.0f);
+    }
+    return inside;
+}
+
+__device__ __forceinline__ uint32_t poly_class(const PolyDev& P, uint32_t cid)
+{
+    return (ld_stream(P.cls + (cid >> 4)) >> ((cid & 15u) * 2u)) & 3u;
+}
+
+// Exit ray in the input frame from the patch polynomial at xi (mirror m,
+// rotation (c, s)).
+template <int D>
+__device__ __forceinline__ void poly_output(const PolyDev& P, uint32_t pid, const float xi[4], float c, float s,
+                                            float m, float o[6])
+{
+    const Acc5 a = poly_eval<D>(P.c4 + (size_t)pid * poly_terms(D), P.cI + (size_t)pid * poly_terms(D), xi);
+    const float yp = m * a.p.y, dyp = m * a.d.y;
+    const float dz2 = fmaf(-a.d.x, a.d.x, fmaf(-dyp, dyp, 1.0f));
+    o[0] = fmaf(c, a.p.x, -s * yp);
+    o[1] = fmaf(s, a.p.x, c * yp);
+    o[2] = fmaf(c, a.d.x, -s * dyp);
+    o[3] = fmaf(s, a.d.x, c * dyp);
+    o[4] = dz2 > 0.0f ? sqrtf(dz2) : 0.0f;
+    o[5] = a.I;
+}
+
+// A ray of a query after classification.
+struct PolyRay {
+    bool ip, tr;                // answered by the polynomial; to be traced (BOUNDARY or outside)
+    uint32_t tag;               // ray index (| kOutsideBit)
+    float x, y, dx, dy, dz, lam;
+    float o[6];
+};
+
+template <int D, int MODE>
+__device__ __forceinline__ void poly_answer(const PolyDev& P, const RaysInDev& in, uint32_t n, uint32_t r,
+                                            PolyRay& c)
+{
+    c.ip = false;
+    c.tr = false;
+    c.tag = r;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) c.o[k] = 0.0f;
+    c.x = c.y = c.dx = c.dy = c.dz = c.lam = 0.0f;
+    if (r >= n) return;
+    c.x = ld_stream(in.x + r);
+    c.y = ld_stream(in.y + r);
+    c.dx = ld_stream(in.dx + r);
+    c.dy = ld_stream(in.dy + r);
+    c.dz = ld_stream(in.dz + r);
+    c.lam = ld_stream(in.lam + r);
+    float u[4], xi[4], cs, sn, m;
+    uint32_t cid, pid;
+    if (!poly_reduce(c.x, c.y, c.dx, c.dy, c.dz, c.lam, u, cs, sn, m) || !poly_locate(P, u, cid, pid, xi)) {
+        c.tr = true;
+        c.tag |= kOutsideBit;
+        return;
+    }
+    uint32_t k;
+    if (MODE == LT_QUERY_TABLE) k = poly_class(P, cid);
+    else k = __ldg(P.patch_ok + pid) ? (uint32_t)LT_CELL_VALID : (uint32_t)LT_CELL_BOUNDARY;
+    if (k == LT_CELL_VALID) {
+        poly_output<D>(P, pid, xi, cs, sn, m, c.o);
+        c.ip = true;
+    } else if (k != LT_CELL_INVALID) {
+        c.tr = true;
+    }
+}
+
+__device__ __forceinline__ void poly_store(const RaysOutDev& out, uint32_t r, const float o[6], uint32_t flags)
+{
+    __stcs(out.x + r, o[0]);
+    __stcs(out.y + r, o[1]);
+    __stcs(out.dx + r, o[2]);
+    __stcs(out.dy + r, o[3]);
+    __stcs(out.dz + r, o[4]);
+    __stcs(out.I + r, o[5]);
+    out.flags[r] = (uint8_t)flags;
+}
+
+// ------------------------------------------------------------------ query kernels
+
+// Large batches: every lane answers its ray (polynomial, or "no output" for
+// an INVALID cell) and writes its row -- a placeholder for a ray to be
+// traced -- and BOUNDARY / outside rays go to the launch's trace queue (one
+// atomic per warp on the block's segment counter); map_trace_kernel then
+// traces the queue.
+template <int D, int MODE>
+__global__ void __launch_bounds__(kPolyTile)
+poly_query_kernel(const __grid_constant__ PolyDev P, RaysInDev in, RaysOutDev out, uint32_t n, TraceQueue Q)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t r = blockIdx.x * kPolyTile + threadIdx.x;
+    PolyRay c;
+    poly_answer<D, MODE>(P, in, n, r, c);
+    const unsigned mq = __ballot_sync(full, c.tr);
+    if (mq) {
+        const int leader = __ffs(mq) - 1;
+        uint32_t b = 0;
+        const uint32_t seg = blockIdx.x % kQSegs;
+        if (lane == leader) b = atomicAdd(Q.count + seg * kQCountStride, (uint32_t)__popc(mq));
+        b = __shfl_sync(full, b, leader);
+        if (c.tr) {
+            const uint32_t k = seg * Q.segcap + b + __popc(mq & ((1u << lane) - 1u));
+            Q.x[k] = c.x;
+            Q.y[k] = c.y;
+            Q.dx[k] = c.dx;
+            Q.dy[k] = c.dy;
+            Q.dz[k] = c.dz;
+            Q.lam[k] = c.lam;
+            Q.tag[k] = c.tag;
+        }
+    }
+    if (r < n) poly_store(out, r, c.o, c.ip ? LT_FLAG_VALID : 0u);
+}
+
+// Large batches, maps of at most kSortMaxPatches patches: each block takes a
+// tile of kSortTile rays and
+//  A. classifies them (coalesced, evict-first loads; four rounds of 256
+//     consecutive rays): BOUNDARY / outside rays go to the trace queue, VALID
+//     rays count into a shared-memory histogram over patches (the atomic's
+//     return value is the ray's rank within its patch) and leave their
+//     patch-local xi, rotation and mirror in shared memory;
+//  B. one warp turns the histogram into offsets (exclusive scan);
+//  C. every VALID ray's tile-local index goes to its sorted slot;
+//  D. the block evaluates the VALID rays in slot order: consecutive lanes
+//     mostly share a patch, so each coefficient load is one or two addresses
+//     for the whole warp instead of one per lane, and no lane idles on an
+//     INVALID or queued ray; the exit ray replaces the record in place;
+//  E. every row of the tile is stored, coalesced: the exit ray of a VALID
+//     ray, zeros otherwise (a placeholder that the queue's tracer overwrites
+//     for a queued ray).
+// Round j of tile b appends to queue segment (4 b + j) % kQSegs: the same
+// segment a 256-ray block of the same rays would use, so the queue's
+// capacity rule (query_segcap) holds.
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 4;
+constexpr int kSortTile = kSortThreads * kSortRounds;
+constexpr int kSortMaxPatches = 1024;
+static_assert(kSortThreads == kQTile, "a sort round must be one queue block");
+
+template <int D, int MODE>
+__global__ void __launch_bounds__(kSortThreads)
+poly_query_sorted_kernel(const __grid_constant__ PolyDev P, RaysInDev in, RaysOutDev out, uint32_t n,
+                         TraceQueue Q)
+{
+    __shared__ uint32_t hist[kSortMaxPatches];
+    __shared__ uint16_t order[kSortTile];
+    __shared__ float4 recA[kSortTile];     // xi, then the exit (x, y, d_x, d_y)
+    __shared__ float4 recB[kSortTile];     // (c, s, m, patch bits), then (d_z, I, -, -)
+    __shared__ uint32_t nvalid;
+    const unsigned full = 0xffffffffu;
+    const int t = threadIdx.x, lane = t & 31;
+    const int NP = P.n_patches;
+    for (int i = t; i < NP; i += kSortThreads) hist[i] = 0;
+    __syncthreads();
+    const uint32_t r0 = blockIdx.x * kSortTile;
+    // A.1: every input of the thread's four rays in flight at once
+    float x[kSortRounds], y[kSortRounds], dx[kSortRounds], dy[kSortRounds], dz[kSortRounds], lam[kSortRounds];
+#pragma unroll
+    for (int j = 0; j < kSortRounds; ++j) {
+        const uint32_t r = r0 + (uint32_t)(j * kSortThreads + t);
+        x[j] = y[j] = dx[j] = dy[j] = dz[j] = lam[j] = 0.0f;
+        if (r < n) {
+            x[j] = ld_stream(in.x + r);
+            y[j] = ld_stream(in.y + r);
+            dx[j] = ld_stream(in.dx + r);
+            dy[j] = ld_stream(in.dy + r);
+            dz[j] = ld_stream(in.dz + r);
+            lam[j] = ld_stream(in.lam + r);
+        }
+    }
+    // A.2: reduce and locate; the record goes to shared memory, the cell's
+    // class word is requested for all four rays before any is used
+    uint32_t cid[kSortRounds], word[kSortRounds], stat[kSortRounds];   // stat: 0 dead, 1 outside, 2 inside
+#pragma unroll
+    for (int j = 0; j < kSortRounds; ++j) {
+        const uint32_t l = (uint32_t)(j * kSortThreads + t);
+        stat[j] = 0;
+        cid[j] = 0;
+        if (r0 + l < n) {
+            float u[4], xi[4], cs, sn, m;
+            uint32_t pid;
+            stat[j] = 1;
+            if (poly_reduce(x[j], y[j], dx[j], dy[j], dz[j], lam[j], u, cs, sn, m) && poly_locate(P, u, cid[j], pid, xi)) {
+                stat[j] = 2;
+                recA[l] = make_float4(xi[0], xi[1], xi[2], xi[3]);
+                recB[l] = make_float4(cs, sn, m, __uint_as_float(pid));
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kSortRounds; ++j) {
+        word[j] = 0;
+        if (stat[j] == 2) {
+            if (MODE == LT_QUERY_TABLE) word[j] = ld_stream(P.cls + (cid[j] >> 4));
+            else word[j] = __ldg(P.patch_ok + __float_as_uint(recB[j * kSortThreads + t].w));
+        }
+    }
+    // A.3: classes, histogram ranks, trace queue
+    uint32_t key[kSortRounds];
+#pragma unroll
+    for (int j = 0; j < kSortRounds; ++j) {
+        const uint32_t l = (uint32_t)(j * kSortThreads + t);
+        const uint32_t r = r0 + l;
+        key[j] = 0xffffffffu;
+        bool tr = stat[j] == 1;
+        const uint32_t tag = r | (stat[j] == 1 ? kOutsideBit : 0u);
+        if (stat[j] == 2) {
+            uint32_t k;
+            if (MODE == LT_QUERY_TABLE) k = (word[j] >> ((cid[j] & 15u) * 2u)) & 3u;
+            else k = word[j] ? (uint32_t)LT_CELL_VALID : (uint32_t)LT_CELL_BOUNDARY;
+            if (k == LT_CELL_VALID) {
+                const uint32_t pid = __float_as_uint(recB[l].w);
+                key[j] = (pid << 16) | atomicAdd(&hist[pid], 1u);
+            } else {
+                tr = k != LT_CELL_INVALID;
+            }
+        }
+        const unsigned mq = __ballot_sync(full, tr);
+        if (mq) {
+            const int leader = __ffs(mq) - 1;
+            uint32_t b = 0;
+            const uint32_t seg = (blockIdx.x * kSortRounds + j) % kQSegs;
+            if (lane == leader) b = atomicAdd(Q.count + seg * kQCountStride, (uint32_t)__popc(mq));
+            b = __shfl_sync(full, b, leader);
+            if (tr) {
+                const uint32_t k = seg * Q.segcap + b + __popc(mq & ((1u << lane) - 1u));
+                Q.x[k] = x[j];
+                Q.y[k] = y[j];
+                Q.dx[k] = dx[j];
+                Q.dy[k] = dy[j];
+                Q.dz[k] = dz[j];
+                Q.lam[k] = lam[j];
+                Q.tag[k] = tag;
+            }
+        }
+    }
+    __syncthreads();
+    if (t < 32) {
+        const int per = (NP + 31) / 32;
+        const int b0 = min(NP, lane * per), b1 = min(NP, b0 + per);
+        uint32_t sum = 0;
+        for (int b = b0; b < b1; ++b) sum += hist[b];
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(full, incl, o);
+            if (lane >= o) incl += v;
+        }
+        uint32_t run = incl - sum;
+        for (int b = b0; b < b1; ++b) {
+            const uint32_t c = hist[b];
+            hist[b] = run;
+            run += c;
+        }
+        if (lane == 31) nvalid = incl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kSortRounds; ++j)
+        if (key[j] != 0xffffffffu) order[hist[key[j] >> 16] + (key[j] & 0xffffu)] = (uint16_t)(j * kSortThreads + t);
+    __syncthreads();
+    const uint32_t nv = nvalid;
+#pragma unroll 1
+    for (uint32_t sl = (uint32_t)t; sl < nv; sl += kSortThreads) {
+        const uint32_t l = order[sl];
+        const float4 a = recA[l], b = recB[l];
+        const float xi[4] = {a.x, a.y, a.z, a.w};
+        float o[6];
+        poly_output<D>(P, __float_as_uint(b.w), xi, b.x, b.y, b.z, o);
+        recA[l] = make_float4(o[0], o[1], o[2], o[3]);
+        recB[l] = make_float4(o[4], o[5], 0.0f, 0.0f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kSortRounds; ++j) {
+        const uint32_t l = (uint32_t)(j * kSortThreads + t);
+        const uint32_t r = r0 + l;
+        if (r >= n) continue;
+        const bool v = key[j] != 0xffffffffu;
+        const float4 a = v ? recA[l] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 b = v ? recB[l] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float o[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+        poly_store(out, r, o, v ? LT_FLAG_VALID : 0u);
+    }
+}
+
+// Small batches: the whole query in one kernel; each block traces its own
+// BOUNDARY and outside rays with survivor compaction (trace_block_states).
+template <int D, int MODE, bool CAUCHY>
+__global__ void __launch_bounds__(kPolyTile)
+poly_query_fused_kernel(const __grid_constant__ MapDev M, const __grid_constant__ PolyDev P, RaysInDev in,
+                        RaysOutDev out, uint32_t n, unsigned long long* work)
+{
+    __shared__ TraceSmem<kPolyTile> S;
+    __shared__ uint32_t tlist[kPolyTile];
+    __shared__ uint32_t tcount;
+    const unsigned full = 0xffffffffu;
+    const int t = threadIdx.x, lane = t & 31;
+    if (t == 0) tcount = 0;
+    __syncthreads();
+    const uint32_t r0 = blockIdx.x * kPolyTile;
+    const uint32_t r = r0 + t;
+    PolyRay c;
+    poly_answer<D, MODE>(P, in, n, r, c);
+    const unsigned mq = __ballot_sync(full, c.tr);
+    if (mq) {
+        const int leader = __ffs(mq) - 1;
+        uint32_t b = 0;
+        if (lane == leader) b = atomicAdd(&tcount, (uint32_t)__popc(mq));
+        b = __shfl_sync(full, b, leader);
+        if (c.tr) tlist[b + __popc(mq & ((1u << lane) - 1u))] = (uint32_t)t | (c.tag & kOutsideBit);
+    }
+    if (r < n && !c.tr) poly_store(out, r, c.o, c.ip ? LT_FLAG_VALID : 0u);
+    __syncthreads();
+    const uint32_t nt = tcount;
+    if (nt == 0) return;
+    RayState st;
+    bool live = false;
+    uint32_t e = 0;
+    S.of[t] = 0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) S.ob[q][t] = 0.0f;
+    if ((uint32_t)t < nt) {
+        e = tlist[t];
+        const uint32_t rr = r0 + (e & ~kOutsideBit);
+        live = trace_init(__ldg(in.x + rr), __ldg(in.y + rr), __ldg(in.dx + rr), __ldg(in.dy + rr),
+                          __ldg(in.dz + rr), __ldg(in.lam + rr), st);
+        if (!live) S.of[t] = (uint8_t)st.flags;
+    }
+    const int nint = trace_block_states<CAUCHY, kPolyTile>(M.L, M.pi, M.pj, live, st, S);
+    __syncthreads();
+    if ((uint32_t)t < nt) {
+        const uint32_t rr = r0 + (e & ~kOutsideBit);
+        const float o[6] = {S.ob[0][t], S.ob[1][t], S.ob[2][t], S.ob[3][t], S.ob[4][t], S.ob[5][t]};
+        poly_store(out, rr, o, S.of[t] | LT_FLAG_TRACED | ((e & kOutsideBit) ? LT_FLAG_OUTSIDE : 0u));
+    }
+    warp_add(work, (unsigned)nint);
+}
+
+// ------------------------------------------------------------------ build kernels
+
+// Box and patch geometry for the build kernels (FP64 where the fit needs it).
+struct PolyBuild {
+    double lo[4], h[4];                  // box corner, patch sides
+    double cheb[kMaxSamplesAxis];        // Chebyshev nodes cos(pi (k + 1/2) / ns)
+    int P[4], ns, M, T;
+    uint32_t pstride[4];
+};
+
+// One thread per (patch, sample): the sample's reduced ray (FP64, rounded
+// once to FP32) traced through the unclipped lens; y = (x', y', d_x', d_y', I).
+template <bool CAUCHY>
+__global__ void __launch_bounds__(256)
+poly_sample_kernel(const __grid_constant__ LensDev Lu, int pi, int pj, const __grid_constant__ PolyBuild B,
+                   float* __restrict__ y, uint8_t* __restrict__ v, uint32_t total)
+{
+    const uint32_t l = blockIdx.x * 256u + threadIdx.x;
+    if (l >= total) return;
+    const uint32_t pid = l / (uint32_t)B.M, s = l % (uint32_t)B.M;
+    double u[4];
+    uint32_t sr = s;
+#pragma unroll
+    for (int k = 3; k >= 0; --k) {
+        const int j = (int)(sr % (uint32_t)B.ns);
+        sr /= (uint32_t)B.ns;
+        const int pk = (int)((pid / B.pstride[k]) % (uint32_t)B.P[k]);
+        u[k] = __dadd_rn(B.lo[k], __dmul_rn(__dadd_rn((double)pk, __dmul_rn(0.5, __dadd_rn(B.cheb[j], 1.0))), B.h[k]));
+    }
+    // uncontracted FP64 (each operation rounded once), then one rounding to FP32
+    const double inv = 1.0 / sqrt(__dadd_rn(__dadd_rn(__dmul_rn(u[1], u[1]), __dmul_rn(u[2], u[2])), 1.0));
+    TraceOut o;
+    int nint;
+    const uint32_t f = trace_ray<CAUCHY>(Lu, pi, pj, (float)u[0], 0.0f, (float)__dmul_rn(u[1], inv),
+                                         (float)__dmul_rn(u[2], inv), (float)inv, (float)(1000.0 / sqrt(u[3])), o,
+                                         nint);
+    y[(size_t)l * 5 + 0] = o.x;
+    y[(size_t)l * 5 + 1] = o.y;
+    y[(size_t)l * 5 + 2] = o.dx;
+    y[(size_t)l * 5 + 3] = o.dy;
+    y[(size_t)l * 5 + 4] = o.I;
+    v[l] = (uint8_t)(f & LT_FLAG_VALID);
+}
+
+// Normal equations of every patch (FP64 reductions over its valid samples):
+// entry e < T(T+1)/2 is G[i][j] = sum a_i a_j (pairs from `ij`), the next 5T
+// are R[i][o] = sum a_i y_o.  Grid (patches, entry blocks).
+__global__ void __launch_bounds__(256)
+poly_normal_kernel(const __grid_constant__ PolyBuild B, const double* __restrict__ A,
+                   const uint16_t* __restrict__ ij, const float* __restrict__ y, const uint8_t* __restrict__ v,
+                   double* __restrict__ G, double* __restrict__ R)
+{
+    const int T = B.T, M = B.M;
+    const int NG = T * (T + 1) / 2;
+    const int e = blockIdx.y * 256 + threadIdx.x;
+    if (e >= NG + 5 * T) return;
+    const uint32_t pid = blockIdx.x;
+    const uint8_t* vp = v + (size_t)pid * M;
+    const float* yp = y + (size_t)pid * M * 5;
+    double acc = 0.0;
+    if (e < NG) {
+        const int i = ij[2 * e], j = ij[2 * e + 1];
+        for (int s = 0; s < M; ++s)
+            if (vp[s]) acc = fma(A[(size_t)s * T + i], A[(size_t)s * T + j], acc);
+        G[(size_t)pid * T * T + (size_t)i * T + j] = acc;
+        G[(size_t)pid * T * T + (size_t)j * T + i] = acc;
+    } else {
+        const int i = (e - NG) / 5, o = (e - NG) % 5;
+        for (int s = 0; s < M; ++s)
+            if (vp[s]) acc = fma(A[(size_t)s * T + i], (double)yp[(size_t)s * 5 + o], acc);
+        R[(size_t)pid * T * 5 + (size_t)i * 5 + o] = acc;
+    }
+}
+
+// One thread per patch: Cholesky factorisation of G (in place, lower
+// triangle) and the two triangular solves for the 5 right-hand sides.  A
+// patch with fewer valid samples than terms, or a pivot below 1e-13 of the
+// largest diagonal entry, gets no fit.
+__global__ void __launch_bounds__(64)
+poly_solve_kernel(const __grid_constant__ PolyBuild B, const uint8_t* __restrict__ v, double* __restrict__ G,
+                  const double* __restrict__ R, double* __restrict__ coef, uint8_t* __restrict__ ok, int npatch)
+{
+    const int pid = blockIdx.x * 64 + threadIdx.x;
+    if (pid >= npatch) return;
+    const int T = B.T, M = B.M;
+    int nv = 0;
+    for (int s = 0; s < M; ++s) nv += v[(size_t)pid * M + s];
+    double* g = G + (size_t)pid * T * T;
+    double* c = coef + (size_t)pid * T * 5;
+    for (int q = 0; q < T * 5; ++q) c[q] = 0.0;
+    ok[pid] = 0;
+    if (nv < T) return;
+    double dmax = 0.0;
+    for (int j = 0; j < T; ++j) dmax = fmax(dmax, g[(size_t)j * T + j]);
+    for (int j = 0; j < T; ++j) {
+        double d = g[(size_t)j * T + j];
+        for (int k = 0; k < j; ++k) d -= g[(size_t)j * T + k] * g[(size_t)j * T + k];
+        if (!(d > 1e-13 * dmax)) return;
+        const double ljj = sqrt(d);
+        g[(size_t)j * T + j] = ljj;
+        for (int i = j + 1; i < T; ++i) {
+            double a = g[(size_t)i * T + j];
+            for (int k = 0; k < j; ++k) a -= g[(size_t)i * T + k] * g[(size_t)j * T + k];
+            g[(size_t)i * T + j] = a / ljj;
+        }
+    }
+    const double* r = R + (size_t)pid * T * 5;
+    for (int o = 0; o < 5; ++o) {
+        // L z = r (z in c), then L^T x = z
+        for (int i = 0; i < T; ++i) {
+            double a = r[(size_t)i * 5 + o];
+            for (int k = 0; k < i; ++k) a -= g[(size_t)i * T + k] * c[(size_t)k * 5 + o];
+            c[(size_t)i * 5 + o] = a / g[(size_t)i * T + i];
+        }
+        for (int i = T - 1; i >= 0; --i) {
+            double a = c[(size_t)i * 5 + o];
+            for (int k = i + 1; k < T; ++k) a -= g[(size_t)k * T + i] * c[(size_t)k * 5 + o];
+            c[(size_t)i * 5 + o] = a / g[(size_t)i * T + i];
+        }
+    }
+    ok[pid] = 1;
+}
+
+// Largest |fit - traced| exit position over the valid samples of fitted
+// patches (FP64; the maximum as ordered bits of a non-negative double), and
+// the FP32 query table packed from the FP64 coefficients.
+__global__ void __launch_bounds__(256)
+poly_sample_residual_kernel(const __grid_constant__ PolyBuild B, const double* __restrict__ A,
+                            const float* __restrict__ y, const uint8_t* __restrict__ v,
+                            const double* __restrict__ coef, const uint8_t* __restrict__ ok,
+                            unsigned long long* resmax, uint32_t total)
+{
+    const uint32_t l = blockIdx.x * 256u + threadIdx.x;
+    double res = 0.0;
+    if (l < total) {
+        const uint32_t pid = l / (uint32_t)B.M, s = l % (uint32_t)B.M;
+        if (v[l] && ok[pid]) {
+            const double* c = coef + (size_t)pid * B.T * 5;
+            double px = 0.0, py = 0.0;
+            for (int k = 0; k < B.T; ++k) {
+                const double a = A[(size_t)s * B.T + k];
+                px = fma(a, c[(size_t)k * 5 + 0], px);
+                py = fma(a, c[(size_t)k * 5 + 1], py);
+            }
+            res = hypot(px - (double)y[(size_t)l * 5 + 0], py - (double)y[(size_t)l * 5 + 1]);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) res = fmax(res, __shfl_xor_sync(0xffffffffu, res, o));
+    if ((threadIdx.x & 31) == 0 && res > 0.0) atomicMax(resmax, (unsigned long long)__double_as_longlong(res));
+}
+
+__global__ void __launch_bounds__(256)
+poly_pack_kernel(const double* __restrict__ coef, float4* __restrict__ c4, float* __restrict__ cI, uint32_t total)
+{
+    const uint32_t l = blockIdx.x * 256u + threadIdx.x;
+    if (l >= total) return;
+    const double* c = coef + (size_t)l * 5;
+    c4[l] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)c[3]);
+    cI[l] = (float)c[4];
+}
+
+// One thread per class-grid node: its FP32 entrance ray (the rule in lt.h)
+// traced through the real lens; the reduced-frame exit (x', y') kept for the
+// corner residuals.
+template <bool CAUCHY>
+__global__ void __launch_bounds__(256)
+poly_node_kernel(const __grid_constant__ LensDev L, int pi, int pj, const __grid_constant__ PolyDev P,
+                 const float4 step, float2* __restrict__ nout, uint8_t* __restrict__ nvalid, uint32_t N)
+{
+    const uint32_t l = blockIdx.x * 256u + threadIdx.x;
+    if (l >= N) return;
+    const float stp[4] = {step.x, step.y, step.z, step.w};
+    float v[4];
+    uint32_t t = l;
+#pragma unroll
+    for (int k = 3; k >= 0; --k) {
+        const uint32_t nk = (uint32_t)P.C[k] + 1u;
+        const uint32_t i = t % nk;
+        t /= nk;
+        v[k] = __fadd_rn(P.lo[k], __fmul_rn((float)i, stp[k]));
+    }
+    const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(v[1], v[1]), __fmul_rn(v[2], v[2])), 1.0f);
+    const float len = __fsqrt_rn(n2);
+    TraceOut o;
+    int nint;
+    const uint32_t f = trace_ray<CAUCHY>(L, pi, pj, v[0], 0.0f, __fdiv_rn(v[1], len), __fdiv_rn(v[2], len),
+                                         __fdiv_rn(1.0f, len), __fdiv_rn(1000.0f, __fsqrt_rn(v[3])), o, nint);
+    nout[l] = make_float2(o.x, o.y);
+    nvalid[l] = (uint8_t)(f & LT_FLAG_VALID);
+}
+
+// One thread per class-grid cell: corner bits for the classification (bit0:
+// all 16 corners valid, the patch fitted and every corner's exit within tol
+// of the FP32 polynomial; bit1: all 16 invalid), the largest corner residual.
+template <int D>
+__global__ void __launch_bounds__(256)
+poly_cell_kernel(const __grid_constant__ PolyDev P, const float2* __restrict__ nout,
+                 const uint8_t* __restrict__ nvalid, float tol, uint8_t* __restrict__ corner_bits,
+                 unsigned int* __restrict__ resmax_all, uint32_t NC)
+{
+    const uint32_t cid = blockIdx.x * 256u + threadIdx.x;
+    float worst = 0.0f;
+    if (cid < NC) {
+        int cell[4];
+        uint32_t t = cid, nstride[4], s = 1;
+#pragma unroll
+        for (int k = 3; k >= 0; --k) {
+            cell[k] = (int)(t % (uint32_t)P.C[k]);
+            t /= (uint32_t)P.C[k];
+            nstride[k] = s;
+            s *= (uint32_t)P.C[k] + 1u;
+        }
+        uint32_t base = 0, pid = 0, pk[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            base += (uint32_t)cell[k] * nstride[k];
+            pk[k] = poly_patch_of(P, k, (uint32_t)cell[k]);
+            pid += pk[k] * P.pstride[k];
+        }
+        int nv = 0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const uint32_t off = base + ((q >> 3) & 1) * nstride[0] + ((q >> 2) & 1) * nstride[1] +
+                                 ((q >> 1) & 1) * nstride[2] + (q & 1) * nstride[3];
+            nv += __ldg(nvalid + off);
+        }
+        uint32_t bits = nv == 0 ? 2u : 0u;
+        if (nv == 16 && __ldg(P.patch_ok + pid)) {
+#pragma unroll 1
+            for (int q = 0; q < 16; ++q) {
+                const int b[4] = {(q >> 3) & 1, (q >> 2) & 1, (q >> 1) & 1, q & 1};
+                float xi[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    xi[k] = fmaf((float)((uint32_t)(cell[k] + b[k]) - pk[k] * (uint32_t)P.m[k]), P.two_over_m[k], -1.0f);
+                const Acc5 a = poly_eval<D>(P.c4 + (size_t)pid * poly_terms(D), P.cI + (size_t)pid * poly_terms(D), xi);
+                const uint32_t off = base + b[0] * nstride[0] + b[1] * nstride[1] + b[2] * nstride[2] + b[3] * nstride[3];
+                const float2 tr = nout[off];
+                worst = fmaxf(worst, hypotf(a.p.x - tr.x, a.p.y - tr.y));
+            }
+            if (!(tol > 0.0f) || worst <= tol) bits |= 1u;
+        }
+        corner_bits[cid] = (uint8_t)bits;
+    }
+    unsigned int wb = __float_as_uint(worst);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wb = max(wb, __shfl_xor_sync(0xffffffffu, wb, o));
+    if ((threadIdx.x & 31) == 0 && wb) atomicMax(resmax_all, wb);
+}
+
+struct PolyFitAccum {
+    unsigned long long inside, valid, n_res;
+    double sumsq;
+    unsigned int max_res_bits;
+};
+
+// One thread per fit ray: traced through the real lens; marks its cell as
+// having seen a valid / invalid ray and, for a valid ray in a cell whose
+// corners qualified, reduces |polynomial - traced| exit position (the
+// polynomial as the query evaluates it).
+template <int D, bool CAUCHY>
+__global__ void __launch_bounds__(256)
+poly_fit_kernel(const __grid_constant__ LensDev L, int pi, int pj, const __grid_constant__ PolyDev P,
+                RaysInDev fit, uint32_t nfit, const uint8_t* __restrict__ corner_bits, uint32_t* __restrict__ seen,
+                uint32_t* __restrict__ resmax, PolyFitAccum* acc)
+{
+    const uint32_t r = blockIdx.x * 256u + threadIdx.x;
+    bool inside = false, valid = false, has_res = false;
+    float res = 0.0f;
+    if (r < nfit) {
+        const float x = __ldg(fit.x + r), y = __ldg(fit.y + r), dx = __ldg(fit.dx + r), dy = __ldg(fit.dy + r),
+                    dz = __ldg(fit.dz + r), lam = __ldg(fit.lam + r);
+        float u[4], xi[4], cs, sn, m;
+        uint32_t cid, pid;
+        inside = poly_reduce(x, y, dx, dy, dz, lam, u, cs, sn, m) && poly_locate(P, u, cid, pid, xi);
+        if (inside) {
+            TraceOut o;
+            int nint;
+            valid = (trace_ray<CAUCHY>(L, pi, pj, x, y, dx, dy, dz, lam, o, nint) & LT_FLAG_VALID) != 0;
+            atomicOr(seen + (cid >> 4), (valid ? 1u : 2u) << ((cid & 15u) * 2u));
+            if (valid && (__ldg(corner_bits + cid) & 1u)) {
+                float q[6];
+                poly_output<D>(P, pid, xi, cs, sn, m, q);
+                res = hypotf(q[0] - o.x, q[1] - o.y);
+                has_res = true;
+                if (resmax) atomicMax(resmax + cid, __float_as_uint(res));
+            }
+        }
+    }
+    const unsigned full = 0xffffffffu;
+    unsigned long long cin = __popc(__ballot_sync(full, inside));
+    unsigned long long cva = __popc(__ballot_sync(full, valid));
+    unsigned long long cre = __popc(__ballot_sync(full, has_res));
+    double sq = has_res ? (double)res * (double)res : 0.0;
+    unsigned int mx = has_res ? __float_as_uint(res) : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sq += __shfl_xor_sync(full, sq, o);
+        mx = max(mx, __shfl_xor_sync(full, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (cin) atomicAdd(&acc->inside, cin);
+        if (cva) atomicAdd(&acc->valid, cva);
+        if (cre) {
+            atomicAdd(&acc->n_res, cre);
+            atomicAdd(&acc->sumsq, sq);
+            atomicMax(&acc->max_res_bits, mx);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ launches
+
+#define LT_POLY_DISPATCH(D, ...)                                                     \
+    switch (D) {                                                                     \
+    case 1: { constexpr int DD = 1; __VA_ARGS__; } break;                            \
+    case 2: { constexpr int DD = 2; __VA_ARGS__; } break;                            \
+    case 3: { constexpr int DD = 3; __VA_ARGS__; } break;                            \
+    case 4: { constexpr int DD = 4; __VA_ARGS__; } break;                            \
+    default: { constexpr int DD = 5; __VA_ARGS__; } break;                           \
+    }
+
+lt_status launch_poly_query(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
+                            int mode, const TraceQueue* Qp, cudaStream_t st)
+{
+    const bool table = mode == LT_QUERY_TABLE;
+    const unsigned blocks = (n + kPolyTile - 1) / kPolyTile;
+    const int D = map->pdev.degree;
+    if (!Qp && n <= kFusedMaxRays) {
+        ProfScope prof("poly_query_fused_kernel", st);
+        unsigned long long* w = prof.work();
+        const bool ca = map->cauchy;
+        LT_POLY_DISPATCH(D, {
+            if (table) {
+                if (ca) poly_query_fused_kernel<DD, LT_QUERY_TABLE, true><<<blocks, kPolyTile, 0, st>>>(map->dev, map->pdev, in, out, n, w);
+                else poly_query_fused_kernel<DD, LT_QUERY_TABLE, false><<<blocks, kPolyTile, 0, st>>>(map->dev, map->pdev, in, out, n, w);
+            } else {
+                if (ca) poly_query_fused_kernel<DD, LT_QUERY_NO_MASK, true><<<blocks, kPolyTile, 0, st>>>(map->dev, map->pdev, in, out, n, w);
+                else poly_query_fused_kernel<DD, LT_QUERY_NO_MASK, false><<<blocks, kPolyTile, 0, st>>>(map->dev, map->pdev, in, out, n, w);
+            }
+        });
+        LT_CUDA_TRY(cudaGetLastError());
+        return LT_OK;
+    }
+    char* buf = nullptr;
+    TraceQueue Q;
+    if (Qp) {
+        Q = *Qp;
+    } else {
+        cudaMemPool_t pool;
+        lt_status s = scratch_pool(&pool);
+        if (s != LT_OK) return s;
+        const size_t bytes = query_scratch_bytes(n);
+        if (cudaMallocFromPoolAsync((void**)&buf, bytes, pool, st) != cudaSuccess)
+            return fail(LT_ENOMEM, "lt_query: trace queue allocation of %zu bytes failed", bytes);
+        Q = trace_queue_at(buf, n);
+    }
+    lt_status s = LT_OK;
+    do {
+        cudaError_t e = cudaMemsetAsync(Q.count, 0, kQHeaderBytes, st);
+        if (e != cudaSuccess) { s = cuda_fail(e, "lt_query: clearing the queue"); break; }
+        if (map->pdev.n_patches <= kSortMaxPatches) {
+            ProfScope prof("poly_query_kernel", st);
+            const unsigned sb = (n + kSortTile - 1) / kSortTile;
+            LT_POLY_DISPATCH(D, {
+                if (table) poly_query_sorted_kernel<DD, LT_QUERY_TABLE><<<sb, kSortThreads, 0, st>>>(map->pdev, in, out, n, Q);
+                else poly_query_sorted_kernel<DD, LT_QUERY_NO_MASK><<<sb, kSortThreads, 0, st>>>(map->pdev, in, out, n, Q);
+            });
+        } else {
+            ProfScope prof("poly_query_kernel", st);
+            LT_POLY_DISPATCH(D, {
+                if (table) poly_query_kernel<DD, LT_QUERY_TABLE><<<blocks, kPolyTile, 0, st>>>(map->pdev, in, out, n, Q);
+                else poly_query_kernel<DD, LT_QUERY_NO_MASK><<<blocks, kPolyTile, 0, st>>>(map->pdev, in, out, n, Q);
+            });
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) { s = cuda_fail(e, "lt_query: launch"); break; }
+        s = launch_queue_trace(map, out, n, Q, st);
+    } while (0);
+    if (buf) cudaFreeAsync(buf, st);
+    return s;
+}
+
+}  // namespace lt
+
+using namespace lt;
+
+namespace {
+
+lt_status poly_check_opts(const lt_lens* lens, const lt_poly_opts* o, int* pi, int* pj)
+{
+    if (!path_ij(lens->S, o->path_id, pi, pj)) return fail(LT_EINVAL, "lt_build_poly_map: bad path id %d", o->path_id);
+    if (o->degree < 1 || o->degree > LT_POLY_MAX_DEGREE)
+        return fail(LT_EINVAL, "lt_build_poly_map: degree %d outside 1..%d", o->degree, LT_POLY_MAX_DEGREE);
+    if (o->samples < o->degree + 1 || o->samples > kMaxSamplesAxis)
+        return fail(LT_EINVAL, "lt_build_poly_map: samples %d outside degree + 1 .. %d", o->samples, kMaxSamplesAxis);
+    if (!(o->rho > 0.0) || !(o->smax > 0.0) || !(o->lam_lo > 0.0) || !(o->lam_hi > o->lam_lo) ||
+        !std::isfinite(o->rho) || !std::isfinite(o->smax) || !std::isfinite(o->lam_hi))
+        return fail(LT_EINVAL, "lt_build_poly_map: empty or non-finite box");
+    uint64_t NC = 1, N = 1, NP = 1;
+    for (int k = 0; k < 4; ++k) {
+        if (o->patches[k] < 1 || o->cells[k] < 1)
+            return fail(LT_EINVAL, "lt_build_poly_map: patches and cells must be >= 1");
+        const uint64_t C = (uint64_t)o->patches[k] * (uint64_t)o->cells[k];
+        if (C > 4096) return fail(LT_EINVAL, "lt_build_poly_map: %llu cells on axis %d (at most 4096)",
+                                  (unsigned long long)C, k);
+        NC *= C;
+        N *= C + 1;
+        NP *= (uint64_t)o->patches[k];
+    }
+    if (N >= (1ull << 31) || NC >= (1ull << 31))
+        return fail(LT_EINVAL, "lt_build_poly_map: %llu class-grid nodes is too many", (unsigned long long)N);
+    uint64_t M = 1;
+    for (int k = 0; k < 4; ++k) M *= (uint64_t)o->samples;
+    if (NP * M >= (1ull << 31)) return fail(LT_EINVAL, "lt_build_poly_map: too many samples");
+    if (o->n_fit > 0) {
+        const void* ps[] = {o->fit_x, o->fit_y, o->fit_dx, o->fit_dy, o->fit_dz, o->fit_lambda};
+        for (const void* p : ps)
+            if (!p || !aligned16(p)) return fail(LT_EINVAL, "lt_build_poly_map: fit arrays must be non-NULL and 16-byte aligned");
+        if (o->n_fit >= (1ull << 31)) return fail(LT_EINVAL, "lt_build_poly_map: too many fit rays");
+    }
+    return LT_OK;
+}
+
+// RAII for the build's temporaries
+struct DevBufs {
+    std::vector<void*> p;
+    ~DevBufs() { for (void* q : p) cudaFree(q); }
+    template <class T>
+    bool get(T** out, size_t bytes)
+    {
+        void* q = nullptr;
+        if (cudaMalloc(&q, bytes ? bytes : 1) != cudaSuccess) return false;
+        p.push_back(q);
+        *out = static_cast<T*>(q);
+        return true;
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+lt_status lt_build_poly_map(const lt_lens* lens, const lt_poly_opts* o, lt_map** out, lt_stream stream)
+{
+    clear_error();
+    auto t0 = std::chrono::steady_clock::now();
+    if (!lens || !o || !out) return fail(LT_EINVAL, "lt_build_poly_map: NULL argument");
+    *out = nullptr;
+    int pi, pj;
+    lt_status s = poly_check_opts(lens, o, &pi, &pj);
+    if (s != LT_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int D = o->degree, T = poly_terms(D), ns = o->samples;
+    const int M = ns * ns * ns * ns;
+
+    lt_map* m = new (std::nothrow) lt_map();
+    if (!m) return fail(LT_ENOMEM, "lt_build_poly_map: host allocation");
+    auto bail = [&](lt_status e) { delete m; return e; };
+    m->kind = LT_MAP_KIND_POLY;
+    m->lens = *lens;
+    m->lens.presc.surfaces = m->lens.surf;
+    m->lens.presc.glasses = m->lens.glass;
+    m->path_id = o->path_id;
+    m->tol = o->max_residual_mm;
+    m->popts = *o;
+    m->popts.fit_x = m->popts.fit_y = m->popts.fit_dx = m->popts.fit_dy = m->popts.fit_dz = m->popts.fit_lambda = nullptr;
+    m->popts.n_fit = 0;
+    std::memset(&m->dev, 0, sizeof m->dev);
+    m->dev.L = lens->dev;
+    m->dev.pi = pi;
+    m->dev.pj = pj;
+    m->cauchy = lens_all_cauchy(lens->dev);
+
+    // box and grids
+    const double lo[4] = {0.0, -o->smax, 0.0, (1000.0 / o->lam_hi) * (1000.0 / o->lam_hi)};
+    const double hi[4] = {o->rho, o->smax, o->smax, (1000.0 / o->lam_lo) * (1000.0 / o->lam_lo)};
+    PolyDev& P = m->pdev;
+    PolyBuild B;
+    std::memset(&B, 0, sizeof B);
+    float step[4];
+    uint64_t NC = 1, N = 1, NP = 1;
+    uint32_t cs = 1, ps = 1;
+    for (int k = 3; k >= 0; --k) {
+        const int C = o->patches[k] * o->cells[k];
+        P.lo[k] = (float)lo[k];
+        P.inv[k] = (float)((double)C / (hi[k] - lo[k]));
+        P.cmax[k] = (float)C;
+        P.two_over_m[k] = (float)(2.0 / (double)o->cells[k]);
+        P.C[k] = C;
+        P.m[k] = o->cells[k];
+        P.P[k] = o->patches[k];
+        P.mdiv[k] = o->cells[k] == 1 ? 0u : (uint32_t)(((1ull << 32) + (uint64_t)o->cells[k] - 1) / (uint64_t)o->cells[k]);
+        P.cstride[k] = cs;
+        P.pstride[k] = ps;
+        cs *= (uint32_t)C;
+        ps *= (uint32_t)o->patches[k];
+        step[k] = (float)((hi[k] - lo[k]) / (double)C);
+        B.lo[k] = lo[k];
+        B.h[k] = (hi[k] - lo[k]) / (double)o->patches[k];
+        B.P[k] = o->patches[k];
+        B.pstride[k] = P.pstride[k];
+        NC *= (uint64_t)C;
+        N *= (uint64_t)C + 1;
+        NP *= (uint64_t)o->patches[k];
+    }
+    P.T = T;
+    P.degree = D;
+    P.n_patches = (int)NP;
+    B.ns = ns;
+    B.M = M;
+    B.T = T;
+    for (int j = 0; j < ns; ++j) B.cheb[j] = std::cos(M_PI * (j + 0.5) / ns);
+    m->n_nodes = N;
+    m->n_cells = NC;
+
+    // design matrix (FP64, horner_exponents order) and the normal-equation pairs
+    std::vector<int32_t> ex;
+    horner_exponents(D, ex);
+    std::vector<double> A((size_t)M * T);
+    for (int sidx = 0; sidx < M; ++sidx) {
+        double xi[4];
+        int r = sidx;
+        for (int k = 3; k >= 0; --k) { xi[k] = B.cheb[r % ns]; r /= ns; }
+        for (int t = 0; t < T; ++t) {
+            double v = 1.0;
+            for (int k = 0; k < 4; ++k)
+                for (int q = 0; q < ex[4 * t + k]; ++q) v *= xi[k];
+            A[(size_t)sidx * T + t] = v;
+        }
+    }
+    std::vector<uint16_t> pairs;
+    for (int i = 0; i < T; ++i)
+        for (int j = i; j < T; ++j) { pairs.push_back((uint16_t)i); pairs.push_back((uint16_t)j); }
+
+    const uint32_t NW = (uint32_t)((NC + 15) / 16);
+    const size_t nsamp = (size_t)NP * M;
+    if (cudaMalloc(&m->coef4, (size_t)NP * T * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc(&m->coefI, (size_t)NP * T * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&m->coef64, (size_t)NP * T * 5 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&m->patch_ok, NP) != cudaSuccess || cudaMalloc(&m->node_valid, N) != cudaSuccess ||
+        cudaMalloc(&m->cls, (size_t)NW * 4) != cudaSuccess)
+        return bail(fail(LT_ENOMEM, "lt_build_poly_map: device allocation of the tables failed"));
+    P.c4 = m->coef4;
+    P.cI = m->coefI;
+    P.patch_ok = m->patch_ok;
+    P.cls = m->cls;
+
+    // the unclipped lens: no clear apertures, no stop
+    LensDev Lu = lens->dev;
+    for (int k = 1; k <= Lu.S; ++k) {
+        Lu.s[k].ap2 = INFINITY;
+        Lu.s[k].eps2a = 0.0f;
+    }
+    Lu.stop_gap = -1;
+
+    DevBufs tmp;
+    double* dA = nullptr;
+    uint16_t* dpairs = nullptr;
+    float* ys = nullptr;
+    uint8_t* vs = nullptr;
+    double* G = nullptr;
+    double* R = nullptr;
+    float2* nout = nullptr;
+    uint8_t* corner_bits = nullptr;
+    uint32_t* seen = nullptr;
+    uint32_t* resmax = nullptr;
+    unsigned long long* sres = nullptr;
+    unsigned int* cres = nullptr;
+    PolyFitAccum* acc = nullptr;
+    unsigned long long* counts = nullptr;
+    const bool use_tol = o->max_residual_mm > 0.0;
+    if (!tmp.get(&dA, A.size() * 8) || !tmp.get(&dpairs, pairs.size() * 2) || !tmp.get(&ys, nsamp * 5 * 4) ||
+        !tmp.get(&vs, nsamp) || !tmp.get(&G, (size_t)NP * T * T * 8) || !tmp.get(&R, (size_t)NP * T * 5 * 8) ||
+        !tmp.get(&nout, (size_t)N * sizeof(float2)) || !tmp.get(&corner_bits, NC) || !tmp.get(&seen, (size_t)NW * 4) ||
+        (o->n_fit > 0 && use_tol && !tmp.get(&resmax, NC * 4)) || !tmp.get(&sres, 8) || !tmp.get(&cres, 4) ||
+        !tmp.get(&acc, sizeof(PolyFitAccum)) || !tmp.get(&counts, 24))
+        return bail(fail(LT_ENOMEM, "lt_build_poly_map: device allocation of temporaries failed"));
+
+#define POLY_TRY(expr)                                               \
+    do {                                                             \
+        cudaError_t _e = (expr);                                     \
+        if (_e != cudaSuccess) return bail(cuda_fail(_e, #expr));    \
+    } while (0)
+    POLY_TRY(cudaMemcpyAsync(dA, A.data(), A.size() * 8, cudaMemcpyHostToDevice, st));
+    POLY_TRY(cudaMemcpyAsync(dpairs, pairs.data(), pairs.size() * 2, cudaMemcpyHostToDevice, st));
+    POLY_TRY(cudaMemsetAsync(seen, 0, (size_t)NW * 4, st));
+    if (resmax) POLY_TRY(cudaMemsetAsync(resmax, 0, NC * 4, st));
+    POLY_TRY(cudaMemsetAsync(sres, 0, 8, st));
+    POLY_TRY(cudaMemsetAsync(cres, 0, 4, st));
+    POLY_TRY(cudaMemsetAsync(acc, 0, sizeof(PolyFitAccum), st));
+    POLY_TRY(cudaMemsetAsync(counts, 0, 24, st));
+
+    // 1. regressor: samples through the unclipped lens, FP64 normal equations, solve, pack
+    const unsigned sb = (unsigned)((nsamp + 255) / 256);
+    if (m->cauchy) poly_sample_kernel<true><<<sb, 256, 0, st>>>(Lu, pi, pj, B, ys, vs, (uint32_t)nsamp);
+    else poly_sample_kernel<false><<<sb, 256, 0, st>>>(Lu, pi, pj, B, ys, vs, (uint32_t)nsamp);
+    const int NE = T * (T + 1) / 2 + 5 * T;
+    poly_normal_kernel<<<dim3((unsigned)NP, (unsigned)((NE + 255) / 256)), 256, 0, st>>>(B, dA, dpairs, ys, vs, G, R);
+    poly_solve_kernel<<<(unsigned)((NP + 63) / 64), 64, 0, st>>>(B, vs, G, R, m->coef64, m->patch_ok, (int)NP);
+    poly_sample_residual_kernel<<<sb, 256, 0, st>>>(B, dA, ys, vs, m->coef64, m->patch_ok, sres, (uint32_t)nsamp);
+    const uint32_t nc = (uint32_t)(NP * T);
+    poly_pack_kernel<<<(nc + 255) / 256, 256, 0, st>>>(m->coef64, m->coef4, m->coefI, nc);
+    POLY_TRY(cudaGetLastError());
+
+    // 2. mask: class-grid nodes through the real lens, corner classes
+    const float4 stp = make_float4(step[0], step[1], step[2], step[3]);
+    const unsigned nb = (unsigned)((N + 255) / 256);
+    if (m->cauchy) poly_node_kernel<true><<<nb, 256, 0, st>>>(lens->dev, pi, pj, P, stp, nout, m->node_valid, (uint32_t)N);
+    else poly_node_kernel<false><<<nb, 256, 0, st>>>(lens->dev, pi, pj, P, stp, nout, m->node_valid, (uint32_t)N);
+    const float tol = use_tol ? (float)o->max_residual_mm : 0.0f;
+    const unsigned cb = (unsigned)((NC + 255) / 256);
+    LT_POLY_DISPATCH(D, { poly_cell_kernel<DD><<<cb, 256, 0, st>>>(P, nout, m->node_valid, tol, corner_bits, cres, (uint32_t)NC); });
+    if (o->n_fit > 0) {
+        RaysInDev fit{o->fit_x, o->fit_y, o->fit_dx, o->fit_dy, o->fit_dz, o->fit_lambda};
+        const unsigned fb = (unsigned)((o->n_fit + 255) / 256);
+        const bool ca = m->cauchy;
+        LT_POLY_DISPATCH(D, {
+            if (ca) poly_fit_kernel<DD, true><<<fb, 256, 0, st>>>(lens->dev, pi, pj, P, fit, (uint32_t)o->n_fit, corner_bits, seen, resmax, acc);
+            else poly_fit_kernel<DD, false><<<fb, 256, 0, st>>>(lens->dev, pi, pj, P, fit, (uint32_t)o->n_fit, corner_bits, seen, resmax, acc);
+        });
+    }
+    POLY_TRY(cudaGetLastError());
+    s = launch_map_classify(corner_bits, seen, resmax, tol, m->cls, (uint32_t)NC, counts, st);
+    if (s != LT_OK) return bail(s);
+
+    // statistics
+    PolyFitAccum ha;
+    unsigned long long hc[3], hs;
+    unsigned int hcr;
+    std::vector<uint8_t> okh(NP), vh(nsamp);
+    POLY_TRY(cudaMemcpyAsync(&ha, acc, sizeof ha, cudaMemcpyDeviceToHost, st));
+    POLY_TRY(cudaMemcpyAsync(hc, counts, sizeof hc, cudaMemcpyDeviceToHost, st));
+    POLY_TRY(cudaMemcpyAsync(&hs, sres, 8, cudaMemcpyDeviceToHost, st));
+    POLY_TRY(cudaMemcpyAsync(&hcr, cres, 4, cudaMemcpyDeviceToHost, st));
+    POLY_TRY(cudaMemcpyAsync(okh.data(), m->patch_ok, NP, cudaMemcpyDeviceToHost, st));
+    POLY_TRY(cudaMemcpyAsync(vh.data(), vs, nsamp, cudaMemcpyDeviceToHost, st));
+    POLY_TRY(cudaStreamSynchronize(st));
+#undef POLY_TRY
+    m->stats.n_nodes = N;
+    m->stats.n_cells = NC;
+    m->stats.cells_invalid = hc[0];
+    m->stats.cells_valid = hc[1];
+    m->stats.cells_boundary = hc[2];
+    m->stats.fit_inside = ha.inside;
+    m->stats.fit_valid = ha.valid;
+    m->stats.fit_residual_rms_mm = ha.n_res ? std::sqrt(ha.sumsq / (double)ha.n_res) : 0.0;
+    float fmx;
+    std::memcpy(&fmx, &ha.max_res_bits, 4);
+    m->stats.fit_residual_max_mm = fmx;
+    m->stats.table_bytes = (uint64_t)NP * T * 20 + NP + N + (uint64_t)NW * 4;
+    lt_poly_stats& ps_ = m->pstats;
+    ps_.patches = (uint32_t)NP;
+    ps_.terms = (uint32_t)T;
+    ps_.patches_fit = 0;
+    for (uint8_t b : okh) ps_.patches_fit += b;
+    ps_.samples_traced = nsamp;
+    ps_.samples_valid = 0;
+    for (uint8_t b : vh) ps_.samples_valid += b;
+    double sr;
+    std::memcpy(&sr, &hs, 8);
+    ps_.sample_residual_max_mm = sr;
+    float crf;
+    std::memcpy(&crf, &hcr, 4);
+    ps_.corner_residual_max_mm = crf;
+    cudaGetDevice(&m->device);
+    m->stats.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = m;
+    return LT_OK;
+}
+
+lt_status lt_poly_stats_get(const lt_map* m, lt_poly_stats* out)
+{
+    clear_error();
+    if (!m || !out) return fail(LT_EINVAL, "lt_poly_stats_get: NULL argument");
+    if (m->kind != LT_MAP_KIND_POLY) return fail(LT_EINVAL, "lt_poly_stats_get: not a polynomial-patch map");
+    *out = m->pstats;
+    return LT_OK;
+}
+
+lt_status lt_poly_export(const lt_map* m, double* coef, int32_t* exps, uint8_t* patch_ok)
+{
+    clear_error();
+    if (!m) return fail(LT_EINVAL, "lt_poly_export: NULL map");
+    if (m->kind != LT_MAP_KIND_POLY) return fail(LT_EINVAL, "lt_poly_export: not a polynomial-patch map");
+    const size_t NP = m->pstats.patches, T = m->pstats.terms;
+    if (coef) LT_CUDA_TRY(cudaMemcpy(coef, m->coef64, NP * T * 5 * sizeof(double), cudaMemcpyDeviceToHost));
+    if (patch_ok) LT_CUDA_TRY(cudaMemcpy(patch_ok, m->patch_ok, NP, cudaMemcpyDeviceToHost));
+    if (exps) {
+        std::vector<int32_t> ex;
+        horner_exponents(m->pdev.degree, ex);
+        std::memcpy(exps, ex.data(), ex.size() * sizeof(int32_t));
+    }
+    return LT_OK;
+}
+
+}  // extern "C"

@@ -364,9 +364,34 @@ class c_map_stats(ctypes.Structure):
                 ("table_bytes", ctypes.c_uint64), ("build_ms", ctypes.c_double)]
 
 
+class c_poly_opts(ctypes.Structure):
+    _fields_ = [("path_id", ctypes.c_int32), ("rho", ctypes.c_double), ("smax", ctypes.c_double),
+                ("lam_lo", ctypes.c_double), ("lam_hi", ctypes.c_double), ("degree", ctypes.c_int32),
+                ("patches", ctypes.c_int32 * 4), ("cells", ctypes.c_int32 * 4),
+                ("samples", ctypes.c_int32), ("max_residual_mm", ctypes.c_double),
+                ("fit_x", _fptr), ("fit_y", _fptr), ("fit_dx", _fptr), ("fit_dy", _fptr),
+                ("fit_dz", _fptr), ("fit_lambda", _fptr), ("n_fit", ctypes.c_size_t)]
+
+
+class c_poly_stats(ctypes.Structure):
+    _fields_ = [("patches", ctypes.c_uint32), ("patches_fit", ctypes.c_uint32),
+                ("terms", ctypes.c_uint32), ("samples_traced", ctypes.c_uint64),
+                ("samples_valid", ctypes.c_uint64), ("sample_residual_max_mm", ctypes.c_double),
+                ("corner_residual_max_mm", ctypes.c_double)]
+
+
+POLY_MAX_DEGREE = 5
+
+
 def _declare_maps(L: ctypes.CDLL) -> None:
     vp = ctypes.c_void_p
     st = ctypes.c_int
+    L.lt_build_poly_map.restype = st
+    L.lt_build_poly_map.argtypes = [vp, ctypes.POINTER(c_poly_opts), ctypes.POINTER(vp), vp]
+    L.lt_poly_stats_get.restype = st
+    L.lt_poly_stats_get.argtypes = [vp, ctypes.POINTER(c_poly_stats)]
+    L.lt_poly_export.restype = st
+    L.lt_poly_export.argtypes = [vp, vp, vp, vp]
     L.lt_build_map.restype = st
     L.lt_build_map.argtypes = [vp, ctypes.POINTER(c_map_opts), ctypes.POINTER(vp), vp]
     L.lt_destroy_map.restype = None
@@ -420,6 +445,53 @@ class Map:
         check(lib().lt_build_map(lens.handle, ctypes.byref(o), ctypes.byref(h),
                                  _stream_handle(stream)))
         return cls(h)
+
+    @classmethod
+    def build_poly(cls, lens: Lens, path_id: int, rho: float, smax: float, degree: int, patches,
+                   cells, samples: int, lam_lo: float = 380.0, lam_hi: float = 780.0, fit=None,
+                   max_residual_mm: float = 0.0, stream=None) -> "Map":
+        """lt_build_poly_map; fit: a batch.DeviceRays (or None)."""
+        o = c_poly_opts()
+        o.path_id = path_id
+        o.rho, o.smax, o.lam_lo, o.lam_hi = float(rho), float(smax), float(lam_lo), float(lam_hi)
+        o.degree = int(degree)
+        for k in range(4):
+            o.patches[k] = int(patches[k])
+            o.cells[k] = int(cells[k])
+        o.samples = int(samples)
+        o.max_residual_mm = float(max_residual_mm)
+        if fit is not None:
+            o.fit_x, o.fit_y, o.fit_dx, o.fit_dy, o.fit_dz = [_ptr(t) for t in fit.inp]
+            o.fit_lambda = _ptr(fit.lam)
+            o.n_fit = fit.n
+        h = ctypes.c_void_p()
+        check(lib().lt_build_poly_map(lens.handle, ctypes.byref(o), ctypes.byref(h),
+                                      _stream_handle(stream)))
+        return cls(h)
+
+    def poly_stats(self) -> dict:
+        s = c_poly_stats()
+        check(lib().lt_poly_stats_get(self.handle, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in c_poly_stats._fields_}
+
+    def poly_export(self):
+        """(coef [patches, terms, 5] FP64, exps [terms, 4], patch_ok [patches])."""
+        import numpy as np
+        ps = self.poly_stats()
+        P, T = ps["patches"], ps["terms"]
+        coef = np.empty((P, T, 5), np.float64)
+        exps = np.empty((T, 4), np.int32)
+        ok = np.empty(P, np.uint8)
+        check(lib().lt_poly_export(self.handle, coef.ctypes.data, exps.ctypes.data, ok.ctypes.data))
+        return coef, exps, ok
+
+    def export_mask(self, n_nodes: int, n_cells: int):
+        """(node_valid [n_nodes], cell_class [n_cells]) of either kind of map."""
+        import numpy as np
+        nv = np.empty(n_nodes, np.uint8)
+        cc = np.empty(n_cells, np.uint8)
+        check(lib().lt_map_export(self.handle, None, nv.ctypes.data, cc.ctypes.data))
+        return nv, cc
 
     @classmethod
     def load(cls, path: str) -> "Map":
@@ -503,7 +575,7 @@ NOALLOC_MAX_RAYS = 1 << 19
 def query_noalloc(gmap: "Map", inp: Sequence, lam, out: Sequence, n: int,
                   mode: int = QUERY_TABLE, stream=None) -> None:
     """lt_query_noalloc: the map query under an allocation-free contract
-    (n <= 2^20)."""
+    (n <= NOALLOC_MAX_RAYS = 2^19)."""
     L = lib()
     L.lt_query_noalloc.restype = ctypes.c_int
     L.lt_query_noalloc.argtypes = [ctypes.c_void_p, ctypes.POINTER(c_rays_in), ctypes.c_void_p,

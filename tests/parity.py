@@ -4,10 +4,17 @@ Tolerances (fixed by the target, not tuned): exit position 1e-4 mm, each
 direction component 1e-6, throughput 1e-6 absolute; the validity mask is
 bit-exact except for rays within 1e-6 mm of an aperture/stop edge (flagged
 by either side) and -- the same rule for the other ill-conditioned test --
-rays within 1e-6 of total internal reflection.  Rays that refract with
-k = 1 - eta^2 sin^2 i below 1e-2 (leaving within ~6 deg of grazing) carry an
-FP32 error amplified by ~1/(2 sqrt k); their values are reported separately
-("ill_cond_*"), not held to the absolute tolerances.
+rays within 1e-6 of total internal reflection.
+
+Every ray valid on both sides is held to a bound: the tolerances, or, where
+the FP32 error exceeds them, the oracle's own sensitivity -- tol + 2 K S,
+S the FP64 output spread under 1-ulp FP32 perturbations of each input (an
+FP32 trace perturbs its state by about an ulp at each of its K
+interactions).  Rays that refract within a few degrees of grazing (k = 1 -
+eta^2 sin^2 i small) are held to the same rule: their error is large only
+because S is.  The one exemption is a ray whose validity itself flips under
+a 1-ulp input change (S infinite): such rays are counted ("exempt") and
+their share of the valid rays is capped per call.
 """
 from __future__ import annotations
 
@@ -25,37 +32,41 @@ F_VALID, F_EDGE, F_TIR, F_BAD, F_GRAZING = 1, 2, 4, 8, 0x40
 
 def ulp_sensitivity(ol, rays, path, idx):
     """FP64 output spread of the oracle under 1-ulp FP32 perturbations of each
-    entrance component (x, y, dx, dy, dz, both signs): (S_pos, S_dir, K) per
-    ray in idx, K the interactions of the path.  An FP32 evaluation perturbs
-    the state by about an ulp at every interaction, so its error is bounded by
-    about 2 K S; rays whose error fits that bound are ill-conditioned, not wrong."""
+    entrance component (x, y, dx, dy, dz, lambda; both signs): (S_pos, S_dir,
+    S_I, K) per ray in idx, K the interactions of the path; S = inf where a
+    perturbation changes the ray's validity."""
     import oracle as _oracle
     S = ol.S
     K = len(_oracle.path_sequence(S, *path)[0]) + 1
     sp = np.zeros(len(idx))
     sd = np.zeros(len(idx))
+    si = np.zeros(len(idx))
     for m, r in enumerate(idx):
         base = [np.float32(a[r]) for a in rays.arrays()]
         v0, o0, _, _ = ol.trace_one(*base, path=path)
-        for comp in range(5):
+        for comp in range(6):
             for sgn in (np.inf, -np.inf):
                 pert = list(base)
                 pert[comp] = np.nextafter(base[comp], np.float32(sgn))
                 v1, o1, _, _ = ol.trace_one(*pert, path=path)
                 if v1 != v0:
-                    sp[m] = sd[m] = np.inf
+                    sp[m] = sd[m] = si[m] = np.inf
                     continue
                 sp[m] = max(sp[m], float(np.abs(o1[:2] - o0[:2]).max()))
                 sd[m] = max(sd[m], float(np.abs(o1[2:5] - o0[2:5]).max()))
-    return sp, sd, K
+                si[m] = max(si[m], float(abs(o1[5] - o0[5])))
+    return sp, sd, si, K
 
 
-def compare_trace(out, flags, ex, ev, edge=None, kmin=None, label="", cond=None):
+def compare_trace(out, flags, ex, ev, edge=None, kmin=None, label="", cond=None,
+                  max_exempt_frac=0.01):
     """out: [n,6] GPU outputs, flags: [n] GPU flags; ex: [n,6] oracle FP64,
     ev: [n] oracle valid byte (1 valid, 8 bad input).  cond = (oracle lens,
-    rays, path) lets rays outside the tolerances be explained by the oracle's
-    own 1-ulp sensitivity (see ulp_sensitivity).  Returns a stats dict;
-    raises AssertionError on any violation."""
+    rays, path) lets rays outside the tolerances be held to the oracle's own
+    1-ulp sensitivity bound instead (see ulp_sensitivity); without it every
+    valid ray is held to the tolerances.  At most max_exempt_frac of the
+    valid rays may be exempt (validity unstable within 1 ulp).  Returns a
+    stats dict; raises AssertionError on any violation."""
     n = len(flags)
     gv = (flags & F_VALID) != 0
     ov = ev == 1
@@ -64,58 +75,58 @@ def compare_trace(out, flags, ex, ev, edge=None, kmin=None, label="", cond=None)
         explained |= edge < EDGE_EPS
     if kmin is not None:
         explained |= kmin < TIR_EPS
-    # ill-conditioned refraction (output error amplified ~1/(2 sqrt k)): values
-    # are reported separately, the mask rule still applies
-    illcond = explained | ((flags & F_GRAZING) != 0)
+    grazing = (flags & F_GRAZING) != 0
     if kmin is not None:
-        illcond |= kmin < GRAZING_K
+        grazing |= kmin < GRAZING_K
     bad_gpu = (flags & F_BAD) != 0
     bad_or = ev == 8
     mism = gv != ov
     unexplained = mism & ~explained
-    both = gv & ov & ~illcond
+    both = gv & ov
     st = {"label": label, "n": n, "valid_gpu": int(gv.sum()), "valid_oracle": int(ov.sum()),
           "mask_mismatch": int(mism.sum()), "mask_mismatch_unflagged": int(unexplained.sum()),
-          "flagged": int(explained.sum()), "ill_conditioned": int((illcond & gv & ov).sum())}
-    if cond is not None:
-        # rays over the tolerances that the oracle itself shows to be that sensitive
-        cand = np.nonzero(gv & ov & ~illcond)[0]
-        if cand.size:
-            ep = np.abs(out[cand, 0:2].astype(np.float64) - ex[cand, 0:2]).max(axis=1)
-            ed = np.abs(out[cand, 2:5].astype(np.float64) - ex[cand, 2:5]).max(axis=1)
-            over = cand[(ep > POS_TOL) | (ed > DIR_TOL)]
-            if over.size:
-                ol, rays, path = cond
-                sp, sd, K = ulp_sensitivity(ol, rays, path, over)
-                ep = np.abs(out[over, 0:2].astype(np.float64) - ex[over, 0:2]).max(axis=1)
-                ed = np.abs(out[over, 2:5].astype(np.float64) - ex[over, 2:5]).max(axis=1)
-                ok = (ep <= POS_TOL + 2 * K * sp) & (ed <= DIR_TOL + 2 * K * sd)
-                illcond[over[ok]] = True
-                both = gv & ov & ~illcond
-                st["sensitive_explained"] = int(ok.sum())
-                st["sensitive_unexplained"] = int((~ok).sum())
-    st["ill_conditioned"] = int((illcond & gv & ov).sum())
-    ic = gv & ov & illcond
-    if ic.any():
-        st["ill_cond_pos_max"] = float(np.abs(out[ic, 0:2] - ex[ic, 0:2]).max())
-        st["ill_cond_dir_max"] = float(np.abs(out[ic, 2:5] - ex[ic, 2:5]).max())
-    if both.any():
-        dp = np.abs(out[both, 0:2].astype(np.float64) - ex[both, 0:2]).max(axis=1)
-        dd = np.abs(out[both, 2:5].astype(np.float64) - ex[both, 2:5]).max(axis=1)
-        di = np.abs(out[both, 5].astype(np.float64) - ex[both, 5])
-        st.update(pos_max=float(dp.max()), pos_p99=float(np.percentile(dp, 99)),
-                  dir_max=float(dd.max()), dir_p99=float(np.percentile(dd, 99)),
-                  I_max=float(di.max()))
+          "flagged": int(explained.sum()), "grazing": int((grazing & both).sum())}
+    ep = np.abs(out[:, 0:2].astype(np.float64) - ex[:, 0:2]).max(axis=1)
+    ed = np.abs(out[:, 2:5].astype(np.float64) - ex[:, 2:5]).max(axis=1)
+    ei = np.abs(out[:, 5].astype(np.float64) - ex[:, 5])
+    within = both & (ep <= POS_TOL) & (ed <= DIR_TOL) & (ei <= I_TOL)
+    over = np.nonzero(both & ~within)[0]
+    sens_ok = np.zeros(n, bool)
+    exempt = np.zeros(n, bool)
+    if over.size and cond is not None:
+        ol, rays, path = cond
+        sp, sd, si, K = ulp_sensitivity(ol, rays, path, over)
+        inf = np.isinf(sp)
+        exempt[over[inf]] = True
+        ok = ~inf & (ep[over] <= POS_TOL + 2 * K * sp) & (ed[over] <= DIR_TOL + 2 * K * sd) & \
+            (ei[over] <= I_TOL + 2 * K * si)
+        sens_ok[over[ok]] = True
+    held = both & ~exempt
+    bad_value = held & ~within & ~sens_ok
+    st.update(within_tol=int(within.sum()), sensitive_explained=int(sens_ok.sum()),
+              exempt=int(exempt.sum()), exempt_frac=float(exempt.sum()) / max(1, int(both.sum())),
+              value_violations=int(bad_value.sum()))
+    if within.any():
+        st.update(pos_max=float(ep[within].max()), pos_p99=float(np.percentile(ep[within], 99)),
+                  dir_max=float(ed[within].max()), dir_p99=float(np.percentile(ed[within], 99)),
+                  I_max=float(ei[within].max()))
     else:
         st.update(pos_max=0.0, pos_p99=0.0, dir_max=0.0, dir_p99=0.0, I_max=0.0)
+    if sens_ok.any():
+        st.update(sensitive_pos_max=float(ep[sens_ok].max()), sensitive_dir_max=float(ed[sens_ok].max()),
+                  sensitive_I_max=float(ei[sens_ok].max()))
+    if exempt.any():
+        st.update(exempt_pos_max=float(ep[exempt].max()), exempt_dir_max=float(ed[exempt].max()))
     if unexplained.any() and edge is not None:
         st["unflagged_edge_dist"] = sorted(float(e) for e in edge[unexplained])[:20]
+    if bad_value.any():
+        st["worst_violations"] = [(int(r), float(ep[r]), float(ed[r]), float(ei[r]))
+                                  for r in np.nonzero(bad_value)[0][:10]]
     print("parity", st)
     assert np.array_equal(bad_gpu, bad_or), f"{label}: bad-input flags differ"
     zero = ~gv
     assert np.all(out[zero] == 0.0), f"{label}: invalid rays must have zero outputs"
     assert st["mask_mismatch_unflagged"] == 0, f"{label}: validity mask differs on unflagged rays"
-    assert st["pos_max"] <= POS_TOL, f"{label}: position error {st['pos_max']}"
-    assert st["dir_max"] <= DIR_TOL, f"{label}: direction error {st['dir_max']}"
-    assert st["I_max"] <= I_TOL, f"{label}: throughput error {st['I_max']}"
+    assert st["value_violations"] == 0, f"{label}: outputs outside every bound: {st.get('worst_violations')}"
+    assert st["exempt_frac"] <= max_exempt_frac, f"{label}: {st['exempt']} rays exempt ({st['exempt_frac']:.4f})"
     return st

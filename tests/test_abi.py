@@ -221,3 +221,32 @@ def test_map_load_rejects_files_that_are_not_maps(tmp_path):
         with pytest.raises(lt.LTError) as e:
             lt.Map.load(str(f))
         assert e.value.code == lt.LT_EIO, f
+
+
+def test_poly_map_options_rejected_before_the_gpu():
+    """lt_build_poly_map validates its options on the host (no device needed)."""
+    import math
+    lens = lt.Lens(w.singlet_lens())
+    smax = math.tan(math.radians(10)) * math.sqrt(2)
+    good = dict(path_id=0, rho=12.0, smax=smax, degree=3, patches=(2, 2, 1, 1), cells=(2, 2, 2, 1), samples=5)
+    bad = [dict(degree=0), dict(degree=lt.POLY_MAX_DEGREE + 1), dict(samples=3), dict(samples=9),
+           dict(patches=(0, 1, 1, 1)), dict(cells=(1, 1, 1, 0)), dict(patches=(64, 1, 1, 1), cells=(65, 1, 1, 1)),
+           dict(rho=0.0), dict(smax=-1.0), dict(path_id=7), dict(lam=(780.0, 380.0))]
+    for b in bad:
+        a = dict(good, **b)
+        lam = a.pop("lam", (380.0, 780.0))
+        with pytest.raises(lt.LTError) as e:
+            lt.Map.build_poly(lens, a["path_id"], a["rho"], a["smax"], a["degree"], a["patches"],
+                              a["cells"], a["samples"], lam_lo=lam[0], lam_hi=lam[1], stream=0)
+        assert e.value.code == -1, (b, e.value)
+    # a table map has no polynomial fit to report
+    h = ctypes.c_void_p()
+    assert lt.lib().lt_poly_stats_get(h, None) == -1
+
+
+def test_binding_constants_match_the_header():
+    src = open(os.path.join(ROOT, "include", "lt.h")).read()
+    m = re.search(r"#define LT_NOALLOC_MAX_RAYS \(1 << (\d+)\)", src)
+    assert m and lt.NOALLOC_MAX_RAYS == 1 << int(m.group(1))
+    m = re.search(r"#define LT_POLY_MAX_DEGREE (\d+)", src)
+    assert m and lt.POLY_MAX_DEGREE == int(m.group(1))

@@ -254,3 +254,14 @@ def test_no_mask_ablation(singlet_map):
     ex, ev, _, _ = singlet_map.lens.trace(rays, (0, 0))
     # vignetted rays now get an output although the lens stops them
     assert np.sum((ev != 1) & (flags & 1 == 1)) > 100
+
+
+def test_fresh_classes_match_the_table(singlet_map):
+    """classify_fresh (a cell's corners traced afresh plus its fit rays) agrees
+    with the class table built in one pass."""
+    pm = singlet_map
+    rng = np.random.default_rng(8)
+    cells = [tuple(rng.integers(0, pm.grid.C)) for _ in range(80)]
+    cells += [tuple(c) for c in np.argwhere(pm.cell_class == poly.CELL_BOUNDARY)[:20]]
+    for cell in cells:
+        assert pm.classify_fresh(cell)[0] == pm.cell_class[cell], cell

@@ -83,3 +83,43 @@ def test_a_bad_input_flag_mismatch_fails(traced):
     f[r] |= 8
     with pytest.raises(AssertionError):
         compare_trace(out, f, ex, ev, edge, kmin, "bad-input")
+
+
+@pytest.fixture(scope="module")
+def ghost():
+    """The singlet's ghost (1, 2): many of its valid rays leave near grazing."""
+    p = w.singlet_lens()
+    ol = oracle.Lens(p)
+    rays = w.singlet_rays(20000)
+    ex, ev, edge, kmin = ol.trace(rays, (1, 2))
+    out = np.where((ev == 1)[:, None], ex, 0.0).astype(np.float32)
+    flags = np.where(ev == 1, F_VALID, np.where(ev == 8, 8, 0)).astype(np.uint8)
+    return ol, rays, out, flags, ex, ev, edge, kmin
+
+
+def test_a_planted_error_on_a_grazing_ray_fails(ghost):
+    """Grazing rays are held to a bound too: an error that neither the
+    tolerance nor the oracle's own sensitivity explains fails."""
+    ol, rays, out, flags, ex, ev, edge, kmin = ghost
+    g = np.flatnonzero((ev == 1) & (kmin < 1e-2) & (edge > 1e-3))
+    assert g.size > 0
+    r = int(g[0])
+    st = compare_trace(out, flags, ex, ev, edge, kmin, "clean ghost", cond=(ol, rays, (1, 2)))
+    assert st["grazing"] > 0 and st["value_violations"] == 0
+    for col, delta in ((0, 0.5), (2, 1e-2), (5, 1e-3)):
+        bad = out.copy()
+        bad[r, col] = np.float32(np.float64(bad[r, col]) + delta)
+        with pytest.raises(AssertionError):
+            compare_trace(bad, flags, ex, ev, edge, kmin, "planted grazing", cond=(ol, rays, (1, 2)))
+
+
+def test_a_planted_error_on_a_flagged_valid_ray_fails(traced):
+    """A near-edge flag exempts a ray's validity bit, never its values."""
+    out, flags, ex, ev, edge, kmin = traced
+    r = pick(traced)
+    f = flags.copy()
+    f[r] |= F_EDGE
+    bad = out.copy()
+    bad[r, 0] = np.float32(np.float64(bad[r, 0]) + 2 * POS_TOL)
+    with pytest.raises(AssertionError):
+        compare_trace(bad, f, ex, ev, edge, kmin, "planted flagged")

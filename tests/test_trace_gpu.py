@@ -83,8 +83,9 @@ def test_ragged_sizes(n):
     p = w.singlet_lens()
     rays = w.singlet_rays(n)
     out, flags = run_gpu(lt.Lens(p), rays, 0)
-    ex, ev, edge, kmin = oracle.Lens(p).trace(rays)
-    compare_trace(out, flags, ex, ev, edge, kmin, f"ragged {n}")
+    ol = oracle.Lens(p)
+    ex, ev, edge, kmin = ol.trace(rays)
+    compare_trace(out, flags, ex, ev, edge, kmin, f"ragged {n}", cond=(ol, rays, (0, 0)))
 
 
 def test_zero_rays_is_a_noop():
@@ -106,8 +107,9 @@ def test_bad_inputs_are_flagged():
     rays.lam[2] = 0.0
     rays.dy[3] = np.inf
     out, flags = run_gpu(lt.Lens(p), rays, 0)
-    ex, ev, edge, kmin = oracle.Lens(p).trace(rays)
-    compare_trace(out, flags, ex, ev, edge, kmin, "bad inputs")
+    ol = oracle.Lens(p)
+    ex, ev, edge, kmin = ol.trace(rays)
+    compare_trace(out, flags, ex, ev, edge, kmin, "bad inputs", cond=(ol, rays, (0, 0)))
     assert np.all(flags[:4] == lt.FLAG_BAD_INPUT)
 
 

@@ -7,8 +7,10 @@ is not allowed.  lt_query_noalloc gives them the map query with its trace
 queue in a fixed array inside the library instead of the memory pool.  This
 checks, through the C ABI, that it answers like lt_query on two calls in a
 row (the array keeps the first call's contents, so the second call shows
-that the counter is cleared), and that it refuses batches larger than the
-array.  The file is named to run last: if it fails, every other test has run.
+that the counter is cleared), that the device's free memory is the same
+before and after its calls (nothing was allocated), and that it refuses
+batches larger than the array.  The file is named to run last: if it fails,
+every other test has run.
 """
 import math
 
@@ -36,8 +38,11 @@ def test_noalloc_query_matches_lt_query_on_two_calls():
         ref = batch.DeviceOut(n)
         gmap.query(d.inp, d.lam, ref.out, n)
         got = batch.DeviceOut(n)
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         lt.query_noalloc(gmap, d.inp, d.lam, got.out, n)
         torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free_before, f"call {call}: device memory was allocated"
         ro, rf = ref.numpy()
         go, gf = got.numpy()
         assert np.array_equal(gf, rf), f"call {call}: flags differ"
