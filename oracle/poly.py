@@ -373,30 +373,95 @@ class PolyMap:
                 pred = self.evaluate(P, xi)
                 res = float(np.hypot(pred[:, 0] - out[:, 0], pred[:, 1] - out[:, 1]).max())
                 cls = CELL_VALID if res <= self.tol else CELL_BOUNDARY
-        if self.fit_rays is not None and len(self.fit_rays):
-            if not hasattr(self, "_fit_cells"):
-                u32, ok = reduce_f32(*self.fit_rays.arrays())
-                g, inside = G.grid_coords(u32)
-                self._fit_in = inside & ok
-                self._fit_cells = np.ravel_multi_index(tuple(G.cell_of(g).T), tuple(G.C))
-            cid = int(np.ravel_multi_index(tuple(cell), tuple(G.C)))
-            idx = np.nonzero(self._fit_in & (self._fit_cells == cid))[0]
-            if idx.size and cls != CELL_BOUNDARY:
-                sub = self.fit_rays.subset(idx)
-                o, v, _, _ = self.lens.trace(sub, self.path)
-                valid = v == 1
-                if cls == CELL_INVALID and valid.any():
+        idx = self._fit_rays_in(cell)
+        if idx.size and cls != CELL_BOUNDARY:
+            sub = self.fit_rays.subset(idx)
+            o, v, _, _ = self.lens.trace(sub, self.path)
+            valid = v == 1
+            if cls == CELL_INVALID and valid.any():
+                cls = CELL_BOUNDARY
+            elif cls == CELL_VALID:
+                if not valid.all():
                     cls = CELL_BOUNDARY
-                elif cls == CELL_VALID:
-                    if not valid.all():
+                else:
+                    pred = self.predict(sub, np.tile(cell, (idx.size, 1)), np.arange(idx.size))
+                    for j in range(idx.size):
+                        r = math.hypot(pred[j][0] - o[j, 0], pred[j][1] - o[j, 1])
+                        res = max(res, r)
+                    if res > self.tol:
                         cls = CELL_BOUNDARY
-                    else:
-                        pred = self.predict(sub, np.tile(cell, (idx.size, 1)), np.arange(idx.size))
-                        for j in range(idx.size):
-                            r = math.hypot(pred[j][0] - o[j, 0], pred[j][1] - o[j, 1])
-                            res = max(res, r)
-                        if res > self.tol:
-                            cls = CELL_BOUNDARY
+        return cls, res
+
+    def _fit_rays_in(self, cell):
+        """Indices of the fit rays inside `cell` (an index sorted by cell, built once)."""
+        if self.fit_rays is None or not len(self.fit_rays):
+            return np.zeros(0, np.int64)
+        G = self.grid
+        if not hasattr(self, "_fit_order"):
+            u32, ok = reduce_f32(*self.fit_rays.arrays())
+            g, inside = G.grid_coords(u32)
+            cid = np.ravel_multi_index(tuple(G.cell_of(g).T), tuple(G.C))
+            cid = np.where(inside & ok, cid, -1)
+            self._fit_order = np.argsort(cid, kind="stable")
+            self._fit_sorted = cid[self._fit_order]
+        c = int(np.ravel_multi_index(tuple(np.asarray(cell, np.int64)), tuple(G.C)))
+        a, b = np.searchsorted(self._fit_sorted, [c, c + 1])
+        return np.sort(self._fit_order[a:b])
+
+    def classify_cells(self, cells):
+        """classify_fresh of many cells [k,4] at once (one trace of all their
+        corners, a patch's polynomial evaluated for all its cells together):
+        (classes [k], residuals [k])."""
+        G = self.grid
+        cells = np.asarray(cells, np.int64).reshape(-1, 4)
+        k = len(cells)
+        corners = np.array(list(itertools.product((0, 1), repeat=4)), np.int64)
+        nodes = (cells[:, None, :] + corners[None, :, :]).reshape(-1, 4)
+        arrs = G.node_rays_f32(nodes)
+        out, v, _, _ = self.lens.trace(_rays(arrs), self.path)
+        vs = (v == 1).reshape(k, 16)
+        out = out.reshape(k, 16, 6)
+        cls = np.where(vs.all(1), CELL_VALID, np.where(vs.any(1), CELL_BOUNDARY, CELL_INVALID)).astype(np.uint8)
+        res = np.zeros(k)
+        P = cells // G.m
+        pid = np.ravel_multi_index(tuple(P.T), tuple(G.P))
+        cls[(cls == CELL_VALID) & ~self.patch_ok[pid]] = CELL_BOUNDARY
+        for q in np.unique(pid[cls == CELL_VALID]):
+            sel = np.nonzero((pid == q) & (cls == CELL_VALID))[0]
+            xi = (2.0 * (cells[sel][:, None, :] + corners[None] - P[sel][:, None, :] * G.m) / G.m - 1.0).reshape(-1, 4)
+            pred = (monomials(xi, self.exps) @ self.coef[q]).reshape(len(sel), 16, 5)
+            r = np.hypot(pred[:, :, 0] - out[sel, :, 0], pred[:, :, 1] - out[sel, :, 1]).max(1)
+            res[sel] = r
+            cls[sel[r > self.tol]] = CELL_BOUNDARY
+        # fit rays inside the cells can only demote them (all of them traced
+        # and evaluated at once; per cell: any valid ray demotes an INVALID
+        # cell, any invalid ray or residual above tol a VALID one)
+        if self.fit_rays is not None and len(self.fit_rays):
+            self._fit_rays_in(cells[0])
+            cid = np.ravel_multi_index(tuple(cells.T), tuple(G.C))
+            a = np.searchsorted(self._fit_sorted, cid)
+            b = np.searchsorted(self._fit_sorted, cid + 1)
+            owner = np.repeat(np.arange(k), b - a)
+            idx = np.concatenate([self._fit_order[x:y] for x, y in zip(a, b)]) if owner.size else \
+                np.zeros(0, np.int64)
+            keep = cls[owner] != CELL_BOUNDARY
+            owner, idx = owner[keep], idx[keep]
+            if idx.size:
+                sub = self.fit_rays.subset(idx)
+                o, v2, _, _ = self.lens.trace(sub, self.path)
+                valid = v2 == 1
+                seen_v = np.zeros(k, bool)
+                seen_i = np.zeros(k, bool)
+                np.logical_or.at(seen_v, owner, valid)
+                np.logical_or.at(seen_i, owner, ~valid)
+                cls[(cls == CELL_INVALID) & seen_v] = CELL_BOUNDARY
+                vsel = np.nonzero((cls[owner] == CELL_VALID) & valid)[0]
+                if vsel.size:
+                    pred = self.predict(sub, cells[owner], vsel)
+                    r = np.array([math.hypot(pred[int(j)][0] - o[j, 0], pred[int(j)][1] - o[j, 1]) for j in vsel])
+                    np.maximum.at(res, owner[vsel], r)
+                bad = (cls == CELL_VALID) & (seen_i | (res > self.tol))
+                cls[bad] = CELL_BOUNDARY
         return cls, res
 
     def _apply_fit_rays(self, rays):

@@ -723,7 +723,7 @@ lt_status launch_queue_trace(const lt_map* map, const RaysOutDev& out, uint32_t 
 lt_status launch_query_with(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
                             int mode, const TraceQueue& Q, cudaStream_t st)
 {
-    if (map->kind == LT_MAP_KIND_POLY) return launch_poly_query(map, in, out, n, mode, &Q, st);
+    if (map->kind == LT_MAP_KIND_POLY) return launch_poly_fused(map, in, out, n, mode, st);
     LT_CUDA_TRY(cudaMemsetAsync(Q.count, 0, kQHeaderBytes, st));
     lt_status s = launch_classify(map, in, out, n, mode, Q, st);
     if (s != LT_OK) return s;
@@ -733,7 +733,7 @@ lt_status launch_query_with(const lt_map* map, const RaysInDev& in, const RaysOu
 lt_status launch_query(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
                        int mode, cudaStream_t st)
 {
-    if (map->kind == LT_MAP_KIND_POLY) return launch_poly_query(map, in, out, n, mode, nullptr, st);
+    if (map->kind == LT_MAP_KIND_POLY) return launch_poly_query(map, in, out, n, mode, st);
     if (n <= kFusedMaxRays) {
         const unsigned blocks = (n + kQTile - 1) / kQTile;
         const bool table = mode == LT_QUERY_TABLE;
@@ -793,8 +793,7 @@ lt_map::~lt_map()
     if (node) cudaFree(node);
     if (node_valid) cudaFree(node_valid);
     if (cls) cudaFree(cls);
-    if (coef4) cudaFree(coef4);
-    if (coefI) cudaFree(coefI);
+    if (coefg) cudaFree(coefg);
     if (coef64) cudaFree(coef64);
     if (patch_ok) cudaFree(patch_ok);
 }

@@ -47,6 +47,24 @@ constexpr size_t query_segcap(size_t n) { return ((n + kQTile - 1) / kQTile + kQ
 // scratch bytes of the queue for n rays: the counters, then 7 arrays of
 // kQSegs * segcap words
 constexpr size_t query_scratch_bytes(size_t n) { return kQHeaderBytes + 7 * 4 * kQSegs * query_segcap(n); }
+
+// The polynomial-patch map's large-batch query also keeps, per tile of
+// kSortTileRays rays, a record of each ray the polynomial answers (its
+// patch-local coordinates, rotation, mirror, patch and index in the tile:
+// 32 bytes) in the tile's region, sorted by patch, and the tile's count.
+constexpr size_t kSortTileRays = 1024;
+constexpr size_t query_tiles(size_t n) { return (n + kSortTileRays - 1) / kSortTileRays; }
+constexpr size_t poly_scratch_bytes(size_t n)
+{
+    return query_scratch_bytes(n) + query_tiles(n) * (kSortTileRays * 32 + 4) + 256;
+}
+struct PolyScratch {
+    float4* rec;          // query_tiles(n) x kSortTileRays x 2 float4
+    uint32_t* tile_nv;    // query_tiles(n)
+};
+// the records and counts after the queue of n rays in `scratch` (poly_scratch_bytes(n))
+PolyScratch poly_scratch_at(void* scratch, size_t n);
+
 // the queue laid out in `scratch` (256-byte aligned, query_scratch_bytes(n))
 TraceQueue trace_queue_at(void* scratch, size_t n);
 
@@ -86,17 +104,20 @@ struct PolyDev {
     uint32_t mdiv[4];                   // ceil(2^32 / m): cell / m = umulhi(cell, mdiv) for cell < 2^16
     uint32_t cstride[4], pstride[4];    // class-grid cell and patch strides (w fastest)
     int T, degree, n_patches;
-    const float4* c4;                   // [patch][term]: x', y', d_x', d_y' coefficients
-    const float* cI;                    // [patch][term]: I coefficients
+    const float4* cg;                   // [patch][group of 4 terms][output]: coefficient groups
     const uint8_t* patch_ok;            // [patch]: 1 if the patch has a fit
     const uint32_t* cls;                // 2 bits per class-grid cell
 };
 
-// The polynomial-patch map's query on `st` (launch_query / launch_query_with
-// dispatch here for such maps); Q may be NULL: then batches of at most
-// kFusedMaxRays run as one kernel and larger ones take a queue from the pool.
+// The polynomial-patch map's query on `st` (launch_query dispatches here for
+// such maps): batches of at most kFusedMaxRays run as one kernel, larger
+// ones take their queue and records from the pool.  launch_query_with, whose
+// caller supplies only a queue, runs the one-kernel form in chunks.
 lt_status launch_poly_query(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
-                            int mode, const TraceQueue* Q, cudaStream_t st);
+                            int mode, cudaStream_t st);
+// the one-kernel form over n rays in chunks of at most kFusedMaxRays (no scratch)
+lt_status launch_poly_fused(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n, int mode,
+                            cudaStream_t st);
 
 }  // namespace lt
 
@@ -121,8 +142,7 @@ struct lt_map {
     lt_poly_opts popts = {};  // the build options (fit arrays cleared)
     lt_poly_stats pstats = {};
     lt::PolyDev pdev = {};
-    float4* coef4 = nullptr;
-    float* coefI = nullptr;
+    float4* coefg = nullptr;  // the FP32 query table (coefficient groups)
     double* coef64 = nullptr; // patches x terms x 5, the FP64 fit
     uint8_t* patch_ok = nullptr;
     ~lt_map();

@@ -11,6 +11,7 @@
 // across the vignetting edge and a low-degree polynomial on a coarse patch
 // reproduces it to the FP32 tracer's own error, while the mask resolves the
 // occlusion on a finer grid.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -48,9 +49,7 @@ static void horner_exponents(int D, std::vector<int32_t>& e)
 
 // ------------------------------------------------------------------ evaluation
 
-// The five outputs of a patch polynomial: (x', y') and (d_x', d_y') as pairs
-// (packed FP32x2 FMAs: two IEEE FMAs per instruction, bit for bit the scalar
-// ones), I alone.
+// The five outputs of a patch polynomial: (x', y'), (d_x', d_y') and I.
 struct Acc5 {
     float2 p, d;
     float I;
@@ -64,55 +63,145 @@ __device__ __forceinline__ void acc_load(Acc5& a, const float4 v, float vi)
 }
 __device__ __forceinline__ void acc_step(Acc5& a, float t, const float4 v, float vi)
 {
-    const float2 tt = make_float2(t, t);
-    a.p = __ffma2_rn(a.p, tt, make_float2(v.x, v.y));
-    a.d = __ffma2_rn(a.d, tt, make_float2(v.z, v.w));
+    a.p.x = fmaf(a.p.x, t, v.x);
+    a.p.y = fmaf(a.p.y, t, v.y);
+    a.d.x = fmaf(a.d.x, t, v.z);
+    a.d.y = fmaf(a.d.y, t, v.w);
     a.I = fmaf(a.I, t, vi);
 }
 __device__ __forceinline__ void acc_step(Acc5& a, float t, const Acc5& v)
 {
-    const float2 tt = make_float2(t, t);
-    a.p = __ffma2_rn(a.p, tt, v.p);
-    a.d = __ffma2_rn(a.d, tt, v.d);
+    a.p.x = fmaf(a.p.x, t, v.p.x);
+    a.p.y = fmaf(a.p.y, t, v.p.y);
+    a.d.x = fmaf(a.d.x, t, v.d.x);
+    a.d.y = fmaf(a.d.y, t, v.d.y);
     a.I = fmaf(a.I, t, v.I);
 }
 
-// The patch polynomial at xi by nested Horner steps (T - 1 FMAs per output):
-// P = sum_a xi_r^a Q_a(xi_p, xi_q, xi_w), each Q_a likewise in the next
-// variable; coefficients are read in horner_exponents order.
-template <int D>
-__device__ __forceinline__ Acc5 poly_eval(const float4* __restrict__ C4, const float* __restrict__ CI,
-                                          const float xi[4])
+// Coefficient groups: per patch poly_groups(D) groups of four consecutive
+// terms (horner_exponents order); group g is five float4s -- the x', y',
+// d_x', d_y' and I coefficients of terms 4g .. 4g + 3 (zeros past the last
+// term) -- so one 16-byte load brings an output's coefficients of four terms.
+__host__ __device__ constexpr int poly_groups(int D) { return (poly_terms(D) + 3) / 4; }
+
+__device__ __forceinline__ float f4c(const float4& v, int i)
 {
-    Acc5 A0;
+    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// The patch polynomial at NR points of one patch (NR = 1 or 2) by nested
+// Horner steps (T - 1 FMAs per output and point):
+// P = sum_a xi_r^a Q_a(xi_p, xi_q, xi_w), each Q_a likewise in the next
+// variable.  The points share every coefficient load.
+template <int D, int NR>
+__device__ __forceinline__ void poly_eval(const float4* __restrict__ G, const float (*xi)[4], Acc5* res)
+{
+    float4 cur[5];
     int k = 0;
+    Acc5 A0[NR];
 #pragma unroll
     for (int a = D; a >= 0; --a) {
-        Acc5 A1;
+        Acc5 A1[NR];
 #pragma unroll
         for (int b = D - a; b >= 0; --b) {
-            Acc5 A2;
+            Acc5 A2[NR];
 #pragma unroll
             for (int c = D - a - b; c >= 0; --c) {
-                Acc5 A3;
+                Acc5 A3[NR];
 #pragma unroll
                 for (int e = D - a - b - c; e >= 0; --e) {
-                    const float4 v = __ldg(C4 + k);
-                    const float vi = __ldg(CI + k);
+                    if (k % 4 == 0) {
+#pragma unroll
+                        for (int o = 0; o < 5; ++o) cur[o] = __ldg(G + (k / 4) * 5 + o);
+                    }
+                    const float4 v = make_float4(f4c(cur[0], k % 4), f4c(cur[1], k % 4), f4c(cur[2], k % 4),
+                                                 f4c(cur[3], k % 4));
+                    const float vi = f4c(cur[4], k % 4);
                     ++k;
-                    if (e == D - a - b - c) acc_load(A3, v, vi);
-                    else acc_step(A3, xi[3], v, vi);
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        if (e == D - a - b - c) acc_load(A3[r], v, vi);
+                        else acc_step(A3[r], xi[r][3], v, vi);
+                    }
                 }
-                if (c == D - a - b) A2 = A3;
-                else acc_step(A2, xi[2], A3);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    if (c == D - a - b) A2[r] = A3[r];
+                    else acc_step(A2[r], xi[r][2], A3[r]);
+                }
             }
-            if (b == D - a) A1 = A2;
-            else acc_step(A1, xi[1], A2);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                if (b == D - a) A1[r] = A2[r];
+                else acc_step(A1[r], xi[r][1], A2[r]);
+            }
         }
-        if (a == D) A0 = A1;
-        else acc_step(A0, xi[0], A1);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            if (a == D) A0[r] = A1[r];
+            else acc_step(A0[r], xi[r][0], A1[r]);
+        }
     }
-    return A0;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) res[r] = A0[r];
+}
+
+// The same evaluation from a table in shared memory (plain loads), each
+// point with its own patch's coefficients (the same addresses when the
+// points share a patch).
+template <int D, int NR>
+__device__ __forceinline__ void poly_eval_tab(const float4* const G[NR], const float (*xi)[4], Acc5* res)
+{
+    float4 cur[NR][5];
+    int k = 0;
+    Acc5 A0[NR];
+#pragma unroll
+    for (int a = D; a >= 0; --a) {
+        Acc5 A1[NR];
+#pragma unroll
+        for (int b = D - a; b >= 0; --b) {
+            Acc5 A2[NR];
+#pragma unroll
+            for (int c = D - a - b; c >= 0; --c) {
+                Acc5 A3[NR];
+#pragma unroll
+                for (int e = D - a - b - c; e >= 0; --e) {
+                    if (k % 4 == 0) {
+#pragma unroll
+                        for (int r = 0; r < NR; ++r)
+#pragma unroll
+                            for (int o = 0; o < 5; ++o) cur[r][o] = G[r][(k / 4) * 5 + o];
+                    }
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const float4 v = make_float4(f4c(cur[r][0], k % 4), f4c(cur[r][1], k % 4),
+                                                     f4c(cur[r][2], k % 4), f4c(cur[r][3], k % 4));
+                        const float vi = f4c(cur[r][4], k % 4);
+                        if (e == D - a - b - c) acc_load(A3[r], v, vi);
+                        else acc_step(A3[r], xi[r][3], v, vi);
+                    }
+                    ++k;
+                }
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    if (c == D - a - b) A2[r] = A3[r];
+                    else acc_step(A2[r], xi[r][2], A3[r]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                if (b == D - a) A1[r] = A2[r];
+                else acc_step(A1[r], xi[r][1], A2[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            if (a == D) A0[r] = A1[r];
+            else acc_step(A0[r], xi[r][0], A1[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) res[r] = A0[r];
 }
 
 // The FP32 rule for the reduced coordinates (documented in lt.h): three
@@ -194,13 +283,10 @@ __device__ __forceinline__ uint32_t poly_class(const PolyDev& P, uint32_t cid)
     return (ld_stream(P.cls + (cid >> 4)) >> ((cid & 15u) * 2u)) & 3u;
 }
 
-// Exit ray in the input frame from the patch polynomial at xi (mirror m,
-// rotation (c, s)).
-template <int D>
-__device__ __forceinline__ void poly_output(const PolyDev& P, uint32_t pid, const float xi[4], float c, float s,
-                                            float m, float o[6])
+// Exit ray in the input frame from a patch polynomial's reduced-frame value
+// (mirror m, rotation (c, s)).
+__device__ __forceinline__ void poly_unreduce(const Acc5& a, float c, float s, float m, float o[6])
 {
-    const Acc5 a = poly_eval<D>(P.c4 + (size_t)pid * poly_terms(D), P.cI + (size_t)pid * poly_terms(D), xi);
     const float yp = m * a.p.y, dyp = m * a.d.y;
     const float dz2 = fmaf(-a.d.x, a.d.x, fmaf(-dyp, dyp, 1.0f));
     o[0] = fmaf(c, a.p.x, -s * yp);
@@ -209,6 +295,21 @@ __device__ __forceinline__ void poly_output(const PolyDev& P, uint32_t pid, cons
     o[3] = fmaf(s, a.d.x, c * dyp);
     o[4] = dz2 > 0.0f ? sqrtf(dz2) : 0.0f;
     o[5] = a.I;
+}
+
+__device__ __forceinline__ const float4* poly_patch_groups(const PolyDev& P, uint32_t pid, int D)
+{
+    return P.cg + (size_t)pid * poly_groups(D) * 5;
+}
+
+template <int D>
+__device__ __forceinline__ void poly_output(const PolyDev& P, uint32_t pid, const float xi[4], float c, float s,
+                                            float m, float o[6])
+{
+    const float x1[1][4] = {{xi[0], xi[1], xi[2], xi[3]}};
+    Acc5 a;
+    poly_eval<D, 1>(poly_patch_groups(P, pid, D), x1, &a);
+    poly_unreduce(a, c, s, m, o);
 }
 
 // A ray of a query after classification.
@@ -302,40 +403,49 @@ poly_query_kernel(const __grid_constant__ PolyDev P, RaysInDev in, RaysOutDev ou
     if (r < n) poly_store(out, r, c.o, c.ip ? LT_FLAG_VALID : 0u);
 }
 
-// Large batches, maps of at most kSortMaxPatches patches: each block takes a
-// tile of kSortTile rays and
-//  A. classifies them (coalesced, evict-first loads; four rounds of 256
-//     consecutive rays): BOUNDARY / outside rays go to the trace queue, VALID
-//     rays count into a shared-memory histogram over patches (the atomic's
-//     return value is the ray's rank within its patch) and leave their
-//     patch-local xi, rotation and mirror in shared memory;
+// Large batches, maps of at most kSortMaxPatches patches, run as three
+// kernels: classify-and-sort, evaluate, and the queue's tracer.
+//
+// poly_sort_kernel takes a tile of kSortTile rays per block:
+//  A. classifies them (coalesced loads that bypass L1, four rounds of 256
+//     consecutive rays, every input of the four in flight at once):
+//     BOUNDARY / outside rays go to the trace queue, VALID rays count into
+//     a shared-memory histogram over patches (the atomic's return value is
+//     the ray's rank within its patch);
 //  B. one warp turns the histogram into offsets (exclusive scan);
-//  C. every VALID ray's tile-local index goes to its sorted slot;
-//  D. the block evaluates the VALID rays in slot order: consecutive lanes
-//     mostly share a patch, so each coefficient load is one or two addresses
-//     for the whole warp instead of one per lane, and no lane idles on an
-//     INVALID or queued ray; the exit ray replaces the record in place;
-//  E. every row of the tile is stored, coalesced: the exit ray of a VALID
-//     ray, zeros otherwise (a placeholder that the queue's tracer overwrites
-//     for a queued ray).
+//  C. every VALID ray writes its record -- patch-local xi, rotation (c, s),
+//     a word holding its mirror and patch, its index in the tile: 32 bytes,
+//     one sector -- to its sorted slot of the tile's region, and the count
+//     goes to the tile's counter.
 // Round j of tile b appends to queue segment (4 b + j) % kQSegs: the same
 // segment a 256-ray block of the same rays would use, so the queue's
 // capacity rule (query_segcap) holds.
+//
+// poly_eval_kernel, a persistent grid launched as a programmatic dependent
+// of the sort kernel, copies the coefficient table to shared memory once
+// per block (while the sort kernel drains) and then, tile after tile:
+// evaluates the tile's records in sorted order (coalesced reads; adjacent
+// records mostly share a patch, so a coefficient load is one or two
+// shared-memory addresses for the whole warp); stages the tile's rows in
+// shared memory (zeros for every other ray: a placeholder the queue's
+// tracer overwrites for a queued ray); and stores the rows coalesced.
 constexpr int kSortThreads = 256;
 constexpr int kSortRounds = 4;
 constexpr int kSortTile = kSortThreads * kSortRounds;
 constexpr int kSortMaxPatches = 1024;
 static_assert(kSortThreads == kQTile, "a sort round must be one queue block");
+static_assert(kSortTile == (int)kSortTileRays, "the sorted-index region is laid out in sort tiles");
+constexpr int kEvalThreads = 256;
+// largest coefficient table the evaluation kernel keeps in shared memory
+constexpr size_t kEvalMaxTableBytes = 96 * 1024;
 
-template <int D, int MODE>
+template <int MODE>
 __global__ void __launch_bounds__(kSortThreads)
-poly_query_sorted_kernel(const __grid_constant__ PolyDev P, RaysInDev in, RaysOutDev out, uint32_t n,
-                         TraceQueue Q)
+poly_sort_kernel(const __grid_constant__ PolyDev P, RaysInDev in, uint32_t n, TraceQueue Q, PolyScratch R)
 {
     __shared__ uint32_t hist[kSortMaxPatches];
-    __shared__ uint16_t order[kSortTile];
-    __shared__ float4 recA[kSortTile];     // xi, then the exit (x, y, d_x, d_y)
-    __shared__ float4 recB[kSortTile];     // (c, s, m, patch bits), then (d_z, I, -, -)
+    __shared__ float4 recA[kSortTile];      // xi
+    __shared__ float4 recB[kSortTile];      // c, s, (mirror << 31 | patch), index in the tile
     __shared__ uint32_t nvalid;
     const unsigned full = 0xffffffffu;
     const int t = threadIdx.x, lane = t & 31;
@@ -358,22 +468,22 @@ poly_query_sorted_kernel(const __grid_constant__ PolyDev P, RaysInDev in, RaysOu
             lam[j] = ld_stream(in.lam + r);
         }
     }
-    // A.2: reduce and locate; the record goes to shared memory, the cell's
-    // class word is requested for all four rays before any is used
-    uint32_t cid[kSortRounds], word[kSortRounds], stat[kSortRounds];   // stat: 0 dead, 1 outside, 2 inside
+    // A.2: cells and patches; the class words of all four are requested
+    // before any is used
+    uint32_t cid[kSortRounds], pid[kSortRounds], word[kSortRounds], stat[kSortRounds];   // 0 none, 1 outside, 2 inside
 #pragma unroll
     for (int j = 0; j < kSortRounds; ++j) {
-        const uint32_t l = (uint32_t)(j * kSortThreads + t);
         stat[j] = 0;
-        cid[j] = 0;
+        cid[j] = pid[j] = 0;
+        const uint32_t l = (uint32_t)(j * kSortThreads + t);
         if (r0 + l < n) {
             float u[4], xi[4], cs, sn, m;
-            uint32_t pid;
             stat[j] = 1;
-            if (poly_reduce(x[j], y[j], dx[j], dy[j], dz[j], lam[j], u, cs, sn, m) && poly_locate(P, u, cid[j], pid, xi)) {
+            if (poly_reduce(x[j], y[j], dx[j], dy[j], dz[j], lam[j], u, cs, sn, m) && poly_locate(P, u, cid[j], pid[j], xi)) {
                 stat[j] = 2;
                 recA[l] = make_float4(xi[0], xi[1], xi[2], xi[3]);
-                recB[l] = make_float4(cs, sn, m, __uint_as_float(pid));
+                recB[l] = make_float4(cs, sn, __uint_as_float((m < 0.0f ? 0x80000000u : 0u) | pid[j]),
+                                      __uint_as_float(l));
             }
         }
     }
@@ -382,49 +492,54 @@ poly_query_sorted_kernel(const __grid_constant__ PolyDev P, RaysInDev in, RaysOu
         word[j] = 0;
         if (stat[j] == 2) {
             if (MODE == LT_QUERY_TABLE) word[j] = ld_stream(P.cls + (cid[j] >> 4));
-            else word[j] = __ldg(P.patch_ok + __float_as_uint(recB[j * kSortThreads + t].w));
+            else word[j] = __ldg(P.patch_ok + pid[j]);
         }
     }
-    // A.3: classes, histogram ranks, trace queue
+    // A.3: classes and histogram ranks; then the trace queue, whose four
+    // appends (one per round, each one atomic per warp) are all issued before
+    // any result is used
     uint32_t key[kSortRounds];
+    unsigned mq[kSortRounds];
 #pragma unroll
     for (int j = 0; j < kSortRounds; ++j) {
-        const uint32_t l = (uint32_t)(j * kSortThreads + t);
-        const uint32_t r = r0 + l;
         key[j] = 0xffffffffu;
         bool tr = stat[j] == 1;
-        const uint32_t tag = r | (stat[j] == 1 ? kOutsideBit : 0u);
         if (stat[j] == 2) {
             uint32_t k;
             if (MODE == LT_QUERY_TABLE) k = (word[j] >> ((cid[j] & 15u) * 2u)) & 3u;
             else k = word[j] ? (uint32_t)LT_CELL_VALID : (uint32_t)LT_CELL_BOUNDARY;
-            if (k == LT_CELL_VALID) {
-                const uint32_t pid = __float_as_uint(recB[l].w);
-                key[j] = (pid << 16) | atomicAdd(&hist[pid], 1u);
-            } else {
-                tr = k != LT_CELL_INVALID;
-            }
+            if (k == LT_CELL_VALID) key[j] = (pid[j] << 16) | atomicAdd(&hist[pid[j]], 1u);
+            else tr = k != LT_CELL_INVALID;
         }
-        const unsigned mq = __ballot_sync(full, tr);
-        if (mq) {
-            const int leader = __ffs(mq) - 1;
-            uint32_t b = 0;
+        mq[j] = __ballot_sync(full, tr);
+    }
+    uint32_t qb[kSortRounds];
+#pragma unroll
+    for (int j = 0; j < kSortRounds; ++j) {
+        qb[j] = 0;
+        if (mq[j] && lane == __ffs(mq[j]) - 1)
+            qb[j] = atomicAdd(Q.count + ((blockIdx.x * kSortRounds + j) % kQSegs) * kQCountStride,
+                              (uint32_t)__popc(mq[j]));
+    }
+#pragma unroll
+    for (int j = 0; j < kSortRounds; ++j) {
+        if (!mq[j]) continue;
+        const uint32_t b = __shfl_sync(full, qb[j], __ffs(mq[j]) - 1);
+        if ((mq[j] >> lane) & 1u) {
             const uint32_t seg = (blockIdx.x * kSortRounds + j) % kQSegs;
-            if (lane == leader) b = atomicAdd(Q.count + seg * kQCountStride, (uint32_t)__popc(mq));
-            b = __shfl_sync(full, b, leader);
-            if (tr) {
-                const uint32_t k = seg * Q.segcap + b + __popc(mq & ((1u << lane) - 1u));
-                Q.x[k] = x[j];
-                Q.y[k] = y[j];
-                Q.dx[k] = dx[j];
-                Q.dy[k] = dy[j];
-                Q.dz[k] = dz[j];
-                Q.lam[k] = lam[j];
-                Q.tag[k] = tag;
-            }
+            const uint32_t k = seg * Q.segcap + b + __popc(mq[j] & ((1u << lane) - 1u));
+            const uint32_t r = r0 + (uint32_t)(j * kSortThreads + t);
+            Q.x[k] = x[j];
+            Q.y[k] = y[j];
+            Q.dx[k] = dx[j];
+            Q.dy[k] = dy[j];
+            Q.dz[k] = dz[j];
+            Q.lam[k] = lam[j];
+            Q.tag[k] = r | (stat[j] == 1 ? kOutsideBit : 0u);
         }
     }
     __syncthreads();
+    // B
     if (t < 32) {
         const int per = (NP + 31) / 32;
         const int b0 = min(NP, lane * per), b1 = min(NP, b0 + per);
@@ -445,32 +560,75 @@ poly_query_sorted_kernel(const __grid_constant__ PolyDev P, RaysInDev in, RaysOu
         if (lane == 31) nvalid = incl;
     }
     __syncthreads();
+    // C
+    float4* rec = R.rec + (size_t)blockIdx.x * kSortTile * 2;
+    if (t == 0) R.tile_nv[blockIdx.x] = nvalid;
 #pragma unroll
     for (int j = 0; j < kSortRounds; ++j)
-        if (key[j] != 0xffffffffu) order[hist[key[j] >> 16] + (key[j] & 0xffffu)] = (uint16_t)(j * kSortThreads + t);
-    __syncthreads();
-    const uint32_t nv = nvalid;
-#pragma unroll 1
-    for (uint32_t sl = (uint32_t)t; sl < nv; sl += kSortThreads) {
-        const uint32_t l = order[sl];
-        const float4 a = recA[l], b = recB[l];
-        const float xi[4] = {a.x, a.y, a.z, a.w};
-        float o[6];
-        poly_output<D>(P, __float_as_uint(b.w), xi, b.x, b.y, b.z, o);
-        recA[l] = make_float4(o[0], o[1], o[2], o[3]);
-        recB[l] = make_float4(o[4], o[5], 0.0f, 0.0f);
+        if (key[j] != 0xffffffffu) {
+            const uint32_t l = (uint32_t)(j * kSortThreads + t);
+            const uint32_t slot = hist[key[j] >> 16] + (key[j] & 0xffffu);
+            rec[slot * 2] = recA[l];
+            rec[slot * 2 + 1] = recB[l];
+        }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kEvalThreads)
+poly_eval_kernel(const __grid_constant__ PolyDev P, RaysOutDev out, uint32_t n, PolyScratch R, uint32_t ntiles)
+{
+    extern __shared__ float4 smc[];                 // the coefficient table
+    __shared__ float ob[6][kSortTile];              // the tile's rows
+    __shared__ uint8_t of[kSortTile];
+    const int t = threadIdx.x;
+    const int ntab = P.n_patches * poly_groups(D) * 5;
+    for (int i = t; i < ntab; i += kEvalThreads) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(smc + i);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(P.cg + i));
     }
+    asm volatile("cp.async.commit_group;");
+    // the sort kernel's records are read only after it has completed
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
+#pragma unroll 1
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint32_t r0 = tile * kSortTile;
+        const uint32_t cnt = min((uint32_t)kSortTile, n - r0);
+        for (uint32_t l = (uint32_t)t; l < (uint32_t)kSortTile; l += kEvalThreads) {
 #pragma unroll
-    for (int j = 0; j < kSortRounds; ++j) {
-        const uint32_t l = (uint32_t)(j * kSortThreads + t);
-        const uint32_t r = r0 + l;
-        if (r >= n) continue;
-        const bool v = key[j] != 0xffffffffu;
-        const float4 a = v ? recA[l] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 b = v ? recB[l] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float o[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
-        poly_store(out, r, o, v ? LT_FLAG_VALID : 0u);
+            for (int q = 0; q < 6; ++q) ob[q][l] = 0.0f;
+            of[l] = 0;
+        }
+        __syncthreads();
+        const uint32_t nv = R.tile_nv[tile];
+        const float4* rec = R.rec + (size_t)tile * kSortTile * 2;
+#pragma unroll 1
+        for (uint32_t sl = (uint32_t)t; sl < nv; sl += kEvalThreads) {
+            const float4 a = rec[sl * 2], b = rec[sl * 2 + 1];
+            const uint32_t w = __float_as_uint(b.z), l = __float_as_uint(b.w);
+            const float xi[1][4] = {{a.x, a.y, a.z, a.w}};
+            const float4* G[1] = {smc + (size_t)(w & 0x7fffffffu) * poly_groups(D) * 5};
+            Acc5 acc;
+            poly_eval_tab<D, 1>(G, xi, &acc);
+            float o[6];
+            poly_unreduce(acc, b.x, b.y, (w & 0x80000000u) ? -1.0f : 1.0f, o);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) ob[q][l] = o[q];
+            of[l] = LT_FLAG_VALID;
+        }
+        __syncthreads();
+        for (uint32_t l = (uint32_t)t; l < cnt; l += kEvalThreads) {
+            const uint32_t r = r0 + l;
+            __stcs(out.x + r, ob[0][l]);
+            __stcs(out.y + r, ob[1][l]);
+            __stcs(out.dx + r, ob[2][l]);
+            __stcs(out.dy + r, ob[3][l]);
+            __stcs(out.dz + r, ob[4][l]);
+            __stcs(out.I + r, ob[5][l]);
+            out.flags[r] = of[l];
+        }
+        __syncthreads();
     }
 }
 
@@ -678,14 +836,21 @@ poly_sample_residual_kernel(const __grid_constant__ PolyBuild B, const double* _
     if ((threadIdx.x & 31) == 0 && res > 0.0) atomicMax(resmax, (unsigned long long)__double_as_longlong(res));
 }
 
+// The FP32 query table from the FP64 fit: one thread per (patch, group,
+// output) float4.
 __global__ void __launch_bounds__(256)
-poly_pack_kernel(const double* __restrict__ coef, float4* __restrict__ c4, float* __restrict__ cI, uint32_t total)
+poly_pack_kernel(const double* __restrict__ coef, float4* __restrict__ cg, int T, int NG, uint32_t total)
 {
     const uint32_t l = blockIdx.x * 256u + threadIdx.x;
     if (l >= total) return;
-    const double* c = coef + (size_t)l * 5;
-    c4[l] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)c[3]);
-    cI[l] = (float)c[4];
+    const uint32_t o = l % 5, g = (l / 5) % (uint32_t)NG, pid = l / (5u * (uint32_t)NG);
+    float v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int k = (int)g * 4 + j;
+        v[j] = k < T ? (float)coef[((size_t)pid * T + k) * 5 + o] : 0.0f;
+    }
+    cg[l] = make_float4(v[0], v[1], v[2], v[3]);
 }
 
 // One thread per class-grid node: its FP32 entrance ray (the rule in lt.h)
@@ -762,7 +927,9 @@ poly_cell_kernel(const __grid_constant__ PolyDev P, const float2* __restrict__ n
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
                     xi[k] = fmaf((float)((uint32_t)(cell[k] + b[k]) - pk[k] * (uint32_t)P.m[k]), P.two_over_m[k], -1.0f);
-                const Acc5 a = poly_eval<D>(P.c4 + (size_t)pid * poly_terms(D), P.cI + (size_t)pid * poly_terms(D), xi);
+                const float x1[1][4] = {{xi[0], xi[1], xi[2], xi[3]}};
+                Acc5 a;
+                poly_eval<D, 1>(poly_patch_groups(P, pid, D), x1, &a);
                 const uint32_t off = base + b[0] * nstride[0] + b[1] * nstride[1] + b[2] * nstride[2] + b[3] * nstride[3];
                 const float2 tr = nout[off];
                 worst = fmaxf(worst, hypotf(a.p.x - tr.x, a.p.y - tr.y));
@@ -849,13 +1016,35 @@ poly_fit_kernel(const __grid_constant__ LensDev L, int pi, int pj, const __grid_
     default: { constexpr int DD = 5; __VA_ARGS__; } break;                           \
     }
 
+PolyScratch poly_scratch_at(void* scratch, size_t n)
+{
+    char* p = static_cast<char*>(scratch) + query_scratch_bytes(n);
+    PolyScratch R;
+    R.rec = reinterpret_cast<float4*>(p);
+    R.tile_nv = reinterpret_cast<uint32_t*>(p + query_tiles(n) * kSortTileRays * 32);
+    return R;
+}
+
+lt_status launch_poly_fused(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n, int mode,
+                            cudaStream_t st)
+{
+    for (uint32_t a = 0; a < n; a += kFusedMaxRays) {
+        const uint32_t k = std::min(kFusedMaxRays, n - a);
+        const RaysInDev ia{in.x + a, in.y + a, in.dx + a, in.dy + a, in.dz + a, in.lam + a};
+        const RaysOutDev oa{out.x + a, out.y + a, out.dx + a, out.dy + a, out.dz + a, out.I + a, out.flags + a};
+        const lt_status s = launch_poly_query(map, ia, oa, k, mode, st);
+        if (s != LT_OK) return s;
+    }
+    return LT_OK;
+}
+
 lt_status launch_poly_query(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
-                            int mode, const TraceQueue* Qp, cudaStream_t st)
+                            int mode, cudaStream_t st)
 {
     const bool table = mode == LT_QUERY_TABLE;
     const unsigned blocks = (n + kPolyTile - 1) / kPolyTile;
     const int D = map->pdev.degree;
-    if (!Qp && n <= kFusedMaxRays) {
+    if (n <= kFusedMaxRays) {
         ProfScope prof("poly_query_fused_kernel", st);
         unsigned long long* w = prof.work();
         const bool ca = map->cauchy;
@@ -871,39 +1060,60 @@ lt_status launch_poly_query(const lt_map* map, const RaysInDev& in, const RaysOu
         LT_CUDA_TRY(cudaGetLastError());
         return LT_OK;
     }
+    cudaMemPool_t pool;
+    lt_status s = scratch_pool(&pool);
+    if (s != LT_OK) return s;
+    const size_t bytes = poly_scratch_bytes(n);
     char* buf = nullptr;
-    TraceQueue Q;
-    if (Qp) {
-        Q = *Qp;
-    } else {
-        cudaMemPool_t pool;
-        lt_status s = scratch_pool(&pool);
-        if (s != LT_OK) return s;
-        const size_t bytes = query_scratch_bytes(n);
-        if (cudaMallocFromPoolAsync((void**)&buf, bytes, pool, st) != cudaSuccess)
-            return fail(LT_ENOMEM, "lt_query: trace queue allocation of %zu bytes failed", bytes);
-        Q = trace_queue_at(buf, n);
-    }
-    lt_status s = LT_OK;
+    if (cudaMallocFromPoolAsync((void**)&buf, bytes, pool, st) != cudaSuccess)
+        return fail(LT_ENOMEM, "lt_query: scratch allocation of %zu bytes failed", bytes);
+    const TraceQueue Q = trace_queue_at(buf, n);
+    const PolyScratch R = poly_scratch_at(buf, n);
     do {
         cudaError_t e = cudaMemsetAsync(Q.count, 0, kQHeaderBytes, st);
         if (e != cudaSuccess) { s = cuda_fail(e, "lt_query: clearing the queue"); break; }
-        if (map->pdev.n_patches <= kSortMaxPatches) {
-            ProfScope prof("poly_query_kernel", st);
+        const size_t tab = (size_t)map->pdev.n_patches * poly_groups(D) * 5 * sizeof(float4);
+        if (map->pdev.n_patches <= kSortMaxPatches && tab <= kEvalMaxTableBytes) {
             const unsigned sb = (n + kSortTile - 1) / kSortTile;
+            {
+                ProfScope prof("poly_sort_kernel", st);
+                if (table) poly_sort_kernel<LT_QUERY_TABLE><<<sb, kSortThreads, 0, st>>>(map->pdev, in, n, Q, R);
+                else poly_sort_kernel<LT_QUERY_NO_MASK><<<sb, kSortThreads, 0, st>>>(map->pdev, in, n, Q, R);
+                e = cudaGetLastError();
+                if (e != cudaSuccess) { s = cuda_fail(e, "lt_query: launch"); break; }
+            }
+            ProfScope prof("poly_eval_kernel", st);
+            cudaLaunchConfig_t cfg = {};
+            cfg.blockDim = dim3(kEvalThreads);
+            cfg.dynamicSmemBytes = tab;
+            cfg.stream = st;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
             LT_POLY_DISPATCH(D, {
-                if (table) poly_query_sorted_kernel<DD, LT_QUERY_TABLE><<<sb, kSortThreads, 0, st>>>(map->pdev, in, out, n, Q);
-                else poly_query_sorted_kernel<DD, LT_QUERY_NO_MASK><<<sb, kSortThreads, 0, st>>>(map->pdev, in, out, n, Q);
+                const void* kf = (const void*)poly_eval_kernel<DD>;
+                e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab);
+                if (e == cudaSuccess) {
+                    int per_sm = 0, sms = 0, dev = 0;
+                    cudaGetDevice(&dev);
+                    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, kEvalThreads, tab);
+                    cfg.gridDim = dim3(std::max(1u, std::min(sb, (unsigned)(std::max(per_sm, 1) * sms))));
+                    e = cudaLaunchKernelEx(&cfg, poly_eval_kernel<DD>, map->pdev, out, n, R, sb);
+                }
             });
+            if (e != cudaSuccess) { s = cuda_fail(e, "lt_query: launch"); break; }
         } else {
             ProfScope prof("poly_query_kernel", st);
             LT_POLY_DISPATCH(D, {
                 if (table) poly_query_kernel<DD, LT_QUERY_TABLE><<<blocks, kPolyTile, 0, st>>>(map->pdev, in, out, n, Q);
                 else poly_query_kernel<DD, LT_QUERY_NO_MASK><<<blocks, kPolyTile, 0, st>>>(map->pdev, in, out, n, Q);
             });
+            e = cudaGetLastError();
+            if (e != cudaSuccess) { s = cuda_fail(e, "lt_query: launch"); break; }
         }
-        e = cudaGetLastError();
-        if (e != cudaSuccess) { s = cuda_fail(e, "lt_query: launch"); break; }
         s = launch_queue_trace(map, out, n, Q, st);
     } while (0);
     if (buf) cudaFreeAsync(buf, st);
@@ -1064,14 +1274,13 @@ lt_status lt_build_poly_map(const lt_lens* lens, const lt_poly_opts* o, lt_map**
 
     const uint32_t NW = (uint32_t)((NC + 15) / 16);
     const size_t nsamp = (size_t)NP * M;
-    if (cudaMalloc(&m->coef4, (size_t)NP * T * sizeof(float4)) != cudaSuccess ||
-        cudaMalloc(&m->coefI, (size_t)NP * T * sizeof(float)) != cudaSuccess ||
+    const int NG = (T + 3) / 4;
+    if (cudaMalloc(&m->coefg, (size_t)NP * NG * 5 * sizeof(float4)) != cudaSuccess ||
         cudaMalloc(&m->coef64, (size_t)NP * T * 5 * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&m->patch_ok, NP) != cudaSuccess || cudaMalloc(&m->node_valid, N) != cudaSuccess ||
         cudaMalloc(&m->cls, (size_t)NW * 4) != cudaSuccess)
         return bail(fail(LT_ENOMEM, "lt_build_poly_map: device allocation of the tables failed"));
-    P.c4 = m->coef4;
-    P.cI = m->coefI;
+    P.cg = m->coefg;
     P.patch_ok = m->patch_ok;
     P.cls = m->cls;
 
@@ -1128,8 +1337,8 @@ lt_status lt_build_poly_map(const lt_lens* lens, const lt_poly_opts* o, lt_map**
     poly_normal_kernel<<<dim3((unsigned)NP, (unsigned)((NE + 255) / 256)), 256, 0, st>>>(B, dA, dpairs, ys, vs, G, R);
     poly_solve_kernel<<<(unsigned)((NP + 63) / 64), 64, 0, st>>>(B, vs, G, R, m->coef64, m->patch_ok, (int)NP);
     poly_sample_residual_kernel<<<sb, 256, 0, st>>>(B, dA, ys, vs, m->coef64, m->patch_ok, sres, (uint32_t)nsamp);
-    const uint32_t nc = (uint32_t)(NP * T);
-    poly_pack_kernel<<<(nc + 255) / 256, 256, 0, st>>>(m->coef64, m->coef4, m->coefI, nc);
+    const uint32_t nc = (uint32_t)(NP * NG * 5);
+    poly_pack_kernel<<<(nc + 255) / 256, 256, 0, st>>>(m->coef64, m->coefg, T, NG, nc);
     POLY_TRY(cudaGetLastError());
 
     // 2. mask: class-grid nodes through the real lens, corner classes
@@ -1177,7 +1386,7 @@ lt_status lt_build_poly_map(const lt_lens* lens, const lt_poly_opts* o, lt_map**
     float fmx;
     std::memcpy(&fmx, &ha.max_res_bits, 4);
     m->stats.fit_residual_max_mm = fmx;
-    m->stats.table_bytes = (uint64_t)NP * T * 20 + NP + N + (uint64_t)NW * 4;
+    m->stats.table_bytes = (uint64_t)NP * NG * 80 + NP + N + (uint64_t)NW * 4;
     lt_poly_stats& ps_ = m->pstats;
     ps_.patches = (uint32_t)NP;
     ps_.terms = (uint32_t)T;

@@ -165,14 +165,15 @@ static size_t round16(size_t b) { return (b + 15) & ~(size_t)15; }
 // Device bytes a request holds while in flight: host staging, the ray
 // queue of the tracer's second kernel (kQueueBytesPerRay per ray of a wave
 // of at most 2^24 rays) for a trace launched on its own, and the trace
-// queue of a map query.
+// queue of a map query (with a polynomial-patch map's sorted records).
 static size_t request_bytes(const lt_request& r, size_t fuse_max_rays)
 {
     size_t b = 0;
     if (r.flags & LT_REQ_HOST_BUFFERS) b += 12 * round16(r.n * 4) + round16(r.n);
     if (r.kind == LT_REQ_TRACE && (r.n > fuse_max_rays || (r.flags & LT_REQ_HOST_BUFFERS)))
         b += (std::min(r.n, (size_t)1 << 24) + 64) * kQueueBytesPerRay + 256;
-    if (r.kind == LT_REQ_QUERY) b += query_scratch_bytes(r.n);
+    if (r.kind == LT_REQ_QUERY)
+        b += r.map && r.map->kind == LT_MAP_KIND_POLY ? poly_scratch_bytes(r.n) : query_scratch_bytes(r.n);
     return b;
 }
 

@@ -56,28 +56,48 @@ def test_pos_err_uses_rays_valid_on_both_sides_and_skips_grazing():
 
 def test_oracle_threads_split_covers_the_batch():
     # the batch goes to k threads in k contiguous parts that tile it exactly,
-    # and the parts' answers equal one call's
+    # each with its rays' classes, and the parts' answers equal one call's
+    from oracle import poly
     p = w.singlet_lens()
-    ol = oracle.Lens(p)
-    lat = oracle.Lattice([4, 4, 4, 4, 3], *bench.map_box(12.0))
-    om = oracle.TableMap(ol, (0, 0), lat, w.singlet_rays(2000))
+    om = poly.PolyMap(p, (0, 0), 12.0, bench.SMAX, 380.0, 780.0, 3, (2, 2, 1, 1), (2, 2, 2, 1), 5, tol=1e-4)
     rays = w.singlet_rays(1001)
-    whole, wf = om.query(rays)
+    inside, cells = om.locate(rays)
+    classes = np.full(len(rays), 2, np.uint8)
+    classes[inside] = om.cell_class[tuple(cells[inside].T)]
+    whole, wf = om.query(rays, classes=classes)
     parts = []
 
     class Spy:
-        def query(self, r):
-            parts.append((r.arrays()[0].copy(), om.query(r)))
+        def query(self, r, classes=None):
+            parts.append((r.arrays()[0].copy(), classes.copy(), om.query(r, classes=classes)))
 
-    dt = bench.oracle_query_threads(Spy(), rays, 3)
+    dt = bench.oracle_query_threads(Spy(), rays, classes, 3)
     assert dt > 0 and len(parts) == 3
     x = rays.arrays()[0]
-    start = {int(np.flatnonzero(x == px[0])[0]): (px, res) for px, res in parts}
-    assert sorted(len(px) for px, _ in parts) == [333, 334, 334]
+    start = {int(np.flatnonzero(x == px[0])[0]): (px, c, res) for px, c, res in parts}
+    assert sorted(len(px) for px, _, _ in parts) == [333, 334, 334]
     pos = 0
     for s0 in sorted(start):
-        px, (o, f) = start[s0]
+        px, c, (o, f) = start[s0]
         assert s0 == pos and np.array_equal(px, x[pos:pos + len(px)])
+        assert np.array_equal(c, classes[pos:pos + len(px)])
         assert np.array_equal(o, whole[pos:pos + len(px)]) and np.array_equal(f, wf[pos:pos + len(px)])
         pos += len(px)
     assert pos == len(rays)
+
+
+def test_map_error_statistics():
+    class F:
+        FLAG_VALID, FLAG_TRACED, FLAG_NEAR_EDGE = 1, 0x10, 2
+    q = np.zeros((5, 6), np.float32)
+    t = np.zeros((5, 6), np.float32)
+    q[0, :2] = [3e-5, -4e-5]
+    q[1, 2] = 2e-7
+    q[2, 5] = 1e-6
+    qf = np.array([1, 1, 1, 1 | 0x10, 0], np.uint8)    # ray 3 traced, ray 4 INVALID
+    tf = np.array([1, 1, 1, 1, 1 | 2], np.uint8)        # ray 4 valid, near an edge
+    e = bench.map_error(q, qf, t, tf, F)
+    assert e["rays_interpolated"] == 3 and e["validity_mismatches"] == 1
+    assert e["validity_mismatches_near_edge"] == 1
+    assert e["pos_max_mm"] == pytest.approx(4e-5) and e["pos_euclid_max_mm"] == pytest.approx(5e-5, rel=1e-6)
+    assert e["dir_max"] == pytest.approx(2e-7) and e["I_max"] == pytest.approx(1e-6)

@@ -265,3 +265,16 @@ def test_fresh_classes_match_the_table(singlet_map):
     cells += [tuple(c) for c in np.argwhere(pm.cell_class == poly.CELL_BOUNDARY)[:20]]
     for cell in cells:
         assert pm.classify_fresh(cell)[0] == pm.cell_class[cell], cell
+
+
+def test_batched_classes_match_fresh(singlet_map):
+    """classify_cells (many cells in one pass) agrees with classify_fresh cell by cell."""
+    pm = singlet_map
+    rng = np.random.default_rng(9)
+    cells = np.array([rng.integers(0, pm.grid.C) for _ in range(120)])
+    cells = np.concatenate([cells, np.argwhere(pm.cell_class == poly.CELL_BOUNDARY)[:30]])
+    cls, res = pm.classify_cells(cells)
+    for j, c in enumerate(cells):
+        want, wres = pm.classify_fresh(tuple(c))
+        assert cls[j] == want, (c, cls[j], want)
+        assert abs(res[j] - wres) <= 1e-12 * max(1.0, wres)
