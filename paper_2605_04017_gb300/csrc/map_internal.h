@@ -51,19 +51,23 @@ constexpr size_t query_scratch_bytes(size_t n) { return kQHeaderBytes + 7 * 4 * 
 // The polynomial-patch map's large-batch query also keeps, per tile of
 // kSortTileRays rays, a record of each ray the polynomial answers (its
 // patch-local coordinates, rotation, mirror, patch and index in the tile:
-// 32 bytes) in the tile's region, sorted by patch, and the tile's count.
+// 32 bytes) in the tile's region, sorted by patch with every patch's run
+// padded to an even length (so that record pairs share a patch), and the
+// tile's padded count.  A tile's region holds kSortTileRays + P records for
+// a map of P patches.
 constexpr size_t kSortTileRays = 1024;
 constexpr size_t query_tiles(size_t n) { return (n + kSortTileRays - 1) / kSortTileRays; }
-constexpr size_t poly_scratch_bytes(size_t n)
+constexpr size_t poly_scratch_bytes(size_t n, size_t patches)
 {
-    return query_scratch_bytes(n) + query_tiles(n) * (kSortTileRays * 32 + 4) + 256;
+    return query_scratch_bytes(n) + query_tiles(n) * ((kSortTileRays + patches) * 32 + 4) + 256;
 }
 struct PolyScratch {
-    float4* rec;          // query_tiles(n) x kSortTileRays x 2 float4
+    float4* rec;          // query_tiles(n) x (kSortTileRays + patches) x 2 float4
     uint32_t* tile_nv;    // query_tiles(n)
+    uint32_t stride;      // records per tile region
 };
-// the records and counts after the queue of n rays in `scratch` (poly_scratch_bytes(n))
-PolyScratch poly_scratch_at(void* scratch, size_t n);
+// the records and counts after the queue of n rays in `scratch` (poly_scratch_bytes(n, patches))
+PolyScratch poly_scratch_at(void* scratch, size_t n, size_t patches);
 
 // the queue laid out in `scratch` (256-byte aligned, query_scratch_bytes(n))
 TraceQueue trace_queue_at(void* scratch, size_t n);

@@ -146,13 +146,11 @@ __device__ __forceinline__ void poly_eval(const float4* __restrict__ G, const fl
     for (int r = 0; r < NR; ++r) res[r] = A0[r];
 }
 
-// The same evaluation from a table in shared memory (plain loads), each
-// point with its own patch's coefficients (the same addresses when the
-// points share a patch).
+// The same evaluation from a table in shared memory (plain loads).
 template <int D, int NR>
-__device__ __forceinline__ void poly_eval_tab(const float4* const G[NR], const float (*xi)[4], Acc5* res)
+__device__ __forceinline__ void poly_eval_tab(const float4* G, const float (*xi)[4], Acc5* res)
 {
-    float4 cur[NR][5];
+    float4 cur[5];
     int k = 0;
     Acc5 A0[NR];
 #pragma unroll
@@ -168,19 +166,17 @@ __device__ __forceinline__ void poly_eval_tab(const float4* const G[NR], const f
                 for (int e = D - a - b - c; e >= 0; --e) {
                     if (k % 4 == 0) {
 #pragma unroll
-                        for (int r = 0; r < NR; ++r)
-#pragma unroll
-                            for (int o = 0; o < 5; ++o) cur[r][o] = G[r][(k / 4) * 5 + o];
+                        for (int o = 0; o < 5; ++o) cur[o] = G[(k / 4) * 5 + o];
                     }
+                    const float4 v = make_float4(f4c(cur[0], k % 4), f4c(cur[1], k % 4), f4c(cur[2], k % 4),
+                                                 f4c(cur[3], k % 4));
+                    const float vi = f4c(cur[4], k % 4);
+                    ++k;
 #pragma unroll
                     for (int r = 0; r < NR; ++r) {
-                        const float4 v = make_float4(f4c(cur[r][0], k % 4), f4c(cur[r][1], k % 4),
-                                                     f4c(cur[r][2], k % 4), f4c(cur[r][3], k % 4));
-                        const float vi = f4c(cur[r][4], k % 4);
                         if (e == D - a - b - c) acc_load(A3[r], v, vi);
                         else acc_step(A3[r], xi[r][3], v, vi);
                     }
-                    ++k;
                 }
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
@@ -207,13 +203,14 @@ __device__ __forceinline__ void poly_eval_tab(const float4* const G[NR], const f
 // The FP32 rule for the reduced coordinates (documented in lt.h): three
 // correctly rounded divisions (1 / d_z, 1 / r, 1000 / lambda), every other
 // operation a correctly rounded product, sum or square root; false for
-// unusable input (non-finite, d_z <= 0, lambda <= 0).
+// d_z <= 0, d_z infinite or lambda <= 0 (a NaN or infinity elsewhere makes
+// the ray fall outside the box).
 __device__ __forceinline__ bool poly_reduce(float x, float y, float dx, float dy, float dz, float lam,
                                             float u[4], float& c, float& s, float& m)
 {
-    const bool ok = isfinite(x) & isfinite(y) & isfinite(dx) & isfinite(dy) & isfinite(dz) &
-                    isfinite(lam) & (dz > 0.0f) & (lam > 0.0f);
-    if (!ok) return false;
+    // d_z must be positive and finite and lambda positive; any other NaN or
+    // infinity reaches a reduced coordinate and fails the box test
+    if (!((dz > 0.0f) & (dz < INFINITY) & (lam > 0.0f))) return false;
     const float idz = __frcp_rn(dz);
     const float sx = __fmul_rn(dx, idz), sy = __fmul_rn(dy, idz);
     const float r = __fsqrt_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)));
@@ -256,25 +253,43 @@ __device__ __forceinline__ uint32_t poly_patch_of(const PolyDev& P, int k, uint3
     return P.m[k] == 1 ? cell : __umulhi(cell, P.mdiv[k]);
 }
 
-// Class-grid cell, patch and patch-local xi of reduced coordinates u; false
+// Class-grid coordinates g, cell and patch of reduced coordinates u; false
 // outside the box.
-__device__ __forceinline__ bool poly_locate(const PolyDev& P, const float u[4], uint32_t& cid, uint32_t& pid,
-                                            float xi[4])
+__device__ __forceinline__ bool poly_cell(const PolyDev& P, const float u[4], float g[4], uint32_t& cid,
+                                          uint32_t& pid)
 {
     bool inside = true;
     cid = 0;
     pid = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const float g = __fmul_rn(__fsub_rn(u[k], P.lo[k]), P.inv[k]);
-        inside &= (g >= 0.0f) & (g <= P.cmax[k]);
-        int cell = inside ? (int)floorf(g) : 0;
+        g[k] = __fmul_rn(__fsub_rn(u[k], P.lo[k]), P.inv[k]);
+        inside &= (g[k] >= 0.0f) & (g[k] <= P.cmax[k]);
+        int cell = inside ? (int)floorf(g[k]) : 0;
         cell = min(max(cell, 0), P.C[k] - 1);
-        const uint32_t pk = poly_patch_of(P, k, (uint32_t)cell);
         cid += (uint32_t)cell * P.cstride[k];
-        pid += pk * P.pstride[k];
-        xi[k] = fmaf(g - (float)(pk * (uint32_t)P.m[k]), P.two_over_m[k], -1.0f);
+        pid += poly_patch_of(P, k, (uint32_t)cell) * P.pstride[k];
     }
+    return inside;
+}
+
+// Patch-local xi of class-grid coordinates g in patch pid.
+__device__ __forceinline__ void poly_xi(const PolyDev& P, uint32_t pid, const float g[4], float xi[4])
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t pk = (pid / P.pstride[k]) % (uint32_t)P.P[k];
+        xi[k] = fmaf(g[k] - (float)(pk * (uint32_t)P.m[k]), P.two_over_m[k], -1.0f);
+    }
+}
+
+// Cell, patch and patch-local xi; false outside the box.
+__device__ __forceinline__ bool poly_locate(const PolyDev& P, const float u[4], uint32_t& cid, uint32_t& pid,
+                                            float xi[4])
+{
+    float g[4];
+    const bool inside = poly_cell(P, u, g, cid, pid);
+    poly_xi(P, pid, g, xi);
     return inside;
 }
 
@@ -413,10 +428,11 @@ poly_query_kernel(const __grid_constant__ PolyDev P, RaysInDev in, RaysOutDev ou
 //     a shared-memory histogram over patches (the atomic's return value is
 //     the ray's rank within its patch);
 //  B. one warp turns the histogram into offsets (exclusive scan);
-//  C. every VALID ray writes its record -- patch-local xi, rotation (c, s),
-//     a word holding its mirror and patch, its index in the tile: 32 bytes,
-//     one sector -- to its sorted slot of the tile's region, and the count
-//     goes to the tile's counter.
+//  C. every VALID ray writes its record -- class-grid coordinates, rotation
+//     (c, s), a word holding its mirror and patch, its index in the tile: 32
+//     bytes, one sector -- to its sorted slot of the tile's region, every
+//     patch's run padded to even length, and the count goes to the tile's
+//     counter.
 // Round j of tile b appends to queue segment (4 b + j) % kQSegs: the same
 // segment a 256-ray block of the same rays would use, so the queue's
 // capacity rule (query_segcap) holds.
@@ -433,6 +449,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortRounds = 4;
 constexpr int kSortTile = kSortThreads * kSortRounds;
 constexpr int kSortMaxPatches = 1024;
+constexpr uint32_t kNoRay = 0xffffffffu;   // the index of a padding record
 static_assert(kSortThreads == kQTile, "a sort round must be one queue block");
 static_assert(kSortTile == (int)kSortTileRays, "the sorted-index region is laid out in sort tiles");
 constexpr int kEvalThreads = 256;
@@ -444,7 +461,7 @@ __global__ void __launch_bounds__(kSortThreads)
 poly_sort_kernel(const __grid_constant__ PolyDev P, RaysInDev in, uint32_t n, TraceQueue Q, PolyScratch R)
 {
     __shared__ uint32_t hist[kSortMaxPatches];
-    __shared__ float4 recA[kSortTile];      // xi
+    __shared__ float4 recA[kSortTile];      // class-grid coordinates g
     __shared__ float4 recB[kSortTile];      // c, s, (mirror << 31 | patch), index in the tile
     __shared__ uint32_t nvalid;
     const unsigned full = 0xffffffffu;
@@ -477,11 +494,11 @@ poly_sort_kernel(const __grid_constant__ PolyDev P, RaysInDev in, uint32_t n, Tr
         cid[j] = pid[j] = 0;
         const uint32_t l = (uint32_t)(j * kSortThreads + t);
         if (r0 + l < n) {
-            float u[4], xi[4], cs, sn, m;
+            float u[4], g[4], cs, sn, m;
             stat[j] = 1;
-            if (poly_reduce(x[j], y[j], dx[j], dy[j], dz[j], lam[j], u, cs, sn, m) && poly_locate(P, u, cid[j], pid[j], xi)) {
+            if (poly_reduce(x[j], y[j], dx[j], dy[j], dz[j], lam[j], u, cs, sn, m) && poly_cell(P, u, g, cid[j], pid[j])) {
                 stat[j] = 2;
-                recA[l] = make_float4(xi[0], xi[1], xi[2], xi[3]);
+                recA[l] = make_float4(g[0], g[1], g[2], g[3]);
                 recB[l] = make_float4(cs, sn, __uint_as_float((m < 0.0f ? 0x80000000u : 0u) | pid[j]),
                                       __uint_as_float(l));
             }
@@ -544,7 +561,7 @@ poly_sort_kernel(const __grid_constant__ PolyDev P, RaysInDev in, uint32_t n, Tr
         const int per = (NP + 31) / 32;
         const int b0 = min(NP, lane * per), b1 = min(NP, b0 + per);
         uint32_t sum = 0;
-        for (int b = b0; b < b1; ++b) sum += hist[b];
+        for (int b = b0; b < b1; ++b) sum += (hist[b] + 1u) & ~1u;
         uint32_t incl = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -552,16 +569,22 @@ poly_sort_kernel(const __grid_constant__ PolyDev P, RaysInDev in, uint32_t n, Tr
             if (lane >= o) incl += v;
         }
         uint32_t run = incl - sum;
+        float4* rec = R.rec + (size_t)blockIdx.x * R.stride * 2;
         for (int b = b0; b < b1; ++b) {
             const uint32_t c = hist[b];
             hist[b] = run;
-            run += c;
+            // an odd run ends in a padding record (index kNoRay: evaluated, not stored)
+            if (c & 1u) {
+                rec[(run + c) * 2] = make_float4(0.f, 0.f, 0.f, 0.f);
+                rec[(run + c) * 2 + 1] = make_float4(0.f, 0.f, __uint_as_float((uint32_t)b), __uint_as_float(kNoRay));
+            }
+            run += (c + 1u) & ~1u;
         }
-        if (lane == 31) nvalid = incl;
+        if (lane == 31) nvalid = run;
     }
     __syncthreads();
     // C
-    float4* rec = R.rec + (size_t)blockIdx.x * kSortTile * 2;
+    float4* rec = R.rec + (size_t)blockIdx.x * R.stride * 2;
     if (t == 0) R.tile_nv[blockIdx.x] = nvalid;
 #pragma unroll
     for (int j = 0; j < kSortRounds; ++j)
@@ -602,20 +625,31 @@ poly_eval_kernel(const __grid_constant__ PolyDev P, RaysOutDev out, uint32_t n, 
         }
         __syncthreads();
         const uint32_t nv = R.tile_nv[tile];
-        const float4* rec = R.rec + (size_t)tile * kSortTile * 2;
+        const float4* rec = R.rec + (size_t)tile * R.stride * 2;
 #pragma unroll 1
-        for (uint32_t sl = (uint32_t)t; sl < nv; sl += kEvalThreads) {
-            const float4 a = rec[sl * 2], b = rec[sl * 2 + 1];
-            const uint32_t w = __float_as_uint(b.z), l = __float_as_uint(b.w);
-            const float xi[1][4] = {{a.x, a.y, a.z, a.w}};
-            const float4* G[1] = {smc + (size_t)(w & 0x7fffffffu) * poly_groups(D) * 5};
-            Acc5 acc;
-            poly_eval_tab<D, 1>(G, xi, &acc);
+        for (uint32_t s0 = 2u * (uint32_t)t; s0 < nv; s0 += 2u * kEvalThreads) {
+            const float4 a0 = rec[s0 * 2], b0 = rec[s0 * 2 + 1], a1 = rec[s0 * 2 + 2], b1 = rec[s0 * 2 + 3];
+            const uint32_t w0 = __float_as_uint(b0.z), w1 = __float_as_uint(b1.z);
+            const uint32_t pid = w0 & 0x7fffffffu;
+            const float g0[4] = {a0.x, a0.y, a0.z, a0.w}, g1[4] = {a1.x, a1.y, a1.z, a1.w};
+            float xi[2][4];
+            poly_xi(P, pid, g0, xi[0]);
+            poly_xi(P, pid, g1, xi[1]);
+            Acc5 acc[2];
+            poly_eval_tab<D, 2>(smc + (size_t)pid * poly_groups(D) * 5, xi, acc);
             float o[6];
-            poly_unreduce(acc, b.x, b.y, (w & 0x80000000u) ? -1.0f : 1.0f, o);
+            uint32_t l = __float_as_uint(b0.w);
+            poly_unreduce(acc[0], b0.x, b0.y, (w0 & 0x80000000u) ? -1.0f : 1.0f, o);
 #pragma unroll
             for (int q = 0; q < 6; ++q) ob[q][l] = o[q];
             of[l] = LT_FLAG_VALID;
+            l = __float_as_uint(b1.w);
+            if (l != kNoRay) {
+                poly_unreduce(acc[1], b1.x, b1.y, (w1 & 0x80000000u) ? -1.0f : 1.0f, o);
+#pragma unroll
+                for (int q = 0; q < 6; ++q) ob[q][l] = o[q];
+                of[l] = LT_FLAG_VALID;
+            }
         }
         __syncthreads();
         for (uint32_t l = (uint32_t)t; l < cnt; l += kEvalThreads) {
@@ -1016,12 +1050,13 @@ poly_fit_kernel(const __grid_constant__ LensDev L, int pi, int pj, const __grid_
     default: { constexpr int DD = 5; __VA_ARGS__; } break;                           \
     }
 
-PolyScratch poly_scratch_at(void* scratch, size_t n)
+PolyScratch poly_scratch_at(void* scratch, size_t n, size_t patches)
 {
     char* p = static_cast<char*>(scratch) + query_scratch_bytes(n);
     PolyScratch R;
+    R.stride = (uint32_t)(kSortTileRays + patches);
     R.rec = reinterpret_cast<float4*>(p);
-    R.tile_nv = reinterpret_cast<uint32_t*>(p + query_tiles(n) * kSortTileRays * 32);
+    R.tile_nv = reinterpret_cast<uint32_t*>(p + query_tiles(n) * R.stride * 32);
     return R;
 }
 
@@ -1063,12 +1098,12 @@ lt_status launch_poly_query(const lt_map* map, const RaysInDev& in, const RaysOu
     cudaMemPool_t pool;
     lt_status s = scratch_pool(&pool);
     if (s != LT_OK) return s;
-    const size_t bytes = poly_scratch_bytes(n);
+    const size_t bytes = poly_scratch_bytes(n, map->pdev.n_patches);
     char* buf = nullptr;
     if (cudaMallocFromPoolAsync((void**)&buf, bytes, pool, st) != cudaSuccess)
         return fail(LT_ENOMEM, "lt_query: scratch allocation of %zu bytes failed", bytes);
     const TraceQueue Q = trace_queue_at(buf, n);
-    const PolyScratch R = poly_scratch_at(buf, n);
+    const PolyScratch R = poly_scratch_at(buf, n, map->pdev.n_patches);
     do {
         cudaError_t e = cudaMemsetAsync(Q.count, 0, kQHeaderBytes, st);
         if (e != cudaSuccess) { s = cuda_fail(e, "lt_query: clearing the queue"); break; }

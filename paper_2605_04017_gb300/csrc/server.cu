@@ -173,7 +173,8 @@ static size_t request_bytes(const lt_request& r, size_t fuse_max_rays)
     if (r.kind == LT_REQ_TRACE && (r.n > fuse_max_rays || (r.flags & LT_REQ_HOST_BUFFERS)))
         b += (std::min(r.n, (size_t)1 << 24) + 64) * kQueueBytesPerRay + 256;
     if (r.kind == LT_REQ_QUERY)
-        b += r.map && r.map->kind == LT_MAP_KIND_POLY ? poly_scratch_bytes(r.n) : query_scratch_bytes(r.n);
+        b += r.map && r.map->kind == LT_MAP_KIND_POLY ? poly_scratch_bytes(r.n, r.map->pstats.patches)
+                                                      : query_scratch_bytes(r.n);
     return b;
 }
 
