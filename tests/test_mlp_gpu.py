@@ -3,13 +3,11 @@ training and inference) against the oracle's FP64 networks (oracle/mlp.py).
 
 Tolerances.  Gradients: the GPU computes forward/backward in FP32 with FP32
 per-block sums of 128 rays and an FP64 sum over blocks; relative to the
-largest gradient entry that is ~1e-6, the test allows 1e-4.  FP32 query: the
-GPU evaluates the same rational tanh as the oracle's reference forward; what
-remains is FP32 rounding of seven 32-term dot products, a few 1e-6 relative
-in standardised units, so outputs are held to 3e-5 x the target standard
-deviation plus two FP32 ulps of the output itself, and the classifier's
-decision is compared where |logit| > 1e-3.
-BF16 / FP16 queries are reported against the exact-tanh FP64 oracle."""
+largest gradient entry that is ~1e-6, the test allows 1e-4.  Queries are
+compared ray by ray (tests/mlp_check.py): FP32 to 3e-5 of each output's
+standard deviation plus two FP32 ulps, BF16 / FP16 to twice a first-order
+bound of the half-precision rounding of the six layers, computed per ray
+from the oracle's activations."""
 import math
 
 import numpy as np
@@ -20,6 +18,8 @@ torch = pytest.importorskip("torch")
 import oracle
 from oracle import mlp
 from paper_2605_04017_gb300 import batch, lt, workloads as w
+
+from mlp_check import check_query
 
 pytestmark = pytest.mark.gpu
 
@@ -129,26 +129,15 @@ def test_query_f32_matches_oracle_forward(singlet, tstats):
     m = lt.Mlp.create(lens, frame(), reg_f, cls_f, t_mean, t_std)
     rays = w.singlet_rays(20000)
     out, flags = run_query(m, rays, lt.MLP_F32)
-    oo, ov, logit = mlp.query_with(as64(cls_f, "cls"), as64(reg_f, "reg"), rays, RHO, WMAX,
-                                   t_mean, t_std, mlp.tanh_lambert)
-    clear = np.abs(logit) > 1e-3
-    gv = (flags & 1) != 0
-    assert np.array_equal(gv[clear], ov[clear])
-    both = gv & ov
-    # network error in standardised units, scaled by the std, plus two FP32
-    # ulps of the de-standardised output (I has mean 0.92 and std 1.6e-3)
-    err = np.abs(out[both].astype(np.float64) - oo[both])
-    tol = 3e-5 * np.asarray(t_std) + 2 * 2.0 ** -23 * np.abs(oo[both])
-    for q in (0, 1, 5):
-        assert np.all(err[:, q] <= tol[:, q]), q
-    assert err[:, 2:5].max() < 3e-5
-    assert np.all(out[~gv] == 0)
+    rep = check_query(out, flags, as64(reg_f, "reg"), as64(cls_f, "cls"), rays, RHO, WMAX, t_mean, t_std,
+                      lt.MLP_F32, "singlet, random networks")
+    assert rep["decided"] > 0.99
 
 
-@pytest.mark.parametrize("precision,bound", [(lt.MLP_BF16, 3e-2), (lt.MLP_F16, 4e-3)])
-def test_query_half_precision_error_report(singlet, tstats, precision, bound):
-    """Per-output error of the tensor-core queries against the exact-tanh FP64
-    oracle, in units of each output's standard deviation."""
+@pytest.mark.parametrize("precision", [lt.MLP_BF16, lt.MLP_F16])
+def test_query_half_precision_matches_oracle_forward(singlet, tstats, precision):
+    """The tensor-core queries of random networks, ray by ray, within the
+    half-precision rounding bound."""
     p, lens, ol = singlet
     reg, cls = init(4)
     reg_f, cls_f = lt.flat_params(reg), lt.flat_params(cls)
@@ -156,19 +145,10 @@ def test_query_half_precision_error_report(singlet, tstats, precision, bound):
     m = lt.Mlp.create(lens, frame(), reg_f, cls_f, t_mean, t_std)
     rays = w.singlet_rays(20000)
     out, flags = run_query(m, rays, precision)
-    oo, ov, logit = mlp.query(as64(cls_f, "cls"), as64(reg_f, "reg"), rays, RHO, WMAX, t_mean, t_std)
-    gv = (flags & 1) != 0
-    clear = np.abs(logit) > 0.05
-    agree = (gv == ov)[clear].mean()
-    both = gv & ov
-    err = np.abs(out[both].astype(np.float64) - oo[both])
-    scaled = err / np.array([t_std[0], t_std[1], 1, 1, 1, t_std[5]])
-    rep = {"decision_agreement": float(agree), "pos_rms_std": float(np.sqrt((scaled[:, :2] ** 2).mean())),
-           "pos_max_std": float(scaled[:, :2].max()), "dir_max": float(scaled[:, 2:5].max()),
-           "I_max_std": float(scaled[:, 5].max())}
+    rep = check_query(out, flags, as64(reg_f, "reg"), as64(cls_f, "cls"), rays, RHO, WMAX, t_mean, t_std,
+                      precision, "singlet, random networks")
     print("precision", precision, rep)
-    assert agree > 0.99
-    assert rep["pos_rms_std"] < bound and rep["dir_max"] < 10 * bound
+    assert rep["decided"] > 0.75 and rep["compared"] > 1000
 
 
 def test_bad_precision_is_rejected(singlet, tstats):
@@ -260,9 +240,8 @@ def precision_batch():
 def test_full_size_precision_queries_sampled(singlet, trained, precision_batch, precision):
     """The precision workload as the bench runs it: the trained networks
     answer all 16,777,216 rays in one launch; 4,098 rays spread over the batch
-    (the first and last included) are checked against the oracle's forward,
-    FP32 within the tolerance of the small FP32 test, BF16 / FP16 within the
-    bounds of the half-precision error report."""
+    (the first and last included) are checked against the oracle's forward
+    ray by ray, with the tolerances of the small tests."""
     p, lens, ol = singlet
     m, _, _ = trained
     rays = precision_batch
@@ -276,26 +255,6 @@ def test_full_size_precision_queries_sampled(singlet, trained, precision_batch, 
     st = m.stats()
     t_mean, t_std = np.array(st["t_mean"]), np.array(st["t_std"])
     reg_f, cls_f = m.params()
-    gv = (flags & 1) != 0
-    if precision == lt.MLP_F32:
-        oo, ov, logit = mlp.query_with(as64(cls_f, "cls"), as64(reg_f, "reg"), sample, RHO, WMAX,
-                                       t_mean, t_std, mlp.tanh_lambert)
-        clear = np.abs(logit) > 1e-3
-        assert np.array_equal(gv[clear], ov[clear])
-        both = gv & ov
-        err = np.abs(out[both].astype(np.float64) - oo[both])
-        tol = 3e-5 * t_std + 2 * 2.0 ** -23 * np.abs(oo[both])
-        for q in (0, 1, 5):
-            assert np.all(err[:, q] <= tol[:, q]), q
-        assert err[:, 2:5].max() < 3e-5
-    else:
-        bound = 3e-2 if precision == lt.MLP_BF16 else 4e-3
-        oo, ov, logit = mlp.query(as64(cls_f, "cls"), as64(reg_f, "reg"), sample, RHO, WMAX, t_mean, t_std)
-        clear = np.abs(logit) > 0.05
-        assert (gv == ov)[clear].mean() > 0.99
-        both = gv & ov
-        scaled = np.abs(out[both].astype(np.float64) - oo[both]) / np.array([t_std[0], t_std[1], 1, 1, 1, t_std[5]])
-        pos_rms = float(np.sqrt((scaled[:, :2] ** 2).mean()))
-        print("full-size precision", precision, "pos_rms_std", pos_rms, "dir_max", float(scaled[:, 2:5].max()))
-        assert pos_rms < bound and scaled[:, 2:5].max() < 10 * bound
-    assert np.all(out[~gv] == 0)
+    rep = check_query(out, flags, as64(reg_f, "reg"), as64(cls_f, "cls"), sample, RHO, WMAX, t_mean, t_std,
+                      precision, "singlet, trained, 16.7 M rays")
+    print("full-size precision", precision, rep)
