@@ -552,6 +552,15 @@ typedef struct {
     int32_t ft_steps, ft_batch;     /* optional regressor fine-tune phase (0 steps: none) */
     double ft_lr;
     uint64_t seed;                  /* batch draws: SplitMix64(seed + step * batch + i) mod n */
+    /* 0: every fit ray is a uniform draw of the input box.  Otherwise the
+     * first n_fit_uniform rays are uniform draws and the rest are samples of
+     * the path's valid region (lt_mcmc_sample), whose extra valid rays raise
+     * the odds of "valid" in the classifier's training set by
+     * k = 1 + (valid rays after the prefix) / (valid rays in the prefix); the
+     * trained classifier's output bias is lowered by ln k so that its logit
+     * answers for uniformly drawn rays (the prior-shift correction of a
+     * calibrated classifier).  The regressor learns from every valid ray. */
+    uint64_t n_fit_uniform;
 } lt_mlp_opts;
 
 typedef struct {
@@ -560,6 +569,8 @@ typedef struct {
     double t_mean[6], t_std[6];     /* target standardisation */
     double train_ms;
     uint64_t tc_wait_timeouts;      /* tensor-core query waits that ran out (0 when healthy) */
+    uint64_t n_valid_uniform;       /* valid rays among the first n_fit_uniform (all fit rays when 0) */
+    double cls_prior_shift;         /* ln k subtracted from the classifier's output bias (0: none) */
 } lt_mlp_stats;
 
 enum {

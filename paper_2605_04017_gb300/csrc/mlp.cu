@@ -118,13 +118,16 @@ __device__ __forceinline__ float tanh_rational(float x)
 // ------------------------------------------------------------------ training data
 
 // Trace each fit ray along the path; write network inputs X (n x 4), the
-// reduced-frame targets T (n x 6, valid rays only) and labels; append valid
-// rays to a list.
+// reduced-frame targets T (n x 6, valid rays only) and labels; count each
+// block's valid rays (bcount) and those among the first n_uniform
+// (bcount_u).  The valid list is built from the labels in ray order by
+// mlp_scan_kernel and mlp_compact_kernel, so that training is a pure
+// function of its inputs.
 template <bool CAUCHY>
 __global__ void __launch_bounds__(256)
 mlp_prep_kernel(const __grid_constant__ LensDev L, int pi, int pj, RaysInDev fit, uint32_t n,
-                MlpFrame F, float* __restrict__ X, float* __restrict__ T,
-                float* __restrict__ label, uint32_t* __restrict__ vlist, uint32_t* vcount)
+                uint32_t n_uniform, MlpFrame F, float* __restrict__ X, float* __restrict__ T,
+                float* __restrict__ label, uint32_t* __restrict__ bcount, uint32_t* __restrict__ bcount_u)
 {
     const uint32_t r = blockIdx.x * 256u + threadIdx.x;
     bool valid = false;
@@ -156,21 +159,89 @@ mlp_prep_kernel(const __grid_constant__ LensDev L, int pi, int pj, RaysInDev fit
         tp[1] = make_float2(t[2], t[3]);
         tp[2] = make_float2(t[4], t[5]);
     }
-    const unsigned full = 0xffffffffu;
-    const unsigned m = __ballot_sync(full, valid);
-    if (m) {
-        const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(vcount, (uint32_t)__popc(m));
-        base = __shfl_sync(full, base, leader);
-        if (valid) vlist[base + __popc(m & ((1u << lane) - 1u))] = r;
+    const int c = __syncthreads_count(valid);
+    const int cu = __syncthreads_count(valid && r < n_uniform);
+    if (threadIdx.x == 0) {
+        bcount[blockIdx.x] = (uint32_t)c;
+        bcount_u[blockIdx.x] = (uint32_t)cu;
     }
 }
 
-// FP64 sums of the targets and their squares over the valid list
+// One block of 1024 threads: exclusive prefix sums of the per-block counts
+// (boff) in chunks of 1024; vcount[0] = valid rays, vcount[1] = valid rays
+// among the uniform prefix.
+__global__ void __launch_bounds__(1024)
+mlp_scan_kernel(const uint32_t* __restrict__ bcount, const uint32_t* __restrict__ bcount_u, uint32_t nb,
+                uint32_t* __restrict__ boff, uint32_t* __restrict__ vcount)
+{
+    __shared__ uint32_t wsum[32];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t carry = 0, su = 0;
+    for (uint32_t base = 0; base < nb; base += 1024u) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t v = i < nb ? bcount[i] : 0u;
+        if (i < nb) su += bcount_u[i];
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(full, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(full, w, o);
+                if (lane >= o) w += y;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        if (i < nb) boff[i] = carry + (warp > 0 ? wsum[warp - 1] : 0u) + x - v;
+        carry += wsum[31];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) su += __shfl_xor_sync(full, su, o);
+    if (lane == 0) wsum[warp] = su;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int k = 0; k < 32; ++k) t += wsum[k];
+        vcount[0] = carry;
+        vcount[1] = t;
+    }
+}
+
+// The valid rays' indices in ray order (same blocks as mlp_prep_kernel).
+__global__ void __launch_bounds__(256)
+mlp_compact_kernel(const float* __restrict__ label, uint32_t n, const uint32_t* __restrict__ boff,
+                   uint32_t* __restrict__ vlist)
+{
+    __shared__ uint32_t wc[8];
+    const uint32_t r = blockIdx.x * 256u + threadIdx.x;
+    const bool valid = r < n && label[r] != 0.0f;
+    const unsigned full = 0xffffffffu;
+    const unsigned m = __ballot_sync(full, valid);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) wc[warp] = (uint32_t)__popc(m);
+    __syncthreads();
+    uint32_t off = boff[blockIdx.x];
+    for (int k = 0; k < warp; ++k) off += wc[k];
+    if (valid) vlist[off + __popc(m & ((1u << lane) - 1u))] = r;
+}
+
+// FP64 sums of the targets and their squares over the valid list: one
+// partial per warp (part[warp][12]), summed in warp order by
+// mlp_stats_sum_kernel.
+constexpr int kStatsBlocks = 152 * 4;
+
 __global__ void __launch_bounds__(256)
 mlp_stats_kernel(const float* __restrict__ T, const uint32_t* __restrict__ vlist,
-                 const uint32_t* __restrict__ vcount, double* sums /* 12 */)
+                 const uint32_t* __restrict__ vcount, double* __restrict__ part)
 {
     const uint32_t cnt = *vcount;
     double s[12];
@@ -192,9 +263,19 @@ mlp_stats_kernel(const float* __restrict__ T, const uint32_t* __restrict__ vlist
         for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(full, s[q], o);
     }
     if ((threadIdx.x & 31) == 0) {
+        double* p = part + ((size_t)blockIdx.x * 8u + (threadIdx.x >> 5)) * 12u;
 #pragma unroll
-        for (int q = 0; q < 12; ++q) atomicAdd(sums + q, s[q]);
+        for (int q = 0; q < 12; ++q) p[q] = s[q];
     }
+}
+
+__global__ void mlp_stats_sum_kernel(const double* __restrict__ part, int nparts, double* __restrict__ sums)
+{
+    const int q = threadIdx.x;
+    if (q >= 12) return;
+    double t = 0.0;
+    for (int k = 0; k < nparts; ++k) t += part[(size_t)k * 12 + q];
+    sums[q] = t;
 }
 
 // ------------------------------------------------------------------ training step
@@ -845,6 +926,7 @@ lt_status lt_mlp_train(const lt_lens* lens, const lt_mlp_opts* o, lt_mlp** out, 
     lt_status s = check_frame(lens, &o->frame, &pi, &pj);
     if (s != LT_OK) return s;
     if (o->n_fit < 1 || o->n_fit >= (1ull << 31)) return fail(LT_EINVAL, "lt_mlp_train: n_fit out of range");
+    if (o->n_fit_uniform > o->n_fit) return fail(LT_EINVAL, "lt_mlp_train: n_fit_uniform above n_fit");
     const void* ps[] = {o->fit_x, o->fit_y, o->fit_dx, o->fit_dy, o->fit_dz, o->fit_lambda};
     for (const void* p : ps)
         if (!p || !aligned16(p)) return fail(LT_EINVAL, "lt_mlp_train: fit arrays must be non-NULL and 16-byte aligned");
@@ -857,8 +939,10 @@ lt_status lt_mlp_train(const lt_lens* lens, const lt_mlp_opts* o, lt_mlp** out, 
     if (!m) return fail(LT_ENOMEM, "lt_mlp_train: allocation");
     const uint32_t n = (uint32_t)o->n_fit;
     float *X = nullptr, *T = nullptr, *lab = nullptr;
-    uint32_t *vlist = nullptr, *vcount = nullptr;
+    uint32_t *vlist = nullptr, *vcount = nullptr, *bc = nullptr;
     double* sums = nullptr;
+    const uint32_t nb = (n + 255) / 256;
+    const int nparts = kStatsBlocks * 8;
     do {
         if (cudaMemcpy(m->reg, o->init_reg, LT_MLP_REG_PARAMS * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(m->cls, o->init_cls, LT_MLP_CLS_PARAMS * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -867,30 +951,35 @@ lt_status lt_mlp_train(const lt_lens* lens, const lt_mlp_opts* o, lt_mlp** out, 
         }
         if (cudaMalloc(&X, (size_t)n * 16) != cudaSuccess || cudaMalloc(&T, (size_t)n * 24) != cudaSuccess ||
             cudaMalloc(&lab, (size_t)n * 4) != cudaSuccess || cudaMalloc(&vlist, (size_t)n * 4) != cudaSuccess ||
-            cudaMalloc(&vcount, 4) != cudaSuccess || cudaMalloc(&sums, 12 * 8) != cudaSuccess) {
+            cudaMalloc(&vcount, 8) != cudaSuccess || cudaMalloc(&bc, (size_t)nb * 12) != cudaSuccess ||
+            cudaMalloc(&sums, (size_t)(12 + nparts * 12) * 8) != cudaSuccess) {
             s = fail(LT_ENOMEM, "lt_mlp_train: training data allocation");
             break;
         }
         // provisional frame for the features (target statistics come next)
         for (int q = 0; q < 6; ++q) { m->t_mean[q] = 0.0; m->t_std[q] = 1.0; }
         set_frame(m);
-        cudaMemsetAsync(vcount, 0, 4, st);
-        cudaMemsetAsync(sums, 0, 96, st);
         RaysInDev fit{o->fit_x, o->fit_y, o->fit_dx, o->fit_dy, o->fit_dz, o->fit_lambda};
+        const uint32_t nu = o->n_fit_uniform == 0 ? n : (uint32_t)o->n_fit_uniform;
+        uint32_t *bcount = bc, *bcount_u = bc + nb, *boff = bc + 2 * (size_t)nb;
         if (m->cauchy)
-            mlp_prep_kernel<true><<<(n + 255) / 256, 256, 0, st>>>(lens->dev, pi, pj, fit, n, m->F, X, T, lab, vlist, vcount);
+            mlp_prep_kernel<true><<<nb, 256, 0, st>>>(lens->dev, pi, pj, fit, n, nu, m->F, X, T, lab, bcount, bcount_u);
         else
-            mlp_prep_kernel<false><<<(n + 255) / 256, 256, 0, st>>>(lens->dev, pi, pj, fit, n, m->F, X, T, lab, vlist, vcount);
-        mlp_stats_kernel<<<152 * 4, 256, 0, st>>>(T, vlist, vcount, sums);
-        uint32_t nv = 0;
+            mlp_prep_kernel<false><<<nb, 256, 0, st>>>(lens->dev, pi, pj, fit, n, nu, m->F, X, T, lab, bcount, bcount_u);
+        mlp_scan_kernel<<<1, 1024, 0, st>>>(bcount, bcount_u, nb, boff, vcount);
+        mlp_compact_kernel<<<nb, 256, 0, st>>>(lab, n, boff, vlist);
+        mlp_stats_kernel<<<kStatsBlocks, 256, 0, st>>>(T, vlist, vcount, sums + 12);
+        mlp_stats_sum_kernel<<<1, 32, 0, st>>>(sums + 12, nparts, sums);
+        uint32_t nvs[2] = {0, 0};
         double hs[12];
         if (cudaGetLastError() != cudaSuccess ||
-            cudaMemcpyAsync(&nv, vcount, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(nvs, vcount, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaMemcpyAsync(hs, sums, 96, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
             s = fail(LT_ECUDA, "lt_mlp_train: data preparation");
             break;
         }
+        const uint32_t nv = nvs[0];
         if (nv < 2) { s = fail(LT_EINVAL, "lt_mlp_train: fewer than 2 valid training rays"); break; }
         for (int q = 0; q < 6; ++q) {
             const double mean = hs[q] / nv;
@@ -903,6 +992,7 @@ lt_status lt_mlp_train(const lt_lens* lens, const lt_mlp_opts* o, lt_mlp** out, 
         set_frame(m);
         m->stats.n_train = n;
         m->stats.n_valid = nv;
+        m->stats.n_valid_uniform = nvs[1];
         TrainBatch tr{X, T, lab, vlist, nv, o->seed, 0, o->reg_batch, 0};
         if (o->reg_steps > 0 &&
             (s = train_net<true>(m, m->reg, tr, o->reg_steps, o->lr, o->lr_decay, o->decay_every,
@@ -916,15 +1006,35 @@ lt_status lt_mlp_train(const lt_lens* lens, const lt_mlp_opts* o, lt_mlp** out, 
         }
         // classifier: batches drawn from all n rays
         TrainBatch tc{X, T, lab, nullptr, n, o->seed ^ 0x9e3779b97f4a7c15ull, 0, o->cls_batch, 0};
-        if (o->cls_steps > 0)
-            s = train_net<false>(m, m->cls, tc, o->cls_steps, o->lr, o->lr_decay, o->decay_every,
-                                 &m->stats.cls_loss, st);
+        if (o->cls_steps > 0 &&
+            (s = train_net<false>(m, m->cls, tc, o->cls_steps, o->lr, o->lr_decay, o->decay_every,
+                                  &m->stats.cls_loss, st)) != LT_OK)
+            break;
+        // valid-region samples after a uniform prefix: shift the classifier's
+        // prior back to that of uniform draws (odds divided by k)
+        if (nu < n && o->cls_steps > 0) {
+            const double k = 1.0 + (double)(nv - nvs[1]) / (double)std::max<uint32_t>(nvs[1], 1u);
+            const int bo = Net<false>::boff(Net<false>::L - 1);
+            float b = 0.f;
+            if (cudaMemcpyAsync(&b, m->cls + bo, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                s = fail(LT_ECUDA, "lt_mlp_train: classifier bias read-back");
+                break;
+            }
+            m->stats.cls_prior_shift = std::log(k);
+            b = (float)((double)b - m->stats.cls_prior_shift);
+            if (cudaMemcpy(m->cls + bo, &b, 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+                s = fail(LT_ECUDA, "lt_mlp_train: classifier bias update");
+                break;
+            }
+        }
     } while (0);
     if (X) cudaFree(X);
     if (T) cudaFree(T);
     if (lab) cudaFree(lab);
     if (vlist) cudaFree(vlist);
     if (vcount) cudaFree(vcount);
+    if (bc) cudaFree(bc);
     if (sums) cudaFree(sums);
     if (s != LT_OK) { delete m; return s; }
     m->frags_stale = true;

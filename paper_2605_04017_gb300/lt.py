@@ -339,6 +339,38 @@ def mcmc_sample(lens: Lens, path_id: int, lo, hi, seed: int, chains: int, steps:
     return f, flags, acc
 
 
+class FitRays:
+    """A device training set for lt_mlp_train: inp = [x, y, dx, dy, dz], lam,
+    n, and n_uniform (how many leading rays are uniform draws of the box)."""
+
+    def __init__(self, inp, lam, n_uniform=0):
+        self.inp, self.lam, self.n = list(inp), lam, int(lam.numel())
+        self.n_uniform = int(n_uniform)
+
+
+def valid_region_fit(lens: Lens, path_id: int, lo, hi, uniform, chains: int, steps: int, seed: int,
+                     small: float = 0.03, p_large: float = 0.05, init_tries: int = 64, stream=None) -> FitRays:
+    """Training rays of one path as Sec. 5.1 collects them: the regressor
+    wants rays spread over the path's valid region, which uniform draws of
+    the input box seldom hit on a ghost path, so a Markov chain sampler whose
+    target is the path's binary visibility (lt_mcmc_sample) supplies them;
+    the classifier wants valid and invalid rays in about equal numbers, which
+    the uniform draws (mostly invalid on a sparse path) complete.  Returns
+    `uniform` (a batch.DeviceRays) followed by the states of every chain that
+    started (chains x steps samples at most), with n_uniform set so that
+    lt_mlp_train corrects its classifier for the sampler's extra valid rays.
+    Joining the two sets is a device copy; tracing, labels and training are
+    the library's."""
+    import torch
+    f, flags, _ = mcmc_sample(lens, path_id, lo, hi, seed, chains, steps, small, p_large, init_tries, stream)
+    torch.cuda.synchronize()          # the joins below run on torch's current stream
+    m = chains * steps
+    keep = flags[:m] != 0
+    inp = [torch.cat([u, s[:m][keep]]) for u, s in zip(uniform.inp, f[:5])]
+    lam = torch.cat([uniform.lam, f[5][:m][keep]])
+    return FitRays(inp, lam, uniform.n)
+
+
 # ------------------------------------------------------------------ maps
 
 QUERY_TABLE = 0
@@ -609,14 +641,15 @@ class c_mlp_opts(ctypes.Structure):
                 ("lr", ctypes.c_double), ("lr_decay", ctypes.c_double),
                 ("decay_every", ctypes.c_int32),
                 ("ft_steps", ctypes.c_int32), ("ft_batch", ctypes.c_int32), ("ft_lr", ctypes.c_double),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("n_fit_uniform", ctypes.c_uint64)]
 
 
 class c_mlp_stats(ctypes.Structure):
     _fields_ = [("n_train", ctypes.c_uint64), ("n_valid", ctypes.c_uint64),
                 ("reg_loss", ctypes.c_double), ("cls_loss", ctypes.c_double),
                 ("t_mean", ctypes.c_double * 6), ("t_std", ctypes.c_double * 6),
-                ("train_ms", ctypes.c_double), ("tc_wait_timeouts", ctypes.c_uint64)]
+                ("train_ms", ctypes.c_double), ("tc_wait_timeouts", ctypes.c_uint64),
+                ("n_valid_uniform", ctypes.c_uint64), ("cls_prior_shift", ctypes.c_double)]
 
 
 def _declare_mlp(L: ctypes.CDLL) -> None:
@@ -678,8 +711,10 @@ class Mlp:
     def train(cls, lens: Lens, frame: c_mlp_frame, fit, init_reg, init_cls, reg_steps=2000,
               reg_batch=8192, cls_steps=2000, cls_batch=8192, lr=1e-4, lr_decay=0.95,
               decay_every=10000, ft_steps=0, ft_batch=8192, ft_lr=1e-6, seed=1,
-              stream=None) -> "Mlp":
-        """fit: a batch.DeviceRays of training rays; init_*: host FP32 parameters."""
+              stream=None, n_fit_uniform=None) -> "Mlp":
+        """fit: a batch.DeviceRays (or FitRays) of training rays; init_*: host
+        FP32 parameters.  n_fit_uniform defaults to the fit set's own
+        (FitRays from valid_region_fit carry it; 0 otherwise)."""
         import numpy as np
         ir = np.ascontiguousarray(init_reg, np.float32)
         ic = np.ascontiguousarray(init_cls, np.float32)
@@ -693,6 +728,7 @@ class Mlp:
         o.lr, o.lr_decay, o.decay_every = lr, lr_decay, decay_every
         o.ft_steps, o.ft_batch, o.ft_lr = ft_steps, ft_batch, ft_lr
         o.seed = seed
+        o.n_fit_uniform = getattr(fit, "n_uniform", 0) if n_fit_uniform is None else n_fit_uniform
         h = ctypes.c_void_p()
         check(lib().lt_mlp_train(lens.handle, ctypes.byref(o), ctypes.byref(h), _stream_handle(stream)))
         return cls(h)
@@ -713,7 +749,8 @@ class Mlp:
         check(lib().lt_mlp_stats_get(self.handle, ctypes.byref(s)))
         return {"n_train": s.n_train, "n_valid": s.n_valid, "reg_loss": s.reg_loss,
                 "cls_loss": s.cls_loss, "t_mean": list(s.t_mean), "t_std": list(s.t_std),
-                "train_ms": s.train_ms, "tc_wait_timeouts": s.tc_wait_timeouts}
+                "train_ms": s.train_ms, "tc_wait_timeouts": s.tc_wait_timeouts,
+                "n_valid_uniform": s.n_valid_uniform, "cls_prior_shift": s.cls_prior_shift}
 
     def params(self):
         import numpy as np
