@@ -191,11 +191,13 @@ lt_status lt_trace(const lt_lens* lens, const lt_rays_in* in, const float* lambd
                    int32_t path_id, const lt_rays_out* out, size_t n, lt_stream stream);
 
 /* Same, with HOST arrays (pageable or pinned; pinned is faster): traces in
- * pipelined chunks of at most 2^20 rays and returns when the outputs are in
- * host memory.  Each chunk passes through three library streams (copy in,
- * kernels, copy out), so one chunk's inputs copy in while an older chunk's
- * outputs copy back.  Errors as lt_trace, plus LT_ENOMEM for staging
- * buffers. */
+ * pipelined chunks of about n / 8 rays (2^16 to 2^20) and returns when the
+ * outputs are in host memory.  Each chunk passes through three library
+ * streams (copy in, kernels, copy out), so one chunk's inputs copy in while
+ * an older chunk's outputs copy back.  When the six input arrays lie at equal
+ * distances in memory (rows of one block), each chunk's inputs move in one
+ * strided copy, and likewise the six float outputs; otherwise one copy per
+ * array.  Errors as lt_trace, plus LT_ENOMEM for staging buffers. */
 lt_status lt_trace_host(const lt_lens* lens, const lt_rays_in* in, const float* lambda_nm,
                         int32_t path_id, const lt_rays_out* out, size_t n);
 

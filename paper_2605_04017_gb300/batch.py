@@ -39,14 +39,19 @@ class DeviceOut:
 
 
 class HostRays:
-    """Pinned host copies of entrance rays and outputs (for the *_host calls)."""
+    """Host copies of entrance rays and outputs (for the *_host calls), pinned
+    by default.  The six input arrays are rows of one (6, n) block and so are
+    the six float outputs: the library then moves each chunk of a direction
+    in one strided copy."""
 
     def __init__(self, rays, pin=True):
-        self.inp = [torch.from_numpy(np.ascontiguousarray(a, np.float32)) for a in rays.arrays()]
-        if pin:
-            self.inp = [t.pin_memory() for t in self.inp]
         n = len(rays)
-        self.out = [torch.empty(n, dtype=torch.float32, pin_memory=pin) for _ in range(6)]
+        blk = torch.from_numpy(np.ascontiguousarray(np.stack([np.asarray(a, np.float32) for a in rays.arrays()])))
+        if pin:
+            blk = blk.pin_memory()
+        self.inp = [blk[q] for q in range(6)]
+        oblk = torch.empty((6, n), dtype=torch.float32, pin_memory=pin)
+        self.out = [oblk[q] for q in range(6)]
         self.flags = torch.empty(n, dtype=torch.uint8, pin_memory=pin)
         self.n = n
 

@@ -49,6 +49,9 @@ struct Staging {
     size_t cap = 0;
     cudaStream_t s_in = nullptr, s_k = nullptr, s_out = nullptr;
     cudaEvent_t in_done[kHostSets] = {}, k_done[kHostSets] = {}, out_done[kHostSets] = {};
+    // per buffer set: the six input arrays, then the six output arrays, then
+    // the flags, one allocation, each array `cap` elements from the previous
+    unsigned char* block[kHostSets] = {};
     float* in[kHostSets][6] = {};
     float* out[kHostSets][6] = {};
     uint8_t* flags[kHostSets] = {};
@@ -57,12 +60,9 @@ struct Staging {
     void release()
     {
         for (int b = 0; b < kHostSets; ++b) {
-            for (int q = 0; q < 6; ++q) {
-                if (in[b][q]) cudaFree(in[b][q]);
-                if (out[b][q]) cudaFree(out[b][q]);
-                in[b][q] = out[b][q] = nullptr;
-            }
-            if (flags[b]) cudaFree(flags[b]);
+            if (block[b]) cudaFree(block[b]);
+            block[b] = nullptr;
+            for (int q = 0; q < 6; ++q) in[b][q] = out[b][q] = nullptr;
             flags[b] = nullptr;
         }
         cap = 0;
@@ -77,6 +77,7 @@ struct Staging {
             s_in = s_k = s_out = nullptr;
             for (int b = 0; b < kHostSets; ++b) {
                 in_done[b] = k_done[b] = out_done[b] = nullptr;
+                block[b] = nullptr;
                 for (int q = 0; q < 6; ++q) in[b][q] = out[b][q] = nullptr;
                 flags[b] = nullptr;
             }
@@ -94,17 +95,16 @@ struct Staging {
         if (chunk <= cap) return LT_OK;
         release();
         for (int b = 0; b < kHostSets; ++b) {
-            for (int q = 0; q < 6; ++q) {
-                if (cudaMalloc(&in[b][q], chunk * sizeof(float)) != cudaSuccess ||
-                    cudaMalloc(&out[b][q], chunk * sizeof(float)) != cudaSuccess) {
-                    release();
-                    return fail(LT_ENOMEM, "host staging: cudaMalloc failed");
-                }
-            }
-            if (cudaMalloc(&flags[b], chunk) != cudaSuccess) {
+            if (cudaMalloc(&block[b], chunk * (12 * sizeof(float) + 1)) != cudaSuccess) {
                 release();
                 return fail(LT_ENOMEM, "host staging: cudaMalloc failed");
             }
+            float* f = reinterpret_cast<float*>(block[b]);
+            for (int q = 0; q < 6; ++q) {
+                in[b][q] = f + q * chunk;
+                out[b][q] = f + (6 + q) * chunk;
+            }
+            flags[b] = block[b] + 12 * sizeof(float) * chunk;
         }
         cap = chunk;
         return LT_OK;
@@ -112,16 +112,28 @@ struct Staging {
 };
 
 
-// Rays per chunk: about n / 4 (so the pipeline fills and drains in a small
-// part of the call), between 2^16 and 2^20 rays.  Measured on the 11-surface
-// lens at 4,194,304 rays: 2^20-ray chunks beat 2^19 and 2^18 (more, smaller
-// copies cost more than the shorter fill and drain save).
+// Rays per chunk: about n / 8 (so the pipeline fills and drains in a small
+// part of the call), between 2^16 and 2^20 rays, a multiple of 64 (which
+// keeps every staged array 16-byte aligned).
 inline size_t host_chunk(size_t n)
 {
-    size_t c = (n + 3) / 4;
+    size_t c = (n + 7) / 8;
     c = std::max<size_t>(c, 65536);
     c = std::min<size_t>(c, (size_t)1 << 20);
     return (c + 63) & ~(size_t)63;
+}
+
+// The byte distance between consecutive arrays of `a` when the six are
+// equally spaced and at least `len` bytes apart (one strided copy then moves
+// a chunk of all six); 0 otherwise.
+inline size_t equal_pitch(const void* const a[6], size_t len)
+{
+    const char* p0 = static_cast<const char*>(a[0]);
+    const ptrdiff_t d = static_cast<const char*>(a[1]) - p0;
+    if (d < (ptrdiff_t)len || d >= ((ptrdiff_t)1 << 31)) return 0;   // a strided copy's pitch is below 2^31
+    for (int q = 2; q < 6; ++q)
+        if (static_cast<const char*>(a[q]) - p0 != d * q) return 0;
+    return (size_t)d;
 }
 
 Staging& host_staging();
@@ -135,14 +147,23 @@ lt_status host_chunks(Staging& S, const lt_rays_in* in, const float* lam, const 
 {
     const float* hin[6] = {in->x, in->y, in->dx, in->dy, in->dz, lam};
     float* hout[6] = {out->x, out->y, out->dx, out->dy, out->dz, out->I};
+    // host arrays laid out at equal distances (one allocation per direction):
+    // one strided copy per direction and chunk instead of six
+    const void* hi[6] = {hin[0], hin[1], hin[2], hin[3], hin[4], hin[5]};
+    const void* ho[6] = {hout[0], hout[1], hout[2], hout[3], hout[4], hout[5]};
+    const size_t pin = equal_pitch(hi, n * sizeof(float)), pout = equal_pitch(ho, n * sizeof(float));
     for (size_t off = 0, c = 0; off < n; off += chunk, ++c) {
         const int b = (int)(c % kHostSets);
         const size_t m = std::min(chunk, n - off);
         // buffer set b was last read by the kernel of chunk c - kHostSets
         if (c >= (size_t)kHostSets) LT_CUDA_TRY(cudaStreamWaitEvent(S.s_in, S.k_done[b], 0));
-        for (int q = 0; q < 6; ++q)
-            LT_CUDA_TRY(cudaMemcpyAsync(S.in[b][q], hin[q] + off, m * sizeof(float),
-                                        cudaMemcpyHostToDevice, S.s_in));
+        if (pin)
+            LT_CUDA_TRY(cudaMemcpy2DAsync(S.in[b][0], S.cap * sizeof(float), hin[0] + off, pin, m * sizeof(float), 6,
+                                          cudaMemcpyHostToDevice, S.s_in));
+        else
+            for (int q = 0; q < 6; ++q)
+                LT_CUDA_TRY(cudaMemcpyAsync(S.in[b][q], hin[q] + off, m * sizeof(float),
+                                            cudaMemcpyHostToDevice, S.s_in));
         LT_CUDA_TRY(cudaEventRecord(S.in_done[b], S.s_in));
         LT_CUDA_TRY(cudaStreamWaitEvent(S.s_k, S.in_done[b], 0));
         // and its outputs were last copied out by chunk c - kHostSets
@@ -154,9 +175,13 @@ lt_status host_chunks(Staging& S, const lt_rays_in* in, const float* lam, const 
         if (s != LT_OK) return s;
         LT_CUDA_TRY(cudaEventRecord(S.k_done[b], S.s_k));
         LT_CUDA_TRY(cudaStreamWaitEvent(S.s_out, S.k_done[b], 0));
-        for (int q = 0; q < 6; ++q)
-            LT_CUDA_TRY(cudaMemcpyAsync(hout[q] + off, S.out[b][q], m * sizeof(float),
-                                        cudaMemcpyDeviceToHost, S.s_out));
+        if (pout)
+            LT_CUDA_TRY(cudaMemcpy2DAsync(hout[0] + off, pout, S.out[b][0], S.cap * sizeof(float), m * sizeof(float),
+                                          6, cudaMemcpyDeviceToHost, S.s_out));
+        else
+            for (int q = 0; q < 6; ++q)
+                LT_CUDA_TRY(cudaMemcpyAsync(hout[q] + off, S.out[b][q], m * sizeof(float),
+                                            cudaMemcpyDeviceToHost, S.s_out));
         LT_CUDA_TRY(cudaMemcpyAsync(out->flags + off, S.flags[b], m, cudaMemcpyDeviceToHost, S.s_out));
         LT_CUDA_TRY(cudaEventRecord(S.out_done[b], S.s_out));
     }

@@ -312,6 +312,12 @@ def test_queue_form_equals_one_kernel_form(eleven_pair, eleven):
     na_out, na_flags = o3.numpy()
     assert np.array_equal(na_flags, big_flags[:m])
     assert np.array_equal(na_out.view(np.uint32), big_out[:m].view(np.uint32))
+    # the host entry point, pinned and pageable arrays
+    for pin in (True, False):
+        h = batch.HostRays(rays, pin=pin)
+        g.query_host(h.inp[:5], h.inp[5], h.out + [h.flags], n)
+        assert np.array_equal(h.flags.numpy(), big_flags), pin
+        assert np.array_equal(np.stack([t.numpy() for t in h.out], 1).view(np.uint32), big_out.view(np.uint32)), pin
 
 
 FULL_CFG = dict(degree=4, patches=(8, 8, 4, 1), cells=(16, 16, 16, 8), samples=6, tol=1e-4)
