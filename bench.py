@@ -61,6 +61,11 @@ NCU_TRAFFIC = {
     # host-side checks of lt_map_load have changed)
     "map_query_kernel": {"bytes_per_ray": 356417280 / 4194304, "hash": "12bf472bbeff6ce1"},
     "map_trace_kernel": {"bytes_per_ray": 105388544 / 4194304, "hash": "12bf472bbeff6ce1"},
+    # ncu --set full, one launch of each kernel of the polynomial-patch query of
+    # the same 4,194,304 rays: 102,797,056 + 7,808,512 bytes (sort) and
+    # 38,197,504 + 45,350,912 bytes (evaluation)
+    "poly_sort_kernel": {"bytes_per_ray": 110605568 / 4194304, "hash": "b0506b74d7c77f28"},
+    "poly_eval_kernel": {"bytes_per_ray": 83548416 / 4194304, "hash": "b0506b74d7c77f28"},
 }
 
 KERNEL_SRCS = ["paper_2605_04017_gb300/csrc/trace.cu", "paper_2605_04017_gb300/csrc/tracer.cuh",
@@ -880,6 +885,95 @@ def bench_serving(args, peaks, seconds=10.0, warm=1.0, rate=2000.0):
             "map_err_vs_fp32_trace": map_err}
 
 
+SWEEP_POLY = [
+    # (degree, patches, cells per patch, max_residual_mm): the headline first
+    (4, [4, 4, 2, 1], [32, 32, 32, 8], 1e-4),
+    (4, [4, 4, 2, 1], [32, 32, 32, 8], 1e-3),
+    (4, [4, 4, 2, 1], [32, 32, 32, 8], 1e-2),
+    (4, [4, 4, 2, 1], [32, 32, 32, 8], 0.0),
+    (4, [4, 4, 2, 1], [16, 16, 16, 4], 1e-4),
+    (4, [4, 4, 2, 1], [64, 64, 64, 8], 1e-4),
+    (5, [4, 4, 2, 1], [32, 32, 32, 8], 1e-4),
+    (3, [8, 8, 4, 2], [16, 16, 16, 4], 1e-4),
+    (2, [16, 16, 8, 2], [8, 8, 8, 4], 1e-4),
+]
+SWEEP_TABLE = [([16, 16, 16, 16, 8], 0.0), ([24, 24, 24, 24, 8], 0.0), ([32, 32, 32, 32, 8], 0.0),
+               ([40, 40, 40, 40, 8], 0.0), ([32, 32, 32, 32, 8], 1e-4)]
+
+
+def bench_sweep(args, stream, flush, peaks):
+    """Accuracy against speed on the headline workload (11-surface lens, the
+    same 4,194,304 rays): the polynomial-patch map over degree, patch grid,
+    mask resolution and certification limit, and the multilinear table map
+    over lattice resolution, each fitted from the same 16,777,216 traced rays;
+    rays/s of the query, its error against the FP32 trace of the same rays
+    and the share of rays it traces, beside the FP32 trace itself."""
+    import torch
+    from paper_2605_04017_gb300 import batch, lt, workloads as w
+    presc = w.eleven_surface_lens(lib_accept)
+    lens = lt.Lens(presc)
+    rho = w.eleven_rho(presc)
+    n = args.rays or w.ELEVEN_N
+    d = batch.DeviceRays(w.entrance_rays(n, w.SEED_BASE + 2, rho))
+    fit = batch.DeviceRays(w.eleven_fit_rays(presc))
+    o, ot = batch.DeviceOut(n), batch.DeviceOut(n)
+    steps = max(3, args.steps // 2)
+
+    def timed(step):
+        t = timed_steps(step, steps, args.warmup, flush, stream)
+        return {"rays_per_s": round(n * len(t) / (sum(t) * 1e-3), 1), "ms_per_step": round(statistics.mean(t), 4)}
+
+    tr = timed(lambda: lt.trace(lens, d.inp, d.lam, 0, ot.out, n, stream))
+    torch.cuda.synchronize()
+    tout = torch.stack(ot.f, 1).cpu().numpy()
+    tflags = ot.flags.cpu().numpy()
+
+    def measured(m, build_s, extra):
+        r = timed(lambda: m.query(d.inp, d.lam, o.out, n, lt.QUERY_TABLE, stream))
+        torch.cuda.synchronize()
+        qflags = o.flags.cpu().numpy()
+        qout = torch.stack(o.f, 1).cpu().numpy()
+        traced = float(((qflags & lt.FLAG_TRACED) != 0).mean())
+        e = map_error(qout, qflags, tout, tflags, lt)
+        keep = ("pos_max_mm", "pos_p99_mm", "pos_rms_mm", "dir_max", "I_max", "valid_agreement",
+                "validity_mismatches", "validity_mismatches_near_edge")
+        row = dict(extra)
+        row.update(r)
+        row.update({"map_over_trace": round(r["rays_per_s"] / tr["rays_per_s"], 3), "build_s": round(build_s, 2),
+                    "traced": round(traced, 4), "answered_by_map": round(e["rays_interpolated"] / n, 4)})
+        row.update({k: e[k] for k in keep if k in e})
+        return row
+
+    rows = []
+    lo, hi = map_box(rho)
+    for deg, pt, cells, tol in SWEEP_POLY:
+        cfg = {"degree": deg, "patches": pt, "cells": cells, "samples": deg + 2, "max_residual_mm": tol}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = build_poly(lt, lens, rho, fit, cfg)
+        torch.cuda.synchronize()
+        bs = time.perf_counter() - t0
+        ps = m.poly_stats()
+        rows.append(measured(m, bs, {"map": "poly", "degree": deg, "patches": pt,
+                                     "mask_cells": [a * b for a, b in zip(pt, cells)], "max_residual_mm": tol,
+                                     "table_bytes": m.stats()["table_bytes"], "patches_fit": ps["patches_fit"]}))
+        del m
+        torch.cuda.empty_cache()
+    for res, tol in SWEEP_TABLE:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = lt.Map.build(lens, 0, res, lo, hi, fit=fit, max_residual_mm=tol)
+        torch.cuda.synchronize()
+        bs = time.perf_counter() - t0
+        rows.append(measured(m, bs, {"map": "table", "res": res, "max_residual_mm": tol,
+                                     "table_bytes": m.stats()["n_nodes"] * 32}))
+        del m
+        torch.cuda.empty_cache()
+    return {"workload": "11-surface lens, %d rays, transmission path; maps fitted from 16,777,216 traced rays; "
+                        "%d timed steps each, L2 flushed before every step" % (n, steps),
+            "trace": tr, "maps": rows}
+
+
 def run_only(args):
     """One of the other workloads alone (1 GPU): prints {"workload_key": ..., ...}."""
     import torch
@@ -891,7 +985,8 @@ def run_only(args):
     def flush():
         flush_buf.fill_(1)
 
-    fns = {"singlet": bench_singlet, "precision": bench_precision, "flares": bench_flares, "mcmc": bench_mcmc}
+    fns = {"singlet": bench_singlet, "precision": bench_precision, "flares": bench_flares, "mcmc": bench_mcmc,
+           "sweep": bench_sweep}
     if args.only == "serving":
         out = bench_serving(args, peaks, seconds=args.serve_seconds)
     else:
@@ -999,7 +1094,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-extra", action="store_true", help="headline workload only")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
-    ap.add_argument("--only", choices=["singlet", "precision", "flares", "mcmc", "serving"],
+    ap.add_argument("--only", choices=["singlet", "precision", "flares", "mcmc", "serving", "sweep"],
                     help="run one of the other workloads alone and print its object")
     ap.add_argument("--rays", type=int, default=0, help="headline batch size (default 4,194,304)")
     ap.add_argument("--precision-rays", type=int, default=0)
