@@ -100,7 +100,7 @@ class ClockSampler:
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
@@ -132,7 +132,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, mx, reasons = [], [], set()
+        sm, mx, util, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
@@ -146,9 +146,14 @@ class ClockSampler:
             for nm, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
+            try:
+                util.append(float(parts[9]))
+            except (IndexError, ValueError):
+                pass
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm),
+                "gpu_util_pct_mean": round(statistics.mean(util), 1) if util else None}
 
 
 def oracle_accept(p):
@@ -508,12 +513,20 @@ def bench_singlet(args, stream, flush, peaks):
     lo, hi = map_box(w.SINGLET_RHO)
     gmap = lt.Map.build(lens, 0, RES, lo, hi, fit=d)
     oq, ot = batch.DeviceOut(n), batch.DeviceOut(n)
-    q, _ = time_kernel(lambda: gmap.query(d.inp, d.lam, oq.out, n, lt.QUERY_TABLE, stream), "q", args, flush,
-                       stream, n, lt)
-    t, _ = time_kernel(lambda: lt.trace(lens, d.inp, d.lam, 0, ot.out, n, stream), "t", args, flush, stream, n, lt)
+    q, pq = time_kernel(lambda: gmap.query(d.inp, d.lam, oq.out, n, lt.QUERY_TABLE, stream), "q", args, flush,
+                        stream, n, lt)
+    t, pt = time_kernel(lambda: lt.trace(lens, d.inp, d.lam, 0, ot.out, n, stream), "t", args, flush, stream, n,
+                        lt)
     torch.cuda.synchronize()
     qo, qf = oq.numpy()
     to, tf = ot.numpy()
+    # the one-kernel query's algorithmic bytes: 24 B in and 25 B out per ray,
+    # and per interpolated ray the 32 corners' 24-byte node values it gathers
+    n_interp = int((((qf & lt.FLAG_VALID) != 0) & ((qf & lt.FLAG_TRACED) == 0)).sum())
+    q["kernel"] = kernel_roofline("map_query_fused_kernel", pq, peaks, args.steps,
+                                  units_bytes=n * 49 + n_interp * 32 * 24)
+    q["kernel"]["note"] = "algorithmic bytes: 49 B per ray + 768 B of corner gathers per interpolated ray"
+    t["kernel"] = kernel_roofline("trace_kernel", pt, peaks, args.steps, flops_per_work=FLOPS_PER_INTERACTION)
     return {"workload": "2-surface singlet (R +-50 mm, t 5 mm, a 10 mm), 65,536 rays, map 32^4x8 fitted on them",
             "query": q, "trace": t, "map_err_vs_fp32_trace": pos_err(qo, qf, to, tf, lt.FLAG_VALID)}
 
@@ -530,6 +543,8 @@ def bench_precision(args, stream, flush, peaks):
     rho = w.SINGLET_RHO
     rng = np.random.Generator(np.random.PCG64(w.SEED_BASE + 3))
     fit = batch.DeviceRays(w.entrance_rays(1 << 21, w.SEED_BASE + 3 + 1000, rho))
+    lt.profile_enable(True)
+    lt.profile_read(reset=True)
     t0 = time.perf_counter()
     if args.untrained:
         # random Xavier networks (profiling: no training launches before the query)
@@ -539,7 +554,38 @@ def bench_precision(args, stream, flush, peaks):
         m = lt.Mlp.train(lens, lt.mlp_frame(0, rho, 0.2421), fit, xavier_flat(MLP_REG_SIZES, rng),
                          xavier_flat(MLP_CLS_SIZES, rng), reg_steps=6000, reg_batch=8192, cls_steps=4000,
                          cls_batch=8192, lr=1e-3, lr_decay=0.95, decay_every=500, seed=5)
+    torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
+    ptrain = lt.profile_read(reset=True)
+    lt.profile_enable(False)
+    train_kernels = {}
+    if not args.untrained:
+        fp32 = fp32_peak_tflops(peaks["sm_max_mhz"])
+        macs = {"mlp_train_reg_kernel": MLP_MACS - 1184, "mlp_train_cls_kernel": 1184}
+        for k, nm in (("mlp_train_reg_kernel", 6000), ("mlp_train_cls_kernel", 4000)):
+            if k in ptrain:
+                launches, ms, _ = ptrain[k]
+                # forward + backward of a batch: 3 x 2 flop per MAC per ray
+                fl = 6.0 * macs[k] * 8192 * launches
+                train_kernels[k] = {"launches": launches, "avg_launch_ms": round(ms / launches, 5),
+                                    "bound": "alu", "achieved": round(fl / (ms * 1e-3) / 1e12, 2),
+                                    "peak": round(fp32, 1), "unit": "TFLOP/s",
+                                    "frac": round(fl / (ms * 1e-3) / 1e12 / fp32, 4),
+                                    "note": "6 flop per MAC per ray (forward + both backward products), "
+                                            "batch 8192"}
+        if "mlp_adam_kernel" in ptrain:
+            launches, ms, _ = ptrain["mlp_adam_kernel"]
+            # per parameter: P read + written (8 B), the moments read + written
+            # (FP64: 32 B) and one gradient partial per training block read (4 B
+            # x 64 blocks of 128 rays)
+            by = (6000 * 4582 + 4000 * 1249) * (8 + 32 + 4 * 64)   # reg 4,582 and cls 1,249 parameters
+            ach = by / (ms * 1e-3) / 1e9
+            train_kernels["mlp_adam_kernel"] = {
+                "launches": launches, "avg_launch_ms": round(ms / launches, 5), "bound": "hbm",
+                "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(ach / peaks["hbm_gbs"], 4),
+                "note": "per parameter and step: 8 B of parameter, 32 B of FP64 moments, 4 B x 64 "
+                        "gradient partials"}
     lo, hi = map_box(rho)
     gmap = lt.Map.build(lens, 0, RES, lo, hi, fit=fit)
     del fit
@@ -572,6 +618,18 @@ def bench_precision(args, stream, flush, peaks):
                 r["kernel"]["tensor_frac"] = round(tflops / peak, 4)
                 r["kernel"]["tensor_peak"] = "%.1f TFLOP/s of measured (bf16 burst; fp16 taken equal)" % peak
             r["kernel"]["hbm_frac"] = round(49.0 * n / avg_s / 1e9 / peaks["hbm_gbs"], 4)
+        if key == "table_f32" and "map_query_kernel" in prof:
+            # as the headline's table map: 24 B in, 25 B out per answered ray, 4 B
+            # per queued ray, the node table (6 floats per node) and classes once
+            qf = outs[key][1]
+            m_fb = int(((qf & lt.FLAG_TRACED) != 0).sum())
+            ms_ = gmap.stats()
+            r["kernel"] = kernel_roofline("map_query_kernel", prof, peaks, args.steps,
+                                          units_bytes=n * 24 + (n - m_fb) * 25 + m_fb * 4 + ms_["n_nodes"] * 24 +
+                                          (ms_["n_cells"] + 15) // 16 * 4)
+        if key == "trace_f32" and "trace_kernel" in prof:
+            r["kernel"] = kernel_roofline("trace_kernel", prof, peaks, args.steps,
+                                          flops_per_work=FLOPS_PER_INTERACTION)
         res[key] = r
     to, tf = outs["trace_f32"]
     errs = {k: pos_err(outs[k][0], outs[k][1], to, tf, lt.FLAG_VALID) for k in outs if k != "trace_f32"}
@@ -581,7 +639,8 @@ def bench_precision(args, stream, flush, peaks):
     st = m.stats()
     return {"workload": "singlet, 16,777,216 rays (seed +3); learned map = classifier 4-32-32-1 + "
                         "regressor 4-(32x5)-6, trained on the GPU from 2,097,152 traced rays",
-            "train": {"s": round(train_s, 2), "reg_loss": st["reg_loss"], "cls_loss": st["cls_loss"],
+            "train": {"s": round(train_s, 2), "kernels": train_kernels,
+                      "reg_loss": st["reg_loss"], "cls_loss": st["cls_loss"],
                       "steps": "reg 6000 + cls 4000, batch 8192, Adam lr 1e-3 x0.95/500"},
             "rays_per_s": res, "pos_err_vs_fp32_trace": errs}
 
@@ -763,7 +822,9 @@ def bench_mcmc(args, stream, flush, peaks):
             "chains_started": round(started, 4),
             "acceptance": round(float(a[a > 0].mean()) / steps, 4) if (a > 0).any() else 0.0,
             "valid_fraction_of_uniform_draws": round(uniform_valid, 5),
-            "useful_tflops": round(useful, 2)}
+            "useful_tflops": round(useful, 2),
+            "roofline": kernel_roofline("mcmc_kernel", prof, peaks, args.steps,
+                                        flops_per_work=FLOPS_PER_INTERACTION)}
 
 
 def bench_serving(args, peaks, seconds=10.0, warm=1.0, rate=2000.0):
@@ -807,81 +868,96 @@ def bench_serving(args, peaks, seconds=10.0, warm=1.0, rate=2000.0):
     del eq, et
     SLOTS = 48
     slots = [batch.DeviceOut(NMAX) for _ in range(SLOTS)]
-    free = queue.Queue()
-    for i in range(SLOTS):
-        free.put(i)
     torch.cuda.synchronize()
-    rng = np.random.Generator(np.random.PCG64(w.SEED_BASE + 5))
-    total = seconds + warm
-    n_req = int(rate * total * 1.2) + 16
-    gaps = rng.exponential(1.0 / rate, n_req)
-    t_arr = np.cumsum(gaps)
-    n_req = int(np.searchsorted(t_arr, total))
-    t_arr = t_arr[:n_req]
-    sizes = np.exp(rng.uniform(np.log(1024), np.log(NMAX), n_req)).astype(np.int64)
-    which = rng.integers(0, len(pres), n_req)
-    main = rng.uniform(size=n_req) < 0.5
-    ghost = [int(rng.integers(1, lenses[k].n_paths)) for k in which]
-    srv = lt.Server(n_streams=4)
-    tickets = queue.Queue()
-    stalls = [0]
 
-    def submitter():
-        t0 = time.perf_counter()
-        for i in range(n_req):
-            while True:
-                dt = t0 + t_arr[i] - time.perf_counter()
-                if dt <= 0:
-                    break
-                time.sleep(dt if dt > 2e-4 else 0)
-            try:
-                slot = free.get_nowait()
-            except queue.Empty:
-                stalls[0] += 1
-                slot = free.get()
-            k, nn = int(which[i]), int(sizes[i])
-            d, o = inputs[k], slots[slot]
-            if main[i]:
-                t = srv.submit_query(maps[k], d.inp, d.lam, o.out, nn)
-            else:
-                t = srv.submit_trace(lenses[k], d.inp, d.lam, ghost[i], o.out, nn)
-            tickets.put((i, t, slot, time.perf_counter() - t0))
-        tickets.put(None)
+    def run(rate, window_us, seed):
+        """One serving run: Poisson arrivals at `rate` for `warm` + `seconds`."""
+        free = queue.Queue()
+        for i in range(SLOTS):
+            free.put(i)
+        rng = np.random.Generator(np.random.PCG64(w.SEED_BASE + 5 + seed))
+        total = seconds + warm
+        n_req = int(rate * total * 1.2) + 16
+        t_arr = np.cumsum(rng.exponential(1.0 / rate, n_req))
+        n_req = int(np.searchsorted(t_arr, total))
+        t_arr = t_arr[:n_req]
+        sizes = np.exp(rng.uniform(np.log(1024), np.log(NMAX), n_req)).astype(np.int64)
+        which = rng.integers(0, len(pres), n_req)
+        main = rng.uniform(size=n_req) < 0.5
+        ghost = [int(rng.integers(1, lenses[k].n_paths)) for k in which]
+        srv = lt.Server(n_streams=4, batch_window_us=window_us)
+        tickets = queue.Queue()
+        stalls = [0]
 
-    lat, rays_done, first_t, last_t = [], 0, None, 0.0
-    th = threading.Thread(target=submitter)
-    wall0 = time.perf_counter()
-    th.start()
-    fails = 0
-    while True:
-        item = tickets.get()
-        if item is None:
-            break
-        i, t, slot, ts = item
-        st, info = srv.poll(t, 60_000_000)
-        free.put(slot)
-        if st != lt.OK:
-            fails += 1
-            continue
-        if t_arr[i] >= warm:
-            lat.append(info["latency_us"])
-            rays_done += int(sizes[i])
-    wall = time.perf_counter() - wall0
-    th.join()
-    stats = srv.stats()
-    srv.close()
-    lat = np.array(lat)
-    meas = seconds
-    return {"workload": "8 seeded lenses (S 4..22), Poisson %g req/s, sizes log-uniform [1024, 4194304], "
-                        "main path via resident 32^4x8 map else a uniform ghost traced; %g s after %g s warm-up"
-                        % (rate, seconds, warm),
-            "requests": int(len(lat)), "failed": fails, "offered_req_per_s": rate,
-            "achieved_req_per_s": round(n_req / wall, 1),
-            "p50_latency_ms": round(float(np.percentile(lat, 50)) / 1e3, 4) if lat.size else None,
-            "p99_latency_ms": round(float(np.percentile(lat, 99)) / 1e3, 4) if lat.size else None,
-            "rays_per_s": round(rays_done / meas, 1),
-            "fused_launches": int(stats["fused_launches"]), "fused_requests": int(stats["fused_requests"]),
-            "launches": int(stats["launches"]), "client_slot_stalls": stalls[0],
+        def submitter():
+            t0 = time.perf_counter()
+            for i in range(n_req):
+                while True:
+                    dt = t0 + t_arr[i] - time.perf_counter()
+                    if dt <= 0:
+                        break
+                    time.sleep(dt if dt > 2e-4 else 0)
+                try:
+                    slot = free.get_nowait()
+                except queue.Empty:
+                    stalls[0] += 1
+                    slot = free.get()
+                k, nn = int(which[i]), int(sizes[i])
+                d, o = inputs[k], slots[slot]
+                if main[i]:
+                    t = srv.submit_query(maps[k], d.inp, d.lam, o.out, nn)
+                else:
+                    t = srv.submit_trace(lenses[k], d.inp, d.lam, ghost[i], o.out, nn)
+                tickets.put((i, t, slot))
+            tickets.put(None)
+
+        lat, rays_done, fused_lat = [], 0, 0
+        th = threading.Thread(target=submitter)
+        sampler = ClockSampler(torch.cuda.current_device())
+        sampler.start()
+        wall0 = time.perf_counter()
+        th.start()
+        fails = 0
+        while True:
+            item = tickets.get()
+            if item is None:
+                break
+            i, t, slot = item
+            st, info = srv.poll(t, 60_000_000)
+            free.put(slot)
+            if st != lt.OK:
+                fails += 1
+                continue
+            if t_arr[i] >= warm:
+                lat.append(info["latency_us"])
+                rays_done += int(sizes[i])
+                fused_lat += int(info["fused"] > 1)
+        wall = time.perf_counter() - wall0
+        th.join()
+        smi = sampler.stop()
+        stats = srv.stats()
+        srv.close()
+        lat = np.array(lat)
+        return {"offered_req_per_s": rate, "batch_window_us": window_us,
+                "requests": int(len(lat)), "failed": fails,
+                "achieved_req_per_s": round(n_req / wall, 1),
+                "p50_latency_ms": round(float(np.percentile(lat, 50)) / 1e3, 4) if lat.size else None,
+                "p99_latency_ms": round(float(np.percentile(lat, 99)) / 1e3, 4) if lat.size else None,
+                "rays_per_s": round(rays_done / seconds, 1),
+                "gpu_util_pct_mean": smi.get("gpu_util_pct_mean"),
+                "fused_launches": int(stats["fused_launches"]), "fused_requests": int(stats["fused_requests"]),
+                "fused_fraction": round(int(stats["fused_requests"]) / max(1, int(stats["completed"])), 4),
+                "launches": int(stats["launches"]), "client_slot_stalls": stalls[0]}
+
+    base = run(rate, 0, 0)
+    loaded = run(args.serve_high_rate, 0, 1)
+    windowed = run(args.serve_high_rate, 200, 2)
+    return {"workload": "8 seeded lenses (S 4..22), Poisson arrivals, sizes log-uniform [1024, 4194304], "
+                        "main path via resident 32^4x8 map else a uniform ghost traced; %g s after %g s warm-up "
+                        "per run" % (seconds, warm),
+            **base,
+            "high_load": loaded,
+            "high_load_batch_window": windowed,
             "map_err_vs_fp32_trace": map_err}
 
 
@@ -1094,6 +1170,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-extra", action="store_true", help="headline workload only")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-high-rate", type=float, default=16000.0,
+                    help="offered request rate of the serving workload's loaded runs")
     ap.add_argument("--only", choices=["singlet", "precision", "flares", "mcmc", "serving", "sweep"],
                     help="run one of the other workloads alone and print its object")
     ap.add_argument("--rays", type=int, default=0, help="headline batch size (default 4,194,304)")

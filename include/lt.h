@@ -620,10 +620,14 @@ lt_status lt_mlp_features(const lt_mlp* mlp, const lt_rays_in* in, const float* 
  * A request server over one GPU: callers submit trace / map-query / learned-
  * map requests from any thread and poll tickets.  A native worker thread
  * launches them in arrival order on a few streams:
- *   - continuous batching: the small TRACE requests waiting at the same time
- *     (n <= fuse_max_rays, any lens and path) run as ONE fused launch whose
- *     request table is a kernel parameter; per-ray results are identical to
- *     lt_trace of the same request;
+ *   - continuous batching: the small requests on device buffers waiting at
+ *     the same time (n <= fuse_max_rays) run as one fused launch per kind
+ *     whose request table is a kernel parameter, each block serving one
+ *     request: TRACE requests of any lens and path together; QUERY requests
+ *     of table maps (by query mode and dispersion form) and of
+ *     polynomial-patch maps (LT_QUERY_TABLE, by degree and dispersion form);
+ *     MLP requests by precision.  Per-ray results are identical to the same
+ *     request made alone (lt_trace, lt_query, lt_mlp_query);
  *   - memory admission: a request holds device bytes while in flight (host
  *     staging 49 B/ray; a trace launched on its own also holds the tracer's
  *     queue of surviving rays, 54 B/ray of a wave of at most 2^24 rays); a
@@ -645,9 +649,12 @@ typedef struct {
     size_t mem_budget_bytes;     /* 0: 1 GiB */
     int32_t n_streams;           /* 0: 4 */
     int32_t fuse_max_requests;   /* requests per fused launch, 1..128 (0: 128) */
-    size_t fuse_max_rays;        /* TRACE requests up to this size are fused (0: 65536) */
+    size_t fuse_max_rays;        /* requests up to this size are fused (0: 65536) */
     int32_t inject_fail_every;   /* host-side fault injection for tests: every k-th launch
                                     is not made and its requests fail with LT_ECUDA (0: off) */
+    uint32_t batch_window_us;    /* 0: launch what is waiting at once; > 0: hold the oldest
+                                    waiting request up to this long while more arrive (until
+                                    fuse_max_requests wait), trading latency for fusion */
 } lt_server_opts;
 
 enum {

@@ -517,10 +517,13 @@ map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out,
 // they save): each block classifies and gathers as map_query_kernel does,
 // lists its BOUNDARY and outside rays in shared memory, and traces them
 // itself with survivor compaction (trace_block_states).
+//
+// The body is a device function of the block index within the batch, so that
+// the server's fused launch (serve_query_kernel) runs the same code for each
+// request's blocks.
 template <int MODE, bool CAUCHY>
-__global__ void __launch_bounds__(kQTile)
-map_query_fused_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out, uint32_t n,
-                       unsigned long long* work)
+__device__ __forceinline__ void fused_query_block(const MapDev& M, const RaysInDev& in, const RaysOutDev& out,
+                                                  uint32_t n, uint32_t blk, unsigned long long* work)
 {
     __shared__ GatherItem gq_all[kQWarps][32];
     __shared__ float ob_all[kQWarps][32 * kObStride];
@@ -531,7 +534,7 @@ map_query_fused_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDe
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (t == 0) tcount = 0;
     __syncthreads();
-    const uint32_t r0 = blockIdx.x * kQTile;
+    const uint32_t r0 = blk * kQTile;
     const uint32_t r = r0 + t;
     const Classified c = classify_ray<MODE>(M, in, n, r);
     const unsigned m = __ballot_sync(full, c.tr);
@@ -568,6 +571,32 @@ map_query_fused_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDe
         store_out(out, rr, o, S.of[t] | LT_FLAG_TRACED | ((e & kOutsideBit) ? LT_FLAG_OUTSIDE : 0u));
     }
     warp_add(work, (unsigned)nint);
+}
+
+template <int MODE, bool CAUCHY>
+__global__ void __launch_bounds__(kQTile)
+map_query_fused_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out, uint32_t n,
+                       unsigned long long* work)
+{
+    fused_query_block<MODE, CAUCHY>(M, in, out, n, blockIdx.x, work);
+}
+
+// The server's fused launch of several small table-map queries (each block
+// serves one request; every request's map has the same MODE and dispersion
+// form): the block stages its request's map constants (a device copy of its
+// MapDev) in shared memory and runs the one-kernel query on its rays.
+static_assert(sizeof(MapDev) % 16 == 0, "MapDev is staged in 16-byte words");
+
+template <int MODE, bool CAUCHY>
+__global__ void __launch_bounds__(kQTile)
+serve_query_kernel(const __grid_constant__ ReqTable T, unsigned long long* work)
+{
+    __shared__ MapDev sm;
+    const int k = req_of_block(T, blockIdx.x);
+    const ReqItem& it = T.item[k];
+    stage_words(&sm, it.dev, sizeof(MapDev));
+    __syncthreads();
+    fused_query_block<MODE, CAUCHY>(sm, it.in, it.out, it.n, blockIdx.x - T.block0[k], work);
 }
 
 // The exact tracer over the query's trace queue (see map_query_kernel):
@@ -758,6 +787,23 @@ lt_status launch_query(const lt_map* map, const RaysInDev& in, const RaysOutDev&
     s = launch_query_with(map, in, out, n, mode, trace_queue_at(buf, n), st);
     cudaFreeAsync(buf, st);
     return s;
+}
+
+lt_status launch_fused_table(const ReqTable& T, int mode, bool cauchy, cudaStream_t st)
+{
+    if (T.n_items < 1 || T.n_items > kMaxFuse) return fail(LT_EINVAL, "fused query: %d requests", T.n_items);
+    const unsigned blocks = T.block0[T.n_items];
+    const bool table = mode == LT_QUERY_TABLE;
+    ProfScope prof("serve_query_kernel", st);
+    if (cauchy) {
+        if (table) serve_query_kernel<LT_QUERY_TABLE, true><<<blocks, kQTile, 0, st>>>(T, prof.work());
+        else serve_query_kernel<LT_QUERY_NO_MASK, true><<<blocks, kQTile, 0, st>>>(T, prof.work());
+    } else {
+        if (table) serve_query_kernel<LT_QUERY_TABLE, false><<<blocks, kQTile, 0, st>>>(T, prof.work());
+        else serve_query_kernel<LT_QUERY_NO_MASK, false><<<blocks, kQTile, 0, st>>>(T, prof.work());
+    }
+    LT_CUDA_TRY(cudaGetLastError());
+    return LT_OK;
 }
 
 lt_status launch_map_classify(const uint8_t* corner_bits, const uint32_t* seen, const uint32_t* resmax,

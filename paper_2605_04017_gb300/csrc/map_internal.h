@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "lt_internal.h"
 #include "rays.cuh"
 
@@ -98,6 +100,63 @@ lt_status launch_queue_trace(const lt_map* map, const RaysOutDev& out, uint32_t 
 lt_status launch_map_classify(const uint8_t* corner_bits, const uint32_t* seen, const uint32_t* resmax,
                               float tol, uint32_t* cls, uint32_t NC, unsigned long long* counts,
                               cudaStream_t st);
+
+// A fused serving launch: several small requests of one kind in one grid,
+// each block serving one request.  The table is the kernel parameter (about
+// 16 KB); `dev` points to a device copy of the request's constants (a
+// MapDev, a map's MapDev + PolyDev, or a learned map's constants).
+constexpr int kMaxFuse = 128;
+struct ReqItem {
+    const void* dev;
+    RaysInDev in;
+    RaysOutDev out;
+    uint32_t n;
+};
+struct ReqTable {
+    int n_items;
+    uint32_t block0[kMaxFuse + 1];   // first block of each request; block0[n_items] = the grid
+    ReqItem item[kMaxFuse];
+};
+
+// the request of block b: the last whose first block is <= b
+__device__ __forceinline__ int req_of_block(const ReqTable& T, uint32_t b)
+{
+    int lo = 0, hi = T.n_items - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (T.block0[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// copy `bytes` (a multiple of 16) from global to shared memory with the
+// whole block (the caller synchronises before use)
+__device__ __forceinline__ void stage_words(void* dst, const void* src, size_t bytes)
+{
+    const int4* s = static_cast<const int4*>(src);
+    int4* d = static_cast<int4*>(dst);
+    for (int k = threadIdx.x; k < (int)(bytes / 16); k += blockDim.x) d[k] = __ldg(s + k);
+}
+
+// Fused launches of the server on `st` over the requests of T, whose block0
+// counts blocks of the kind's rays per block (kFusedQueryRays for both map
+// kinds, fused_mlp_rays(precision) for learned maps): table maps
+// (launch_fused_table: every map of the same dispersion form, `cauchy`),
+// polynomial-patch maps (launch_fused_poly: the same degree and dispersion
+// form) and learned maps (launch_fused_mlp: one precision).  Per-ray results
+// equal those of the same request made alone.  LT_EINVAL for an empty or
+// oversized table.
+constexpr uint32_t kFusedQueryRays = kQTile;
+uint32_t fused_mlp_rays(int precision);
+// the device-copy bytes of a request's constants: a map (serve_blob) or a
+// learned map at one precision (mlp_serve_blob; builds its tensor-core
+// weight images first if they are out of date)
+lt_status serve_blob(const lt_map* m, std::vector<unsigned char>& bytes);
+lt_status mlp_serve_blob(const lt_mlp* m, int precision, std::vector<unsigned char>& bytes);
+lt_status launch_fused_table(const ReqTable& T, int mode, bool cauchy, cudaStream_t st);
+lt_status launch_fused_poly(const ReqTable& T, int degree, int mode, bool cauchy, cudaStream_t st);
+lt_status launch_fused_mlp(const ReqTable& T, int precision, cudaStream_t st);
 
 // The polynomial-patch map as its query kernels see it (a __grid_constant__
 // parameter): FP32 constants of the class grid over (r, p, q, w), the patch

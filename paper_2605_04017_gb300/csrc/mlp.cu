@@ -22,6 +22,7 @@
 #include <new>
 #include <vector>
 
+#include "map_internal.h"
 #include "profile.h"
 #include "rays.cuh"
 #include "tracer.cuh"
@@ -565,9 +566,11 @@ __device__ __forceinline__ bool ray_ok(float x, float y, float dx, float dy, flo
 
 constexpr int kMB = 128;
 
+// The FP32 query of block `blk` of a batch (shared by mlp_query_f32_kernel
+// and the server's fused launch, serve_mlp_f32_kernel).
 template <bool USE_CLS>
-__global__ void __launch_bounds__(kMB)
-mlp_query_f32_kernel(const __grid_constant__ MlpDev D, RaysInDev in, RaysOutDev out, uint32_t n)
+__device__ __forceinline__ void f32_query_block(const MlpDev& D, const RaysInDev& in, const RaysOutDev& out,
+                                                uint32_t n, uint32_t blk)
 {
     // the classifier starts on a 16-byte boundary so both networks' weight
     // rows load as float4
@@ -576,7 +579,7 @@ mlp_query_f32_kernel(const __grid_constant__ MlpDev D, RaysInDev in, RaysOutDev 
     for (int i = threadIdx.x; i < Net<true>::NP; i += kMB) W[i] = D.reg[i];
     for (int i = threadIdx.x; i < Net<false>::NP; i += kMB) W[kClsAt + i] = D.cls[i];
     __syncthreads();
-    const uint32_t r = blockIdx.x * kMB + threadIdx.x;
+    const uint32_t r = blk * kMB + threadIdx.x;
     if (r >= n) return;
     const float x = __ldg(in.x + r), y = __ldg(in.y + r), dx = __ldg(in.dx + r),
                 dy = __ldg(in.dy + r), dz = __ldg(in.dz + r), lam = __ldg(in.lam + r);
@@ -608,6 +611,28 @@ mlp_query_f32_kernel(const __grid_constant__ MlpDev D, RaysInDev in, RaysOutDev 
     __stcs(out.dz + r, o[4]);
     __stcs(out.I + r, o[5]);
     out.flags[r] = (uint8_t)f;
+}
+
+template <bool USE_CLS>
+__global__ void __launch_bounds__(kMB)
+mlp_query_f32_kernel(const __grid_constant__ MlpDev D, RaysInDev in, RaysOutDev out, uint32_t n)
+{
+    f32_query_block<USE_CLS>(D, in, out, n, blockIdx.x);
+}
+
+// The server's fused launch of several small FP32 learned-map queries (each
+// block serves one request): the block stages its request's MlpDev (a device
+// copy) in shared memory, then its weights, and answers its rays.
+template <bool USE_CLS>
+__global__ void __launch_bounds__(kMB)
+serve_mlp_f32_kernel(const __grid_constant__ ReqTable T)
+{
+    __shared__ MlpDev sd;
+    const int k = req_of_block(T, blockIdx.x);
+    const ReqItem& it = T.item[k];
+    if (threadIdx.x == 0) sd = *static_cast<const MlpDev*>(it.dev);
+    __syncthreads();
+    f32_query_block<USE_CLS>(sd, it.in, it.out, it.n, blockIdx.x - T.block0[k]);
 }
 
 // ------------------------------------------------------------------ tensor-core query
@@ -774,6 +799,62 @@ static lt_status build_tc_image(lt_mlp* m)
     LT_CUDA_TRY(cudaMemcpy(m->tc_bf16, ib.data(), kImgBytes, cudaMemcpyHostToDevice));
     LT_CUDA_TRY(cudaMemcpy(m->tc_f16, ih.data(), kImgBytes, cudaMemcpyHostToDevice));
     m->frags_stale = false;
+    return LT_OK;
+}
+
+// ------------------------------------------------------------------ fused serving launches
+
+uint32_t fused_mlp_rays(int precision)
+{
+    return precision == LT_MLP_BF16 || precision == LT_MLP_F16 ? (uint32_t)(128 * kTcWG * kTcSlots)
+                                                                : (uint32_t)kMB;
+}
+
+lt_status mlp_serve_blob(const lt_mlp* mc, int precision, std::vector<unsigned char>& b)
+{
+    lt_mlp* m = const_cast<lt_mlp*>(mc);
+    if (precision == LT_MLP_BF16 || precision == LT_MLP_F16) {
+        if (m->frags_stale) {
+            const lt_status s = build_tc_image(m);
+            if (s != LT_OK) return s;
+        }
+        TcServe X{};
+        X.F = m->F;
+        X.B = m->tc_bias;
+        X.img = precision == LT_MLP_BF16 ? m->tc_bf16 : m->tc_f16;
+        X.err = m->tc_err;
+        b.assign(reinterpret_cast<const unsigned char*>(&X), reinterpret_cast<const unsigned char*>(&X) + sizeof X);
+        return LT_OK;
+    }
+    if (precision != LT_MLP_F32 && precision != LT_MLP_F32_NOCLS)
+        return fail(LT_EINVAL, "learned map: unknown precision %d", precision);
+    const MlpDev D{m->F, m->reg, m->cls};
+    b.assign(reinterpret_cast<const unsigned char*>(&D), reinterpret_cast<const unsigned char*>(&D) + sizeof D);
+    return LT_OK;
+}
+
+lt_status launch_fused_mlp(const ReqTable& T, int precision, cudaStream_t st)
+{
+    if (T.n_items < 1 || T.n_items > kMaxFuse) return fail(LT_EINVAL, "fused query: %d requests", T.n_items);
+    const unsigned blocks = T.block0[T.n_items];
+    if (precision == LT_MLP_F32 || precision == LT_MLP_F32_NOCLS) {
+        ProfScope prof("serve_mlp_f32_kernel", st);
+        if (precision == LT_MLP_F32) serve_mlp_f32_kernel<true><<<blocks, kMB, 0, st>>>(T);
+        else serve_mlp_f32_kernel<false><<<blocks, kMB, 0, st>>>(T);
+    } else if (precision == LT_MLP_BF16 || precision == LT_MLP_F16) {
+        const bool bf = precision == LT_MLP_BF16;
+        // as the single query: more than half of an SM's shared memory, so
+        // one CTA (and one TMEM allocation of all 512 columns) per SM
+        const size_t smem = std::max(kTcServeAt + sizeof(TcServe) + 16, (size_t)116 * 1024);
+        const void* k = bf ? (const void*)serve_mlp_tc_kernel<true> : (const void*)serve_mlp_tc_kernel<false>;
+        LT_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ProfScope prof(bf ? "serve_mlp_bf16_kernel" : "serve_mlp_f16_kernel", st);
+        if (bf) serve_mlp_tc_kernel<true><<<blocks, kTcThreads, smem, st>>>(T);
+        else serve_mlp_tc_kernel<false><<<blocks, kTcThreads, smem, st>>>(T);
+    } else {
+        return fail(LT_EINVAL, "fused learned-map query: unknown precision %d", precision);
+    }
+    LT_CUDA_TRY(cudaGetLastError());
     return LT_OK;
 }
 

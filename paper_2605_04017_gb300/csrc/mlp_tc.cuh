@@ -180,14 +180,16 @@ struct TcTile {
     uint32_t r;
 };
 
+// The query of one CTA: CTA `cta` of `ncta` takes tiles (cta * kTcWG + g) *
+// kTcSlots + {0, 1} and every ncta * kTcWG * kTcSlots tiles after them.
+// `bias` holds the TcBias words (a kernel parameter, or a shared-memory copy
+// in the server's fused launch).
 template <bool BF16>
-__global__ void __launch_bounds__(kTcThreads, 1)
-mlp_query_tc_kernel(const __grid_constant__ MlpFrame F, const __grid_constant__ TcBias B,
-                    const unsigned char* __restrict__ gimg, RaysInDev in, RaysOutDev out, uint32_t n,
-                    uint32_t* __restrict__ err)
+__device__ __forceinline__ void tc_query_cta(TcShared& S, const MlpFrame& F, const float* __restrict__ bias,
+                                             const unsigned char* __restrict__ gimg, const RaysInDev& in,
+                                             const RaysOutDev& out, uint32_t n, uint32_t* __restrict__ err,
+                                             uint32_t cta, uint32_t ncta)
 {
-    extern __shared__ __align__(16) unsigned char tc_smem_raw[];
-    TcShared& S = *reinterpret_cast<TcShared*>(tc_smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, g = warp >> 2, row = tid & 127;
     // weights and biases into shared memory
     for (int i = tid; i < kImgBytes / 16; i += kTcThreads)
@@ -245,8 +247,8 @@ mlp_query_tc_kernel(const __grid_constant__ MlpFrame F, const __grid_constant__ 
     };
 
     const uint32_t tiles = (n + 127) / 128;
-    const uint32_t tstep = gridDim.x * kTcWG * kTcSlots;
-    for (uint32_t t0 = (blockIdx.x * kTcWG + g) * kTcSlots; t0 < tiles; t0 += tstep) {
+    const uint32_t tstep = ncta * kTcWG * kTcSlots;
+    for (uint32_t t0 = (cta * kTcWG + g) * kTcSlots; t0 < tiles; t0 += tstep) {
         TcTile T[kTcSlots];
         // layer-0 A operands (features) of both slots, then both layer-0 MMAs
 #pragma unroll
@@ -287,12 +289,12 @@ mlp_query_tc_kernel(const __grid_constant__ MlpFrame F, const __grid_constant__ 
                 parity[sl] ^= 1u;
                 tc_fence_after();
                 if (layer < 5) {
-                    tc_hidden<BF16>(lanes | cD[sl], S.areg[g][sl], row, B.b + kBiasReg + 32 * layer);
-                    if (layer <= 1) tc_hidden<BF16>(lanes | (cD[sl] + 32), S.acls[g][sl], row, B.b + kBiasCls + 32 * layer);
+                    tc_hidden<BF16>(lanes | cD[sl], S.areg[g][sl], row, bias + kBiasReg + 32 * layer);
+                    if (layer <= 1) tc_hidden<BF16>(lanes | (cD[sl] + 32), S.acls[g][sl], row, bias + kBiasCls + 32 * layer);
                     if (layer == 2) {
                         uint32_t v[8];
                         tmem_ld8(lanes | (cD[sl] + 32), v);
-                        T[sl].logit = __uint_as_float(v[0]) + B.b[kBiasClsOut];
+                        T[sl].logit = __uint_as_float(v[0]) + bias[kBiasClsOut];
                     }
                     // this slot's next layer goes to the tensor core while the
                     // warpgroup finishes the other slot
@@ -304,7 +306,7 @@ mlp_query_tc_kernel(const __grid_constant__ MlpFrame F, const __grid_constant__ 
                     uint32_t v[8];
                     tmem_ld8(lanes | cD[sl], v);
 #pragma unroll
-                    for (int q = 0; q < 6; ++q) zr[sl][q] = __uint_as_float(v[q]) + B.b[kBiasRegOut + q];
+                    for (int q = 0; q < 6; ++q) zr[sl][q] = __uint_as_float(v[q]) + bias[kBiasRegOut + q];
                 }
             }
         }
@@ -336,6 +338,45 @@ mlp_query_tc_kernel(const __grid_constant__ MlpFrame F, const __grid_constant__ 
     tc_fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(S.tmem), "r"(kTcCols) : "memory");
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(kTcThreads, 1)
+mlp_query_tc_kernel(const __grid_constant__ MlpFrame F, const __grid_constant__ TcBias B,
+                    const unsigned char* __restrict__ gimg, RaysInDev in, RaysOutDev out, uint32_t n,
+                    uint32_t* __restrict__ err)
+{
+    extern __shared__ __align__(16) unsigned char tc_smem_raw[];
+    TcShared& S = *reinterpret_cast<TcShared*>(tc_smem_raw);
+    tc_query_cta<BF16>(S, F, B.b, gimg, in, out, n, err, blockIdx.x, gridDim.x);
+}
+
+// The constants of one learned map for the server's fused launch (a device
+// copy per map and precision): frame, biases, weight image, wait-error counter.
+struct alignas(16) TcServe {
+    MlpFrame F;
+    TcBias B;
+    const unsigned char* img;
+    uint32_t* err;
+};
+constexpr size_t kTcServeAt = (sizeof(TcShared) + 15) & ~(size_t)15;   // its place after TcShared
+
+// The server's fused launch of several small tensor-core learned-map queries:
+// each CTA serves one request (kTcWG * kTcSlots tiles of it, one pass), with
+// that request's frame and biases staged in shared memory after TcShared.
+template <bool BF16>
+__global__ void __launch_bounds__(kTcThreads, 1)
+serve_mlp_tc_kernel(const __grid_constant__ ReqTable T)
+{
+    extern __shared__ __align__(16) unsigned char tc_smem_raw[];
+    TcShared& S = *reinterpret_cast<TcShared*>(tc_smem_raw);
+    TcServe& X = *reinterpret_cast<TcServe*>(tc_smem_raw + kTcServeAt);
+    const int k = req_of_block(T, blockIdx.x);
+    const ReqItem& it = T.item[k];
+    stage_words(&X, it.dev, sizeof(TcServe));
+    __syncthreads();
+    tc_query_cta<BF16>(S, X.F, X.B.b, X.img, it.in, it.out, it.n, X.err, blockIdx.x - T.block0[k],
+                       T.block0[k + 1] - T.block0[k]);
 }
 
 }  // namespace lt

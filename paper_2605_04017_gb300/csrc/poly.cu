@@ -668,10 +668,12 @@ poly_eval_kernel(const __grid_constant__ PolyDev P, RaysOutDev out, uint32_t n, 
 
 // Small batches: the whole query in one kernel; each block traces its own
 // BOUNDARY and outside rays with survivor compaction (trace_block_states).
+// The body is a device function of the block index within the batch, shared
+// with the server's fused launch (serve_poly_kernel).
 template <int D, int MODE, bool CAUCHY>
-__global__ void __launch_bounds__(kPolyTile)
-poly_query_fused_kernel(const __grid_constant__ MapDev M, const __grid_constant__ PolyDev P, RaysInDev in,
-                        RaysOutDev out, uint32_t n, unsigned long long* work)
+__device__ __forceinline__ void poly_fused_block(const MapDev& M, const PolyDev& P, const RaysInDev& in,
+                                                 const RaysOutDev& out, uint32_t n, uint32_t blk,
+                                                 unsigned long long* work)
 {
     __shared__ TraceSmem<kPolyTile> S;
     __shared__ uint32_t tlist[kPolyTile];
@@ -680,7 +682,7 @@ poly_query_fused_kernel(const __grid_constant__ MapDev M, const __grid_constant_
     const int t = threadIdx.x, lane = t & 31;
     if (t == 0) tcount = 0;
     __syncthreads();
-    const uint32_t r0 = blockIdx.x * kPolyTile;
+    const uint32_t r0 = blk * kPolyTile;
     const uint32_t r = r0 + t;
     PolyRay c;
     poly_answer<D, MODE>(P, in, n, r, c);
@@ -717,6 +719,38 @@ poly_query_fused_kernel(const __grid_constant__ MapDev M, const __grid_constant_
         poly_store(out, rr, o, S.of[t] | LT_FLAG_TRACED | ((e & kOutsideBit) ? LT_FLAG_OUTSIDE : 0u));
     }
     warp_add(work, (unsigned)nint);
+}
+
+template <int D, int MODE, bool CAUCHY>
+__global__ void __launch_bounds__(kPolyTile)
+poly_query_fused_kernel(const __grid_constant__ MapDev M, const __grid_constant__ PolyDev P, RaysInDev in,
+                        RaysOutDev out, uint32_t n, unsigned long long* work)
+{
+    poly_fused_block<D, MODE, CAUCHY>(M, P, in, out, n, blockIdx.x, work);
+}
+
+// The server's fused launch of several small polynomial-patch map queries
+// (each block serves one request; every request's map has the same degree,
+// MODE and dispersion form): the block stages its request's constants (a
+// device copy of the map's MapDev and PolyDev) in shared memory and runs the
+// one-kernel query on its rays.
+struct PolyServe {
+    MapDev M;
+    PolyDev P;
+};
+static_assert(sizeof(PolyServe) % 16 == 0, "PolyServe is staged in 16-byte words");
+static_assert(kPolyTile == (int)kFusedQueryRays, "the server lays out fused blocks of kFusedQueryRays");
+
+template <int D, int MODE, bool CAUCHY>
+__global__ void __launch_bounds__(kPolyTile)
+serve_poly_kernel(const __grid_constant__ ReqTable T, unsigned long long* work)
+{
+    __shared__ PolyServe sm;
+    const int k = req_of_block(T, blockIdx.x);
+    const ReqItem& it = T.item[k];
+    stage_words(&sm, it.dev, sizeof(PolyServe));
+    __syncthreads();
+    poly_fused_block<D, MODE, CAUCHY>(sm.M, sm.P, it.in, it.out, it.n, blockIdx.x - T.block0[k], work);
 }
 
 // ------------------------------------------------------------------ build kernels
@@ -1070,6 +1104,38 @@ lt_status launch_poly_fused(const lt_map* map, const RaysInDev& in, const RaysOu
         const lt_status s = launch_poly_query(map, ia, oa, k, mode, st);
         if (s != LT_OK) return s;
     }
+    return LT_OK;
+}
+
+lt_status serve_blob(const lt_map* m, std::vector<unsigned char>& b)
+{
+    if (m->kind == LT_MAP_KIND_POLY) {
+        PolyServe X{};
+        X.M = m->dev;
+        X.P = m->pdev;
+        b.assign(reinterpret_cast<const unsigned char*>(&X), reinterpret_cast<const unsigned char*>(&X) + sizeof X);
+    } else {
+        b.assign(reinterpret_cast<const unsigned char*>(&m->dev),
+                 reinterpret_cast<const unsigned char*>(&m->dev) + sizeof(MapDev));
+    }
+    return LT_OK;
+}
+
+// The server fuses LT_QUERY_TABLE requests only (LT_QUERY_NO_MASK ones run
+// alone), which keeps the fused kernel to one instantiation per degree and
+// dispersion form.
+lt_status launch_fused_poly(const ReqTable& T, int degree, int mode, bool cauchy, cudaStream_t st)
+{
+    if (T.n_items < 1 || T.n_items > kMaxFuse) return fail(LT_EINVAL, "fused query: %d requests", T.n_items);
+    if (mode != LT_QUERY_TABLE) return fail(LT_EINVAL, "fused polynomial query: mode %d not fused", mode);
+    const unsigned blocks = T.block0[T.n_items];
+    ProfScope prof("serve_poly_kernel", st);
+    unsigned long long* w = prof.work();
+    LT_POLY_DISPATCH(degree, {
+        if (cauchy) serve_poly_kernel<DD, LT_QUERY_TABLE, true><<<blocks, kPolyTile, 0, st>>>(T, w);
+        else serve_poly_kernel<DD, LT_QUERY_TABLE, false><<<blocks, kPolyTile, 0, st>>>(T, w);
+    });
+    LT_CUDA_TRY(cudaGetLastError());
     return LT_OK;
 }
 

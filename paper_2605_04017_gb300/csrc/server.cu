@@ -8,6 +8,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -23,7 +24,6 @@ namespace lt {
 using Clock = std::chrono::steady_clock;
 
 constexpr int kServeBlock = 256;
-constexpr int kMaxFuse = 128;
 
 struct FuseItem {
     const LensDev* L;     // device copy of the request's lens
@@ -98,6 +98,11 @@ struct LensCopy {
     LensDev* dev = nullptr;
 };
 
+struct BlobCopy {
+    std::vector<unsigned char> host;
+    void* dev = nullptr;
+};
+
 struct Done;
 
 }  // namespace lt
@@ -118,6 +123,11 @@ struct lt_server {
     lt_server_stats stats{};
     std::unordered_map<const lt_lens*, lt::LensCopy> lens_cache;   // worker thread only
     std::vector<lt::LensDev*> retired_lens;                         // freed at destroy
+    // device copies of maps' and learned maps' constants for fused launches,
+    // keyed by (object, precision) (worker thread only); stale copies are
+    // kept until destroy, like the lenses'
+    std::map<std::pair<const void*, int>, lt::BlobCopy> blob_cache;
+    std::vector<void*> retired_blobs;
     std::thread worker;
 };
 
@@ -243,10 +253,51 @@ static lt_status launch_staged(const lt_request& r, cudaStream_t st)
     return s;
 }
 
-static bool fusable(const lt_server* s, const lt_request& r)
+// Requests that may share a launch: small requests on device buffers whose
+// kernels are the same instantiation.  *key names that group: traces (any
+// lens, any path), table-map queries by mode and dispersion form,
+// polynomial-patch map queries (LT_QUERY_TABLE only) by degree and
+// dispersion form, learned-map queries by precision.
+static bool fusable(const lt_server* s, const lt_request& r, int* key)
 {
-    return r.kind == LT_REQ_TRACE && !(r.flags & LT_REQ_HOST_BUFFERS) && r.n <= s->o.fuse_max_rays &&
-           s->o.fuse_max_requests > 1;
+    if ((r.flags & LT_REQ_HOST_BUFFERS) || r.n > s->o.fuse_max_rays || s->o.fuse_max_requests < 2) return false;
+    if (r.kind == LT_REQ_TRACE) {
+        *key = 0;
+        return true;
+    }
+    if (r.kind == LT_REQ_QUERY) {
+        if (r.map->kind == LT_MAP_KIND_POLY) {
+            if (r.query_mode != LT_QUERY_TABLE) return false;
+            *key = 2000 + 2 * r.map->pdev.degree + (r.map->cauchy ? 1 : 0);
+        } else {
+            *key = 1000 + 2 * r.query_mode + (r.map->cauchy ? 1 : 0);
+        }
+        return true;
+    }
+    *key = 3000 + r.precision;
+    return true;
+}
+
+// The device copy of a request's map or learned-map constants (made once per
+// object and precision, renewed if the object at that address changed).
+static lt_status blob_on_device(lt_server* s, const lt_request& r, const void** out)
+{
+    std::vector<unsigned char> b;
+    const void* obj = r.kind == LT_REQ_QUERY ? (const void*)r.map : (const void*)r.mlp;
+    const int variant = r.kind == LT_REQ_QUERY ? -1 : r.precision;
+    const lt_status st = r.kind == LT_REQ_QUERY ? serve_blob(r.map, b) : mlp_serve_blob(r.mlp, r.precision, b);
+    if (st != LT_OK) return st;
+    BlobCopy& c = s->blob_cache[std::make_pair(obj, variant)];
+    if (!c.dev || c.host != b) {
+        void* d = nullptr;
+        LT_CUDA_TRY(cudaMalloc(&d, b.size()));
+        LT_CUDA_TRY(cudaMemcpy(d, b.data(), b.size(), cudaMemcpyHostToDevice));
+        if (c.dev) s->retired_blobs.push_back(c.dev);
+        c.dev = d;
+        c.host.swap(b);
+    }
+    *out = c.dev;
+    return LT_OK;
 }
 
 // Finishes one launch: either enqueue the completion host function or, if
@@ -331,6 +382,49 @@ static void launch_fused(lt_server* s, std::vector<Pending>& group)
     group.clear();
 }
 
+// A fused launch of map or learned-map queries (every request of the group
+// has the same fusion key).
+static void launch_fused_queries(lt_server* s, std::vector<Pending>& group)
+{
+    if (group.empty()) return;
+    cudaStream_t st = s->streams[s->next_stream++ % s->streams.size()];
+    const lt_request& r0 = group[0].req;
+    const uint32_t rpb = r0.kind == LT_REQ_QUERY ? kFusedQueryRays : fused_mlp_rays(r0.precision);
+    std::vector<uint64_t> ids;
+    size_t bytes = 0, rays = 0;
+    ReqTable T;
+    T.n_items = 0;
+    uint32_t blocks = 0;
+    lt_status ls = LT_OK;
+    for (Pending& p : group) {
+        ids.push_back(p.id);
+        bytes += p.bytes;
+        rays += p.req.n;
+        const void* dev = nullptr;
+        if (ls == LT_OK) ls = blob_on_device(s, p.req, &dev);
+        if (ls != LT_OK) continue;
+        ReqItem& it = T.item[T.n_items];
+        it.dev = dev;
+        it.in = RaysInDev{p.req.in.x, p.req.in.y, p.req.in.dx, p.req.in.dy, p.req.in.dz, p.req.lambda_nm};
+        it.out = RaysOutDev{p.req.out.x, p.req.out.y, p.req.out.dx, p.req.out.dy, p.req.out.dz, p.req.out.I,
+                            p.req.out.flags};
+        it.n = (uint32_t)p.req.n;
+        T.block0[T.n_items] = blocks;
+        blocks += (uint32_t)((p.req.n + rpb - 1) / rpb);
+        T.n_items++;
+    }
+    T.block0[T.n_items] = blocks;
+    if (ls == LT_OK && injected_failure(s)) ls = fail(LT_ECUDA, "server: injected launch failure");
+    if (ls == LT_OK) {
+        if (r0.kind == LT_REQ_MLP) ls = launch_fused_mlp(T, r0.precision, st);
+        else if (r0.map->kind == LT_MAP_KIND_POLY)
+            ls = launch_fused_poly(T, r0.map->pdev.degree, r0.query_mode, r0.map->cauchy, st);
+        else ls = launch_fused_table(T, r0.query_mode, r0.map->cauchy, st);
+    }
+    finish_launch(s, st, ids, bytes, rays, true, ls);
+    group.clear();
+}
+
 static void launch_one(lt_server* s, Pending& p)
 {
     cudaStream_t st = s->streams[s->next_stream++ % s->streams.size()];
@@ -354,6 +448,14 @@ static void worker_main(lt_server* s)
     while (true) {
         s->cv_work.wait(lk, [&] { return s->stop || !s->pending.empty(); });
         if (s->stop) break;
+        if (s->o.batch_window_us > 0) {
+            // hold the oldest request up to the window while more arrive
+            const Clock::time_point until =
+                s->pending.front().t_submit + std::chrono::microseconds(s->o.batch_window_us);
+            while (!s->stop && (int)s->pending.size() < s->o.fuse_max_requests && Clock::now() < until)
+                s->cv_work.wait_until(lk, until);
+            if (s->stop) break;
+        }
         // admit requests in arrival order while the budget allows; expire the
         // ones past their deadline
         std::vector<Pending> take;
@@ -383,17 +485,27 @@ static void worker_main(lt_server* s)
             continue;
         }
         lk.unlock();
-        std::vector<Pending> group;
+        // small requests of one fusion key share a launch (up to
+        // fuse_max_requests each); the rest launch on their own
+        std::map<int, std::vector<Pending>> groups;
+        auto launch_group = [&](int key, std::vector<Pending>& g) {
+            if (g.size() == 1) launch_one(s, g[0]);
+            else if (key == 0) launch_fused(s, g);
+            else launch_fused_queries(s, g);
+            g.clear();
+        };
         for (Pending& p : take) {
-            if (fusable(s, p.req)) {
-                group.push_back(p);
-                if ((int)group.size() >= s->o.fuse_max_requests) launch_fused(s, group);
+            int key = 0;
+            if (fusable(s, p.req, &key)) {
+                std::vector<Pending>& g = groups[key];
+                g.push_back(p);
+                if ((int)g.size() >= s->o.fuse_max_requests) launch_group(key, g);
             } else {
                 launch_one(s, p);
             }
         }
-        if (group.size() == 1) launch_one(s, group[0]);
-        else launch_fused(s, group);
+        for (auto& kv : groups)
+            if (!kv.second.empty()) launch_group(kv.first, kv.second);
         lk.lock();
     }
 }
@@ -456,6 +568,9 @@ void lt_server_destroy(lt_server* s)
     for (auto& kv : s->lens_cache)
         if (kv.second.dev) cudaFree(kv.second.dev);
     for (LensDev* d : s->retired_lens) cudaFree(d);
+    for (auto& kv : s->blob_cache)
+        if (kv.second.dev) cudaFree(kv.second.dev);
+    for (void* d : s->retired_blobs) cudaFree(d);
     delete s;
 }
 

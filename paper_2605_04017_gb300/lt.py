@@ -810,7 +810,7 @@ OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, ENOTREADY = 0, -1, -2, -3, -4, -5, -
 class c_server_opts(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_size_t), ("n_streams", ctypes.c_int32),
                 ("fuse_max_requests", ctypes.c_int32), ("fuse_max_rays", ctypes.c_size_t),
-                ("inject_fail_every", ctypes.c_int32)]
+                ("inject_fail_every", ctypes.c_int32), ("batch_window_us", ctypes.c_uint32)]
 
 
 class c_request(ctypes.Structure):
@@ -862,9 +862,9 @@ class Server:
     """lt_server: submit trace / query / learned-map requests, poll tickets."""
 
     def __init__(self, mem_budget_bytes=0, n_streams=0, fuse_max_requests=0, fuse_max_rays=0,
-                 inject_fail_every=0):
+                 inject_fail_every=0, batch_window_us=0):
         o = c_server_opts(mem_budget_bytes, n_streams, fuse_max_requests, fuse_max_rays,
-                          inject_fail_every)
+                          inject_fail_every, batch_window_us)
         self.handle = ctypes.c_void_p()
         check(lib().lt_server_create(ctypes.byref(o), ctypes.byref(self.handle)))
 

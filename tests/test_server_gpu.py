@@ -116,6 +116,60 @@ def test_mix_matches_alone(lenses, singlet_map, singlet_mlp):
     srv.close()
 
 
+@pytest.fixture(scope="module")
+def eleven_poly_map(lenses):
+    import math
+    pres, ls = lenses
+    rho = w.eleven_rho(pres[1])
+    smax = math.tan(math.radians(10.0)) * math.sqrt(2.0)
+    return lt.Map.build_poly(ls[1], 0, rho, smax, 3, [4, 4, 2, 1], [8, 8, 8, 4], 5,
+                             fit=batch.DeviceRays(w.entrance_rays(1 << 18, 11, rho)), max_residual_mm=1e-4)
+
+
+def test_fused_every_kind(lenses, singlet_map, singlet_mlp, eleven_poly_map):
+    """With a batching window the server holds waiting requests until 96 are
+    in: the small traces, table-map queries (both query modes),
+    polynomial-patch map queries and learned-map queries of every precision
+    each share launches, and every result equals the request made alone, bit
+    for bit (ragged sizes, several blocks per request, a tail block)."""
+    pres, ls = lenses
+    srv = lt.Server(n_streams=2, fuse_max_requests=96, batch_window_us=2_000_000)
+    rng = np.random.Generator(np.random.PCG64(23))
+    kinds = [(lt.REQ_TRACE, ls[1], 0, pres[1]), (lt.REQ_TRACE, ls[2], 3, pres[2]),
+             (lt.REQ_QUERY, singlet_map, lt.QUERY_TABLE, pres[0]),
+             (lt.REQ_QUERY, singlet_map, lt.QUERY_NO_MASK, pres[0]),
+             (lt.REQ_QUERY, eleven_poly_map, lt.QUERY_TABLE, pres[1])] + \
+        [(lt.REQ_MLP, singlet_mlp, p, pres[0]) for p in range(4)]
+    reqs = []
+    for k in range(96):
+        kind, obj, arg, pr = kinds[k % len(kinds)]
+        n = int(rng.choice([1, 77, 256, 1023, 1025, 4099, 20000]))
+        d = batch.DeviceRays(rays_for(pr, n, 2000 + k))
+        reqs.append((kind, obj, arg, d, batch.DeviceOut(n), n))
+    torch.cuda.synchronize()
+    tickets = []
+    for kind, obj, arg, d, o, n in reqs:
+        if kind == lt.REQ_TRACE:
+            tickets.append(srv.submit_trace(obj, d.inp, d.lam, arg, o.out, n))
+        elif kind == lt.REQ_QUERY:
+            tickets.append(srv.submit_query(obj, d.inp, d.lam, o.out, n, query_mode=arg))
+        else:
+            tickets.append(srv.submit_mlp(obj, d.inp, d.lam, o.out, n, precision=arg))
+    fused = [srv.wait(t)["fused"] for t in tickets]
+    st = srv.stats()
+    print("server stats", st)
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    # every kind ran fused: the 96 requests fill one window, so each of the 8
+    # fusion groups (the two lenses' traces share one) is one launch of all
+    # its requests
+    for (kind, obj, arg, _), f in zip(kinds, fused[:len(kinds)]):
+        assert f > 1, (kind, arg, f)
+    assert st["fused_launches"] == 8 and st["fused_requests"] == 96
+    for kind, obj, arg, d, o, n in reqs:
+        assert same(o.numpy(), alone(kind, obj, d, n, arg)), (kind, n, arg)
+    srv.close()
+
+
 def test_host_buffers(lenses):
     pres, ls = lenses
     srv = lt.Server()
