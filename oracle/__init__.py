@@ -18,6 +18,9 @@ Parity status per function (what pins it; see tests/test_oracle_*.py):
                  aspheres: the zero-asphere sphere, a Cartesian oval's
                  perfect focus, a polynomial surface's hit and normal
   or_map_*       affine-field exactness, node reproduction, brute-force class
+  quantize16     exact round trip of representable values, the half-step
+                 error bound, the exponent's bracket, zeros for invalid
+                 nodes, the quantised query within half a step of the FP64 one
   poly           polynomial-patch map: exact reproduction of degree-<=D fields
                  (and not of degree D + 1), the symmetry reduction's rotation
                  invariance and round trip, unclipped = real lens on valid
@@ -34,6 +37,7 @@ Parity status per function (what pins it; see tests/test_oracle_*.py):
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -366,6 +370,12 @@ class TableMap:
                            _ptr(self.node_valid, _bp), _ptr(self.cell_class, _bp),
                            _ptr(self.cell_maxres, _dp))
 
+    def quantize16(self):
+        """Replace the node values by their 16-bit decoded form (quantize16);
+        returns the six steps."""
+        self.node6, steps = quantize16(self.node6, self.node_valid)
+        return steps
+
     def query(self, rays):
         n = len(rays)
         arrs = [_f32(a) for a in rays.arrays()]
@@ -377,6 +387,28 @@ class TableMap:
                            _ptr(self.cell_class, _bp), n, *[_ptr(a, _fp) for a in arrs],
                            _ptr(out, _dp), _ptr(flags, _bp))
         return out, flags
+
+
+def quantize16(node6: np.ndarray, node_valid: np.ndarray):
+    """The half-size node table (16 bits per output): output k of a node is
+    stored as an integer q in [-32768, 32767] times step_k = 2^(e_k - 15),
+    where 2^e_k is the smallest power of two above the largest |value| of
+    output k over the valid nodes (step 2^-15 if there is none), and
+    q = value / step_k rounded to the nearest integer, ties to even;
+    invalid nodes store 0.  Returns the decoded node values (q * step, FP64)
+    and the six steps.  A power-of-two step makes value / step exact, so the
+    only rounding is the one to an integer."""
+    v = np.asarray(node6, np.float64)
+    ok = np.asarray(node_valid) != 0
+    steps = np.empty(6, np.float64)
+    out = np.zeros_like(v)
+    for k in range(6):
+        m = float(np.abs(v[ok, k]).max()) if ok.any() else 0.0
+        e = math.frexp(m)[1] if m > 0.0 else 0      # 2^(e-1) <= m < 2^e
+        steps[k] = math.ldexp(1.0, e - 15)
+        q = np.clip(np.rint(v[:, k] / steps[k]), -32768, 32767)
+        out[:, k] = np.where(ok, q * steps[k], 0.0)
+    return out, steps
 
 
 def trace_nodes(lens: Lens, path, lattice: Lattice):

@@ -221,3 +221,60 @@ def test_query_one_matches_whole_map(small_map):
         cell = lat.cell_of(ray)
         cls, corner6, cv, mr = oracle.classify_cell(L, (0, 0), lat, cell, fit)
         assert cls == m.cell_class[ids[r]]
+
+
+# ---------------------------------------------------------------- 16-bit node table
+
+def test_quantize16_round_trip_is_exact():
+    """Values that are integer multiples of the chosen step come back
+    unchanged: the step is a power of two, so value / step is exact and the
+    rounding to an integer is the only rounding."""
+    rng = np.random.default_rng(7)
+    q = rng.integers(-32767, 32768, size=(5000, 6))
+    q[0] = 32767            # the largest code sets the exponent: 2^14 <= 32767
+    step = np.array([2.0 ** -10, 2.0 ** -15, 2.0 ** -16, 2.0 ** -3, 2.0 ** 0, 2.0 ** -20])
+    v = q * step
+    valid = np.ones(len(v), np.uint8)
+    dec, steps = oracle.quantize16(v, valid)
+    assert np.array_equal(steps, step)
+    assert np.array_equal(dec, v)
+
+
+def test_quantize16_error_bound_and_exponent():
+    """|decoded - value| <= step / 2, and the step brackets the largest
+    magnitude: 2^14 step <= max |v| < 2^15 step (so every code fits 16 bits);
+    invalid nodes decode to zero whatever they held."""
+    rng = np.random.default_rng(8)
+    v = rng.normal(size=(20000, 6)) * np.array([17.0, 3.3, 0.21, 0.2, 0.97, 0.5])
+    v[:, 4] = np.abs(v[:, 4])
+    valid = (rng.uniform(size=len(v)) < 0.8).astype(np.uint8)
+    dec, steps = oracle.quantize16(v, valid)
+    ok = valid != 0
+    m = np.abs(v[ok]).max(axis=0)
+    assert np.all(2.0 ** 14 * steps <= m) and np.all(m < 2.0 ** 15 * steps)
+    assert np.all(np.abs(dec[ok] - v[ok]) <= steps / 2)
+    assert np.all(dec[~ok] == 0.0)
+    # steps are powers of two
+    assert np.all(np.frexp(steps)[0] == 0.5)
+
+
+def test_quantized_map_query_within_half_a_step(small_map):
+    """Multilinear interpolation is a convex combination of the 32 corners,
+    so the quantised map's interpolated x, y and I stay within half a step of
+    the FP64 map's (direction within a few steps after renormalisation);
+    classes and traced rays are untouched."""
+    L, lat, rays, m = small_map
+    out0, f0 = m.query(rays)
+    mq = oracle.TableMap(L, (0, 0), lat, rays)
+    steps = mq.quantize16()
+    out1, f1 = mq.query(rays)
+    assert np.array_equal(f0, f1)
+    interp = ((f1 & 1) != 0) & ((f1 & 16) == 0)
+    assert interp.sum() > 100
+    d = np.abs(out1[interp] - out0[interp])
+    for k in (0, 1, 5):
+        assert d[:, k].max() <= steps[k] / 2 * (1 + 1e-12)
+    for k in (2, 3, 4):
+        assert d[:, k].max() <= 4 * steps[2:5].max()
+    traced = (f1 & 16) != 0
+    assert np.array_equal(out1[traced], out0[traced])
