@@ -27,15 +27,15 @@ constexpr int kTraceBlock = 256;
 constexpr int kShortPath = 4;
 constexpr size_t kWaveRays = (size_t)1 << 24;   // rays per front/rest pair (queue <= 872 MB)
 
-template <bool CAUCHY>
+template <bool CAUCHY, bool MAIN>
 __global__ void __launch_bounds__(kTraceBlock)
 trace_short_kernel(const __grid_constant__ LensDev L, int pi, int pj, RaysInDev in, RaysOutDev out,
                    uint32_t n, unsigned long long* work)
 {
     __shared__ TraceSmem<kTraceBlock> S;
     const uint32_t r0 = blockIdx.x * kTraceBlock;
-    const int nint = trace_block<CAUCHY, kTraceBlock>(L, pi, pj, in.x, in.y, in.dx, in.dy, in.dz, in.lam,
-                                                      n, r0, S);
+    const int nint = trace_block<CAUCHY, kTraceBlock, MAIN>(L, pi, pj, in.x, in.y, in.dx, in.dy, in.dz, in.lam,
+                                                            n, r0, S);
     __syncthreads();
     const int t = threadIdx.x;
     const uint32_t r = r0 + (uint32_t)t;
@@ -64,7 +64,7 @@ __device__ __forceinline__ void store_result(const RaysOutDev& out, uint32_t r, 
     out.flags[r] = (uint8_t)(done ? st.flags : (st.flags & ~LT_FLAG_VALID));
 }
 
-template <bool CAUCHY>
+template <bool CAUCHY, bool MAIN>
 __global__ void __launch_bounds__(kTraceBlock)
 trace_front_kernel(const __grid_constant__ LensDev L, int pi, int pj, RaysInDev in, RaysOutDev out,
                    uint32_t n, RayQueue Q, unsigned long long* work)
@@ -78,7 +78,7 @@ trace_front_kernel(const __grid_constant__ LensDev L, int pi, int pj, RaysInDev 
         live = trace_init(__ldg(in.x + r), __ldg(in.y + r), __ldg(in.dx + r), __ldg(in.dy + r),
                           __ldg(in.dz + r), __ldg(in.lam + r), st);
         int res = live ? STEP_GO : STEP_DEAD;
-        for (int i = 0; i < kFront && res == STEP_GO; ++i) res = trace_step<CAUCHY>(L, pi, pj, K, st);
+        for (int i = 0; i < kFront && res == STEP_GO; ++i) res = trace_step<CAUCHY, MAIN>(L, pi, pj, K, st);
         if (res != STEP_GO) {
             if (live) nint = st.k + (res == STEP_DONE ? 1 : 0);
             live = false;
@@ -92,7 +92,7 @@ trace_front_kernel(const __grid_constant__ LensDev L, int pi, int pj, RaysInDev 
     warp_add(work, (unsigned)nint);
 }
 
-template <bool CAUCHY>
+template <bool CAUCHY, bool MAIN>
 __global__ void __launch_bounds__(kTraceBlock)
 trace_rest_kernel(const __grid_constant__ LensDev L, int pi, int pj, RayQueue Q, RaysOutDev out,
                   unsigned long long* work)
@@ -106,7 +106,7 @@ trace_rest_kernel(const __grid_constant__ LensDev L, int pi, int pj, RayQueue Q,
         int res;
 #pragma unroll 1
         do {
-            res = trace_step<CAUCHY>(L, pi, pj, K, st);
+            res = trace_step<CAUCHY, MAIN>(L, pi, pj, K, st);
         } while (res == STEP_GO);
         nint += st.k + (res == STEP_DONE ? 1 : 0);
         store_result(out, Q.ray[i], st, res);
@@ -133,7 +133,7 @@ unsigned persistent_blocks(const void* kernel, int block, size_t items, size_t p
 lt_status launch_trace(const lt_lens* L, int pi, int pj, const RaysInDev& in,
                        const RaysOutDev& out, size_t n, cudaStream_t st)
 {
-    const bool cauchy = lens_all_cauchy(L->dev);
+    const bool cauchy = lens_all_cauchy(L->dev), main = pj == 0;
     if (path_length(L->S, pi, pj) <= kShortPath) {
         for (size_t off = 0; off < n; off += ((size_t)1 << 30)) {
             const uint32_t m = (uint32_t)std::min<size_t>(n - off, (size_t)1 << 30);
@@ -142,8 +142,10 @@ lt_status launch_trace(const lt_lens* L, int pi, int pj, const RaysInDev& in,
                          out.I + off, out.flags + off};
             ProfScope prof("trace_kernel", st);
             const unsigned g = (m + kTraceBlock - 1) / kTraceBlock;
-            if (cauchy) trace_short_kernel<true><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, prof.work());
-            else trace_short_kernel<false><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, prof.work());
+            if (cauchy && main) trace_short_kernel<true, true><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, prof.work());
+            else if (cauchy) trace_short_kernel<true, false><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, prof.work());
+            else if (main) trace_short_kernel<false, true><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, prof.work());
+            else trace_short_kernel<false, false><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, prof.work());
             LT_CUDA_TRY(cudaGetLastError());
         }
         return LT_OK;
@@ -164,7 +166,8 @@ lt_status launch_trace(const lt_lens* L, int pi, int pj, const RaysInDev& in,
     Q.ray = reinterpret_cast<uint32_t*>(buf + 12 * cap * 4);
     Q.path = nullptr;
     Q.count = reinterpret_cast<uint32_t*>(buf + 13 * cap * 4);
-    const void* rest = cauchy ? (const void*)trace_rest_kernel<true> : (const void*)trace_rest_kernel<false>;
+    const void* rest = cauchy ? (main ? (const void*)trace_rest_kernel<true, true> : (const void*)trace_rest_kernel<true, false>)
+                              : (main ? (const void*)trace_rest_kernel<false, true> : (const void*)trace_rest_kernel<false, false>);
     for (size_t off = 0; off < n && s == LT_OK; off += wave) {
         const uint32_t m = (uint32_t)std::min(n - off, wave);
         RaysInDev a{in.x + off, in.y + off, in.dx + off, in.dy + off, in.dz + off, in.lam + off};
@@ -176,12 +179,18 @@ lt_status launch_trace(const lt_lens* L, int pi, int pj, const RaysInDev& in,
         const unsigned g = (m + kTraceBlock - 1) / kTraceBlock;
         // the rest kernel's grid: resident blocks, no more than the wave could need
         const unsigned gr = persistent_blocks(rest, kTraceBlock, m, 32);
-        if (cauchy) {
-            trace_front_kernel<true><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, Q, prof.work());
-            trace_rest_kernel<true><<<gr, kTraceBlock, 0, st>>>(L->dev, pi, pj, Q, b, prof.work());
+        if (cauchy && main) {
+            trace_front_kernel<true, true><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, Q, prof.work());
+            trace_rest_kernel<true, true><<<gr, kTraceBlock, 0, st>>>(L->dev, pi, pj, Q, b, prof.work());
+        } else if (cauchy) {
+            trace_front_kernel<true, false><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, Q, prof.work());
+            trace_rest_kernel<true, false><<<gr, kTraceBlock, 0, st>>>(L->dev, pi, pj, Q, b, prof.work());
+        } else if (main) {
+            trace_front_kernel<false, true><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, Q, prof.work());
+            trace_rest_kernel<false, true><<<gr, kTraceBlock, 0, st>>>(L->dev, pi, pj, Q, b, prof.work());
         } else {
-            trace_front_kernel<false><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, Q, prof.work());
-            trace_rest_kernel<false><<<gr, kTraceBlock, 0, st>>>(L->dev, pi, pj, Q, b, prof.work());
+            trace_front_kernel<false, false><<<g, kTraceBlock, 0, st>>>(L->dev, pi, pj, a, b, m, Q, prof.work());
+            trace_rest_kernel<false, false><<<gr, kTraceBlock, 0, st>>>(L->dev, pi, pj, Q, b, prof.work());
         }
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = cuda_fail(e, "lt_trace: launch");
