@@ -588,6 +588,7 @@ def bench_precision(args, stream, flush, peaks):
                         "gradient partials"}
     lo, hi = map_box(rho)
     gmap = lt.Map.build(lens, 0, RES, lo, hi, fit=fit)
+    gmap16 = lt.Map.build(lens, 0, RES, lo, hi, fit=fit, node_format=lt.NODE_S16)
     del fit
     rays = w.precision_rays(args.precision_rays or w.PRECISION_N)
     n = len(rays)
@@ -599,6 +600,7 @@ def bench_precision(args, stream, flush, peaks):
             ("mlp_bf16", lambda: m.query(d.inp, d.lam, o.out, n, lt.MLP_BF16, stream), "mlp_query_bf16_kernel"),
             ("mlp_f16", lambda: m.query(d.inp, d.lam, o.out, n, lt.MLP_F16, stream), "mlp_query_f16_kernel"),
             ("table_f32", lambda: gmap.query(d.inp, d.lam, o.out, n, lt.QUERY_TABLE, stream), None),
+            ("table_s16", lambda: gmap16.query(d.inp, d.lam, o.out, n, lt.QUERY_TABLE, stream), None),
             ("trace_f32", lambda: lt.trace(lens, d.inp, d.lam, 0, o.out, n, stream), None)]
     bf16_peak = None
     if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
@@ -618,14 +620,16 @@ def bench_precision(args, stream, flush, peaks):
                 r["kernel"]["tensor_frac"] = round(tflops / peak, 4)
                 r["kernel"]["tensor_peak"] = "%.1f TFLOP/s of measured (bf16 burst; fp16 taken equal)" % peak
             r["kernel"]["hbm_frac"] = round(49.0 * n / avg_s / 1e9 / peaks["hbm_gbs"], 4)
-        if key == "table_f32" and "map_query_kernel" in prof:
+        if key in ("table_f32", "table_s16") and "map_query_kernel" in prof:
             # as the headline's table map: 24 B in, 25 B out per answered ray, 4 B
-            # per queued ray, the node table (6 floats per node) and classes once
+            # per queued ray, the node table (6 values per node: FP32 or 16-bit)
+            # and classes once
             qf = outs[key][1]
             m_fb = int(((qf & lt.FLAG_TRACED) != 0).sum())
             ms_ = gmap.stats()
+            vb = 24 if key == "table_f32" else 12
             r["kernel"] = kernel_roofline("map_query_kernel", prof, peaks, args.steps,
-                                          units_bytes=n * 24 + (n - m_fb) * 25 + m_fb * 4 + ms_["n_nodes"] * 24 +
+                                          units_bytes=n * 24 + (n - m_fb) * 25 + m_fb * 4 + ms_["n_nodes"] * vb +
                                           (ms_["n_cells"] + 15) // 16 * 4)
         if key == "trace_f32" and "trace_kernel" in prof:
             r["kernel"] = kernel_roofline("trace_kernel", prof, peaks, args.steps,
@@ -964,17 +968,20 @@ def bench_serving(args, peaks, seconds=10.0, warm=1.0, rate=2000.0):
 SWEEP_POLY = [
     # (degree, patches, cells per patch, max_residual_mm): the headline first
     (4, [4, 4, 2, 1], [32, 32, 32, 8], 1e-4),
-    (4, [4, 4, 2, 1], [32, 32, 32, 8], 1e-3),
-    (4, [4, 4, 2, 1], [32, 32, 32, 8], 1e-2),
     (4, [4, 4, 2, 1], [32, 32, 32, 8], 0.0),
     (4, [4, 4, 2, 1], [16, 16, 16, 4], 1e-4),
     (4, [4, 4, 2, 1], [64, 64, 64, 8], 1e-4),
     (5, [4, 4, 2, 1], [32, 32, 32, 8], 1e-4),
     (3, [8, 8, 4, 2], [16, 16, 16, 4], 1e-4),
     (2, [16, 16, 8, 2], [8, 8, 8, 4], 1e-4),
+    (2, [16, 16, 8, 2], [8, 8, 8, 4], 0.0),
+    (2, [4, 4, 2, 1], [32, 32, 32, 8], 1e-4),
+    (2, [4, 4, 2, 1], [32, 32, 32, 8], 0.0),
 ]
-SWEEP_TABLE = [([16, 16, 16, 16, 8], 0.0), ([24, 24, 24, 24, 8], 0.0), ([32, 32, 32, 32, 8], 0.0),
-               ([40, 40, 40, 40, 8], 0.0), ([32, 32, 32, 32, 8], 1e-4)]
+SWEEP_TABLE = [  # (lattice, max_residual_mm, node format: 0 FP32, 1 16-bit)
+    ([16, 16, 16, 16, 8], 0.0, 0), ([24, 24, 24, 24, 8], 0.0, 0), ([32, 32, 32, 32, 8], 0.0, 0),
+    ([40, 40, 40, 40, 8], 0.0, 0), ([32, 32, 32, 32, 8], 1e-4, 0),
+    ([32, 32, 32, 32, 8], 0.0, 1), ([40, 40, 40, 40, 8], 0.0, 1)]
 
 
 def bench_sweep(args, stream, flush, peaks):
@@ -1015,7 +1022,7 @@ def bench_sweep(args, stream, flush, peaks):
                 "validity_mismatches", "validity_mismatches_near_edge")
         row = dict(extra)
         row.update(r)
-        row.update({"map_over_trace": round(r["rays_per_s"] / tr["rays_per_s"], 3), "build_s": round(build_s, 2),
+        row.update({"map_over_trace": round(r["rays_per_s"] / tr["rays_per_s"], 3), "build_s": round(build_s, 4),
                     "traced": round(traced, 4), "answered_by_map": round(e["rays_interpolated"] / n, 4)})
         row.update({k: e[k] for k in keep if k in e})
         return row
@@ -1035,14 +1042,15 @@ def bench_sweep(args, stream, flush, peaks):
                                      "table_bytes": m.stats()["table_bytes"], "patches_fit": ps["patches_fit"]}))
         del m
         torch.cuda.empty_cache()
-    for res, tol in SWEEP_TABLE:
+    for res, tol, fmt in SWEEP_TABLE:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        m = lt.Map.build(lens, 0, res, lo, hi, fit=fit, max_residual_mm=tol)
+        m = lt.Map.build(lens, 0, res, lo, hi, fit=fit, max_residual_mm=tol, node_format=fmt)
         torch.cuda.synchronize()
         bs = time.perf_counter() - t0
         rows.append(measured(m, bs, {"map": "table", "res": res, "max_residual_mm": tol,
-                                     "table_bytes": m.stats()["n_nodes"] * 32}))
+                                     "node_format": "s16" if fmt else "f32",
+                                     "table_bytes": m.stats()["table_bytes"]}))
         del m
         torch.cuda.empty_cache()
     return {"workload": "11-surface lens, %d rays, transmission path; maps fitted from 16,777,216 traced rays; "

@@ -340,7 +340,21 @@ typedef struct {
                                     ray's |interpolated - traced| exit position <= this */
     const float *fit_x, *fit_y, *fit_dx, *fit_dy, *fit_dz, *fit_lambda;  /* device arrays */
     size_t n_fit;                /* fit rays (may be 0: classes from corners alone) */
+    int32_t node_format;         /* LT_NODE_F32 (0) or LT_NODE_S16 */
 } lt_map_opts;
+
+/* Node table formats (Sec. 4.2's regressor as a table).  LT_NODE_F32: six
+ * FP32 outputs per node in a 32-byte record.  LT_NODE_S16: the half-size
+ * table -- output k of a node is a 16-bit integer q times step_k =
+ * 2^(e_k - 15), 2^e_k the smallest power of two above the largest |value| of
+ * output k over the valid nodes, q the FP32 node value times 2^(15 - e_k)
+ * rounded to nearest (ties to even), invalid nodes 0; 16-byte records
+ * (6 x int16 + 4 bytes of padding), so a cell's lambda-adjacent pair of
+ * corners is one 32-byte sector.  A query interpolates the integers in FP32
+ * and multiplies by step_k, so it differs from interpolating the FP32 nodes
+ * by at most step_k / 2 before the direction is renormalised.  The class
+ * certification (max_residual_mm) is made on the FP32 nodes. */
+enum { LT_NODE_F32 = 0, LT_NODE_S16 = 1 };
 
 typedef struct {
     uint64_t n_nodes, n_cells, valid_nodes;
@@ -350,6 +364,8 @@ typedef struct {
     double fit_residual_max_mm;
     uint64_t table_bytes;                    /* device bytes held by the map */
     double build_ms;                         /* wall time of lt_build_map */
+    int32_t node_format;                     /* LT_NODE_* */
+    float node_step[6];                      /* LT_NODE_S16: step_k of each output; else 0 */
 } lt_map_stats;
 
 /* Build a map on the current device: trace the lattice nodes, trace and
@@ -501,7 +517,8 @@ lt_status lt_poly_stats_get(const lt_map* map, lt_poly_stats* out);
 lt_status lt_poly_export(const lt_map* map, double* coef, int32_t* exps, uint8_t* patch_ok);
 
 /* Copy the map to host memory for inspection: node6 (n_nodes x 6 floats; a
- * table map only, NULL for a polynomial-patch map), node_valid (n_nodes
+ * table map only, NULL for a polynomial-patch map; an LT_NODE_S16 table gives
+ * its decoded values q * step), node_valid (n_nodes
  * bytes, 1/0), cell_class (n_cells bytes: 0 INVALID, 1 VALID, 2 BOUNDARY;
  * cells and nodes row-major over the map's axes, the last fastest).  Any
  * pointer may be NULL. */
@@ -509,7 +526,8 @@ lt_status lt_map_export(const lt_map* map, float* node6, uint8_t* node_valid,
                         uint8_t* cell_class);
 
 /* Persist a map (lattice, tables, classes, the lens it was built on) to a
- * file, and load it back onto the current device.  Errors: LT_EIO. */
+ * file, and load it back onto the current device.  Table maps with an
+ * LT_NODE_F32 table only (LT_EINVAL otherwise).  Errors: LT_EIO. */
 lt_status lt_map_save(const lt_map* map, const char* path);
 lt_status lt_map_load(const char* path, lt_map** out);
 

@@ -6,6 +6,7 @@
 // regressor f used only where g = 1.  Here the mask is 2 bits per lattice
 // cell and the regressor a table of traced nodes; cells the mask cannot decide
 // (BOUNDARY) are answered by the tracer itself.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -291,6 +292,56 @@ map_classify_kernel(const uint8_t* __restrict__ corner_bits, const uint32_t* __r
     }
 }
 
+// LT_NODE_S16 build: per output, the largest |value| over the valid nodes
+// (as FP32 bits: non-negative floats order like their bit patterns)
+__global__ void __launch_bounds__(256)
+map_absmax_kernel(const float* __restrict__ node, const uint8_t* __restrict__ node_valid, uint32_t N,
+                  unsigned* __restrict__ mx)
+{
+    float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (uint32_t l = blockIdx.x * 256u + threadIdx.x; l < N; l += gridDim.x * 256u) {
+        if (!node_valid[l]) continue;
+        const float4* p = reinterpret_cast<const float4*>(node + (size_t)l * kNodeFloats);
+        const float4 a = __ldg(p), b = __ldg(p + 1);
+        m[0] = fmaxf(m[0], fabsf(a.x));
+        m[1] = fmaxf(m[1], fabsf(a.y));
+        m[2] = fmaxf(m[2], fabsf(a.z));
+        m[3] = fmaxf(m[3], fabsf(a.w));
+        m[4] = fmaxf(m[4], fabsf(b.x));
+        m[5] = fmaxf(m[5], fabsf(b.y));
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m[k] = fmaxf(m[k], __shfl_xor_sync(0xffffffffu, m[k], o));
+        if ((threadIdx.x & 31) == 0) atomicMax(mx + k, __float_as_uint(m[k]));
+    }
+}
+
+struct QuantInv {
+    float inv[6];   // 2^(15 - e_k): exact powers of two
+};
+
+// LT_NODE_S16 build: each node's six outputs as int16 q = rint(v * inv_k)
+// (ties to even), clamped to the int16 range; invalid nodes all zero.
+__global__ void __launch_bounds__(256)
+map_quantize_kernel(const float* __restrict__ node, const uint8_t* __restrict__ node_valid, uint32_t N,
+                    QuantInv Q, uint4* __restrict__ node16)
+{
+    const uint32_t l = blockIdx.x * 256u + threadIdx.x;
+    if (l >= N) return;
+    const float4* p = reinterpret_cast<const float4*>(node + (size_t)l * kNodeFloats);
+    const float4 a = __ldg(p), b = __ldg(p + 1);
+    const float v[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+    uint32_t h[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const int q = node_valid[l] ? max(-32768, min(32767, __float2int_rn(v[k] * Q.inv[k]))) : 0;
+        h[k] = (uint32_t)q & 0xffffu;
+    }
+    node16[l] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), 0u);
+}
+
 // ------------------------------------------------------------------ query kernels
 
 // Cell of a ray for the query: as cell_of, plus the node index of the cell's
@@ -481,7 +532,101 @@ __device__ __forceinline__ void gather_and_write(const MapDev& M, const RaysOutD
     }
 }
 
-template <int MODE, bool CAUCHY>
+// A 16-bit table entry as FP32: the sign-extended integer added to the bits
+// of 1.5 * 2^23 gives the float 1.5 * 2^23 + q exactly (|q| < 2^22), from
+// which subtracting 1.5 * 2^23 leaves q.
+__device__ __forceinline__ float s16_lo(uint32_t w)
+{
+    return __int_as_float(0x4B400000 + (((int)(w << 16)) >> 16)) - 12582912.0f;
+}
+__device__ __forceinline__ float s16_hi(uint32_t w)
+{
+    return __int_as_float(0x4B400000 + (((int)w) >> 16)) - 12582912.0f;
+}
+
+// gather_and_write for an LT_NODE_S16 table: a pair of lanes per ray (part
+// 0: the lower-lambda node of each of the 16 (x, y, s_x, s_y) corners, part
+// 1: the upper), sixteen rays per round; each lane loads one 16-byte record
+// per corner, weights its six integers by the corner's multilinear factor
+// and sums in FP32; one shuffle adds the pair, and the sums are scaled by the
+// steps.
+__device__ __forceinline__ void gather_and_write_s16(const MapDev& M, const RaysOutDev& out, uint32_t n,
+                                                     uint32_t r, const Classified& c, GatherItem* gq, float* ob)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned mv = __ballot_sync(full, c.ip);
+    const int nv = __popc(mv);
+    if (c.ip) {
+        GatherItem e;
+        e.slot = (uint32_t)lane;
+        e.base = c.base;
+#pragma unroll
+        for (int d = 0; d < 5; ++d) e.f[d] = c.f[d];
+        e.pad = 0.0f;
+        gq[__popc(mv & ((1u << lane) - 1u))] = e;
+    }
+    __syncwarp();
+    const int part = lane & 1;
+    const uint32_t s0 = M.stride[0], s1 = M.stride[1], s2 = M.stride[2], s3 = M.stride[3];
+#pragma unroll 1
+    for (int g0 = 0; g0 < nv; g0 += 16) {
+        const int gi = g0 + (lane >> 1);
+        const bool act = gi < nv;
+        const GatherItem e = gq[min(gi, nv - 1)];
+        const float fl = part ? e.f[4] : 1.0f - e.f[4];
+        const uint4* __restrict__ p = M.node16 + (size_t)e.base + part;
+        float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (act) {
+#pragma unroll
+            for (int qq = 0; qq < 16; ++qq) {
+                const uint32_t off = ((qq & 8) ? s0 : 0u) + ((qq & 4) ? s1 : 0u) + ((qq & 2) ? s2 : 0u) +
+                                     ((qq & 1) ? s3 : 0u);
+                const uint4 v = __ldg(p + off);
+                const float w = (((qq & 8) ? e.f[0] : 1.0f - e.f[0]) * ((qq & 4) ? e.f[1] : 1.0f - e.f[1])) *
+                                (((qq & 2) ? e.f[2] : 1.0f - e.f[2]) * (((qq & 1) ? e.f[3] : 1.0f - e.f[3]) * fl));
+                a[0] = fmaf(w, s16_lo(v.x), a[0]);
+                a[1] = fmaf(w, s16_hi(v.x), a[1]);
+                a[2] = fmaf(w, s16_lo(v.y), a[2]);
+                a[3] = fmaf(w, s16_hi(v.y), a[3]);
+                a[4] = fmaf(w, s16_lo(v.z), a[4]);
+                a[5] = fmaf(w, s16_hi(v.z), a[5]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a[k] += __shfl_xor_sync(full, a[k], 1);
+        if (act && part == 0) {
+            float* o = ob + e.slot * kObStride;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) o[k] = a[k] * M.qstep[k];
+        }
+    }
+    __syncwarp();
+    if (r < n) {
+        float o[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (c.ip) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) o[k] = ob[lane * kObStride + k];
+            const float n2 = fmaf(o[2], o[2], fmaf(o[3], o[3], o[4] * o[4]));
+            float inv = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
+            inv = inv * fmaf(-0.5f * n2, inv * inv, 1.5f);
+            o[2] *= inv;
+            o[3] *= inv;
+            o[4] *= inv;
+        }
+        store_out(out, r, o, c.ip ? LT_FLAG_VALID : 0u);
+    }
+}
+
+template <bool S16>
+__device__ __forceinline__ void gather_any(const MapDev& M, const RaysOutDev& out, uint32_t n, uint32_t r,
+                                           const Classified& c, GatherItem* gq, float* ob)
+{
+    if (S16) gather_and_write_s16(M, out, n, r, c, gq, ob);
+    else gather_and_write(M, out, n, r, c, gq, ob);
+}
+
+template <int MODE, bool CAUCHY, bool S16>
 __global__ void __launch_bounds__(kQTile)
 map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out, uint32_t n, TraceQueue Q)
 {
@@ -509,7 +654,7 @@ map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out,
             Q.tag[k] = c.tag;
         }
     }
-    gather_and_write(M, out, n, r, c, gq_all[warp], ob_all[warp]);
+    gather_any<S16>(M, out, n, r, c, gq_all[warp], ob_all[warp]);
 }
 
 // The whole query in one kernel, for small batches (fewer blocks than the
@@ -521,7 +666,7 @@ map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out,
 // The body is a device function of the block index within the batch, so that
 // the server's fused launch (serve_query_kernel) runs the same code for each
 // request's blocks.
-template <int MODE, bool CAUCHY>
+template <int MODE, bool CAUCHY, bool S16>
 __device__ __forceinline__ void fused_query_block(const MapDev& M, const RaysInDev& in, const RaysOutDev& out,
                                                   uint32_t n, uint32_t blk, unsigned long long* work)
 {
@@ -545,7 +690,7 @@ __device__ __forceinline__ void fused_query_block(const MapDev& M, const RaysInD
         b = __shfl_sync(full, b, leader);
         if (c.tr) tlist[b + __popc(m & ((1u << lane) - 1u))] = (uint32_t)t | (c.tag & kOutsideBit);
     }
-    gather_and_write(M, out, n, r, c, gq_all[warp], ob_all[warp]);
+    gather_any<S16>(M, out, n, r, c, gq_all[warp], ob_all[warp]);
     __syncthreads();
     const uint32_t nt = tcount;
     if (nt == 0) return;
@@ -573,12 +718,12 @@ __device__ __forceinline__ void fused_query_block(const MapDev& M, const RaysInD
     warp_add(work, (unsigned)nint);
 }
 
-template <int MODE, bool CAUCHY>
+template <int MODE, bool CAUCHY, bool S16>
 __global__ void __launch_bounds__(kQTile)
 map_query_fused_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out, uint32_t n,
                        unsigned long long* work)
 {
-    fused_query_block<MODE, CAUCHY>(M, in, out, n, blockIdx.x, work);
+    fused_query_block<MODE, CAUCHY, S16>(M, in, out, n, blockIdx.x, work);
 }
 
 // The server's fused launch of several small table-map queries (each block
@@ -587,7 +732,7 @@ map_query_fused_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDe
 // MapDev) in shared memory and runs the one-kernel query on its rays.
 static_assert(sizeof(MapDev) % 16 == 0, "MapDev is staged in 16-byte words");
 
-template <int MODE, bool CAUCHY>
+template <int MODE, bool CAUCHY, bool S16>
 __global__ void __launch_bounds__(kQTile)
 serve_query_kernel(const __grid_constant__ ReqTable T, unsigned long long* work)
 {
@@ -596,7 +741,7 @@ serve_query_kernel(const __grid_constant__ ReqTable T, unsigned long long* work)
     const ReqItem& it = T.item[k];
     stage_words(&sm, it.dev, sizeof(MapDev));
     __syncthreads();
-    fused_query_block<MODE, CAUCHY>(sm, it.in, it.out, it.n, blockIdx.x - T.block0[k], work);
+    fused_query_block<MODE, CAUCHY, S16>(sm, it.in, it.out, it.n, blockIdx.x - T.block0[k], work);
 }
 
 // The exact tracer over the query's trace queue (see map_query_kernel):
@@ -706,6 +851,25 @@ TraceQueue trace_queue_at(void* scratch, size_t n)
     return Q;
 }
 
+// a query kernel's instantiation by mode, dispersion form and node format
+// (QM, QC, QS in the statement)
+#define LT_QDISPATCH1(QMV, CA, S16, ...)                                                              \
+    do {                                                                                              \
+        constexpr int QM = QMV;                                                                       \
+        if (CA) {                                                                                     \
+            constexpr bool QC = true;                                                                 \
+            if (S16) { constexpr bool QS = true; __VA_ARGS__; } else { constexpr bool QS = false; __VA_ARGS__; } \
+        } else {                                                                                      \
+            constexpr bool QC = false;                                                                \
+            if (S16) { constexpr bool QS = true; __VA_ARGS__; } else { constexpr bool QS = false; __VA_ARGS__; } \
+        }                                                                                             \
+    } while (0)
+#define LT_QDISPATCH(TABLE, CA, S16, ...)                                   \
+    do {                                                                    \
+        if (TABLE) LT_QDISPATCH1(LT_QUERY_TABLE, CA, S16, __VA_ARGS__);     \
+        else LT_QDISPATCH1(LT_QUERY_NO_MASK, CA, S16, __VA_ARGS__);         \
+    } while (0)
+
 // the classify-and-gather kernel on `st` (the queue's counters already cleared)
 static lt_status launch_classify(const lt_map* map, const RaysInDev& in, const RaysOutDev& out, uint32_t n,
                                  int mode, const TraceQueue& Q, cudaStream_t st)
@@ -713,13 +877,8 @@ static lt_status launch_classify(const lt_map* map, const RaysInDev& in, const R
     const unsigned blocks = (n + kQTile - 1) / kQTile;
     const bool table = mode == LT_QUERY_TABLE;
     ProfScope prof("map_query_kernel", st);
-    if (map->cauchy) {
-        if (table) map_query_kernel<LT_QUERY_TABLE, true><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, Q);
-        else map_query_kernel<LT_QUERY_NO_MASK, true><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, Q);
-    } else {
-        if (table) map_query_kernel<LT_QUERY_TABLE, false><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, Q);
-        else map_query_kernel<LT_QUERY_NO_MASK, false><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, Q);
-    }
+    LT_QDISPATCH(table, map->cauchy, map->node_format == LT_NODE_S16,
+                 map_query_kernel<QM, QC, QS><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, Q));
     LT_CUDA_TRY(cudaGetLastError());
     return LT_OK;
 }
@@ -767,13 +926,8 @@ lt_status launch_query(const lt_map* map, const RaysInDev& in, const RaysOutDev&
         const unsigned blocks = (n + kQTile - 1) / kQTile;
         const bool table = mode == LT_QUERY_TABLE;
         ProfScope prof("map_query_fused_kernel", st);
-        if (map->cauchy) {
-            if (table) map_query_fused_kernel<LT_QUERY_TABLE, true><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, prof.work());
-            else map_query_fused_kernel<LT_QUERY_NO_MASK, true><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, prof.work());
-        } else {
-            if (table) map_query_fused_kernel<LT_QUERY_TABLE, false><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, prof.work());
-            else map_query_fused_kernel<LT_QUERY_NO_MASK, false><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, prof.work());
-        }
+        LT_QDISPATCH(table, map->cauchy, map->node_format == LT_NODE_S16,
+                     map_query_fused_kernel<QM, QC, QS><<<blocks, kQTile, 0, st>>>(map->dev, in, out, n, prof.work()));
         LT_CUDA_TRY(cudaGetLastError());
         return LT_OK;
     }
@@ -789,19 +943,13 @@ lt_status launch_query(const lt_map* map, const RaysInDev& in, const RaysOutDev&
     return s;
 }
 
-lt_status launch_fused_table(const ReqTable& T, int mode, bool cauchy, cudaStream_t st)
+lt_status launch_fused_table(const ReqTable& T, int mode, bool cauchy, bool s16, cudaStream_t st)
 {
     if (T.n_items < 1 || T.n_items > kMaxFuse) return fail(LT_EINVAL, "fused query: %d requests", T.n_items);
     const unsigned blocks = T.block0[T.n_items];
     const bool table = mode == LT_QUERY_TABLE;
     ProfScope prof("serve_query_kernel", st);
-    if (cauchy) {
-        if (table) serve_query_kernel<LT_QUERY_TABLE, true><<<blocks, kQTile, 0, st>>>(T, prof.work());
-        else serve_query_kernel<LT_QUERY_NO_MASK, true><<<blocks, kQTile, 0, st>>>(T, prof.work());
-    } else {
-        if (table) serve_query_kernel<LT_QUERY_TABLE, false><<<blocks, kQTile, 0, st>>>(T, prof.work());
-        else serve_query_kernel<LT_QUERY_NO_MASK, false><<<blocks, kQTile, 0, st>>>(T, prof.work());
-    }
+    LT_QDISPATCH(table, cauchy, s16, serve_query_kernel<QM, QC, QS><<<blocks, kQTile, 0, st>>>(T, prof.work()));
     LT_CUDA_TRY(cudaGetLastError());
     return LT_OK;
 }
@@ -815,6 +963,48 @@ lt_status launch_map_classify(const uint8_t* corner_bits, const uint32_t* seen, 
     const uint32_t NW = (NC + 15) / 16;
     map_classify_kernel<<<(NW + 255) / 256, 256, 0, st>>>(corner_bits, seen, resmax, tol_bits, cls, NC, counts);
     LT_CUDA_TRY(cudaGetLastError());
+    return LT_OK;
+}
+
+// LT_NODE_S16: steps from the largest |value| of each output over the valid
+// nodes (step_k = 2^(e_k - 15), 2^(e_k - 1) <= max < 2^e_k), the 16-bit
+// records, then the FP32 table is released.
+lt_status quantize_nodes(lt_map* m, cudaStream_t st)
+{
+    const uint32_t N = (uint32_t)m->n_nodes;
+    unsigned* mx = nullptr;
+    if (cudaMalloc(&mx, 6 * sizeof(unsigned)) != cudaSuccess) return fail(LT_ENOMEM, "lt_build_map: quantisation");
+    unsigned hm[6] = {0, 0, 0, 0, 0, 0};
+    cudaError_t e = cudaMemsetAsync(mx, 0, 6 * sizeof(unsigned), st);
+    if (e == cudaSuccess) {
+        const unsigned g = std::min<unsigned>((N + 255) / 256, 152u * 8u);
+        map_absmax_kernel<<<g, 256, 0, st>>>(m->node, m->node_valid, N, mx);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hm, mx, sizeof hm, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(mx);
+    if (e != cudaSuccess) return cuda_fail(e, "lt_build_map: quantisation");
+    QuantInv Q;
+    for (int k = 0; k < 6; ++k) {
+        float mk;
+        std::memcpy(&mk, &hm[k], 4);
+        int ex = 0;
+        if (mk > 0.0f) std::frexp((double)mk, &ex);
+        m->dev.qstep[k] = (float)std::ldexp(1.0, ex - 15);
+        Q.inv[k] = (float)std::ldexp(1.0, 15 - ex);
+        m->stats.node_step[k] = m->dev.qstep[k];
+    }
+    if (cudaMalloc(&m->node16, (size_t)N * 16) != cudaSuccess) return fail(LT_ENOMEM, "lt_build_map: 16-bit table");
+    map_quantize_kernel<<<(N + 255) / 256, 256, 0, st>>>(m->node, m->node_valid, N, Q, m->node16);
+    LT_CUDA_TRY(cudaGetLastError());
+    LT_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(m->node);
+    m->node = nullptr;
+    m->dev.node = nullptr;
+    m->dev.node16 = m->node16;
+    m->node_format = LT_NODE_S16;
+    m->stats.node_format = LT_NODE_S16;
     return LT_OK;
 }
 
@@ -837,6 +1027,7 @@ using namespace lt;
 lt_map::~lt_map()
 {
     if (node) cudaFree(node);
+    if (node16) cudaFree(node16);
     if (node_valid) cudaFree(node_valid);
     if (cls) cudaFree(cls);
     if (coefg) cudaFree(coefg);
@@ -863,6 +1054,8 @@ lt_status lt_build_map(const lt_lens* lens, const lt_map_opts* o, lt_map** out, 
         NC *= (uint64_t)(o->res[d] - 1);
     }
     if (N * kNodeFloats >= (1ull << 32)) return fail(LT_EINVAL, "lt_build_map: %llu nodes is too many", (unsigned long long)N);
+    if (o->node_format != LT_NODE_F32 && o->node_format != LT_NODE_S16)
+        return fail(LT_EINVAL, "lt_build_map: unknown node format %d", o->node_format);
     if (o->n_fit > 0) {
         const void* ps[] = {o->fit_x, o->fit_y, o->fit_dx, o->fit_dy, o->fit_dz, o->fit_lambda};
         for (const void* p : ps)
@@ -977,6 +1170,13 @@ lt_status lt_build_map(const lt_lens* lens, const lt_map_opts* o, lt_map** out, 
         std::memcpy(&mx, &ha.max_res_bits, 4);
         m->stats.fit_residual_max_mm = mx;
         m->stats.table_bytes = N * kNodeFloats * 4 + N + (uint64_t)NW * 4;
+        m->stats.node_format = LT_NODE_F32;
+        if (o->node_format == LT_NODE_S16) {
+            // the half-size table from the FP32 one, which is then released
+            s = quantize_nodes(m, st);
+            if (s != LT_OK) break;
+            m->stats.table_bytes = N * 16 + N + (uint64_t)NW * 4;
+        }
     } while (0);
     if (corner_bits) cudaFree(corner_bits);
     if (seen) cudaFree(seen);
@@ -1040,9 +1240,16 @@ lt_status lt_map_export(const lt_map* m, float* node6, uint8_t* node_valid, uint
     if (!m) return fail(LT_EINVAL, "lt_map_export: NULL map");
     if (node6 && m->kind != LT_MAP_KIND_TABLE)
         return fail(LT_EINVAL, "lt_map_export: a polynomial-patch map has no node table (node6 must be NULL)");
-    if (node6)
+    if (node6 && m->node_format == LT_NODE_S16) {
+        // the decoded values q * step
+        std::vector<int16_t> q(m->n_nodes * 8);
+        LT_CUDA_TRY(cudaMemcpy(q.data(), m->node16, m->n_nodes * 16, cudaMemcpyDeviceToHost));
+        for (uint64_t l = 0; l < m->n_nodes; ++l)
+            for (int k = 0; k < 6; ++k) node6[l * 6 + k] = (float)q[l * 8 + k] * m->dev.qstep[k];
+    } else if (node6) {
         LT_CUDA_TRY(cudaMemcpy2D(node6, 6 * sizeof(float), m->node, kNodeFloats * sizeof(float),
                                  6 * sizeof(float), m->n_nodes, cudaMemcpyDeviceToHost));
+    }
     if (node_valid) LT_CUDA_TRY(cudaMemcpy(node_valid, m->node_valid, m->n_nodes, cudaMemcpyDeviceToHost));
     if (cell_class) {
         const size_t NW = (m->n_cells + 15) / 16;
@@ -1070,6 +1277,8 @@ lt_status lt_map_save(const lt_map* m, const char* path)
 {
     clear_error();
     if (!m || !path) return fail(LT_EINVAL, "lt_map_save: NULL argument");
+    if (m->kind != LT_MAP_KIND_TABLE || m->node_format != LT_NODE_F32)
+        return fail(LT_EINVAL, "lt_map_save: only table maps with an FP32 node table are saved");
     std::vector<float> node(m->n_nodes * 6);
     std::vector<uint8_t> nv(m->n_nodes);
     const size_t NW = (m->n_cells + 15) / 16;

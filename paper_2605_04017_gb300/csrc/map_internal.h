@@ -23,8 +23,10 @@ struct MapDev {
     int res[5];
     float lo[5], step[5], inv[5], umax[5];
     uint32_t stride[5], cstride[5];
-    const float* node;      // n_nodes x 6 floats
+    const float* node;      // n_nodes x 8 floats (LT_NODE_F32)
     const uint32_t* cls;    // 2 bits per cell
+    const uint4* node16;    // n_nodes x 16-byte records of 6 int16 (LT_NODE_S16)
+    float qstep[6];         // LT_NODE_S16: the value of one integer step per output
 };
 
 // The map query's trace queue: per queued ray its entrance ray (structure of
@@ -142,7 +144,8 @@ __device__ __forceinline__ void stage_words(void* dst, const void* src, size_t b
 // Fused launches of the server on `st` over the requests of T, whose block0
 // counts blocks of the kind's rays per block (kFusedQueryRays for both map
 // kinds, fused_mlp_rays(precision) for learned maps): table maps
-// (launch_fused_table: every map of the same dispersion form, `cauchy`),
+// (launch_fused_table: every map of the same dispersion form, `cauchy`, and
+// node format, `s16`),
 // polynomial-patch maps (launch_fused_poly: the same degree and dispersion
 // form) and learned maps (launch_fused_mlp: one precision).  Per-ray results
 // equal those of the same request made alone.  LT_EINVAL for an empty or
@@ -154,7 +157,7 @@ uint32_t fused_mlp_rays(int precision);
 // weight images first if they are out of date)
 lt_status serve_blob(const lt_map* m, std::vector<unsigned char>& bytes);
 lt_status mlp_serve_blob(const lt_mlp* m, int precision, std::vector<unsigned char>& bytes);
-lt_status launch_fused_table(const ReqTable& T, int mode, bool cauchy, cudaStream_t st);
+lt_status launch_fused_table(const ReqTable& T, int mode, bool cauchy, bool s16, cudaStream_t st);
 lt_status launch_fused_poly(const ReqTable& T, int degree, int mode, bool cauchy, cudaStream_t st);
 lt_status launch_fused_mlp(const ReqTable& T, int precision, cudaStream_t st);
 
@@ -195,6 +198,8 @@ struct lt_map {
     double tol = 0.0;
     uint64_t n_nodes = 0, n_cells = 0;
     float* node = nullptr;
+    uint4* node16 = nullptr;  // LT_NODE_S16 table (node is then released after the build)
+    int node_format = LT_NODE_F32;
     uint8_t* node_valid = nullptr;
     uint32_t* cls = nullptr;
     int device = 0;

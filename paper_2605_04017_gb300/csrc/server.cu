@@ -255,7 +255,7 @@ static lt_status launch_staged(const lt_request& r, cudaStream_t st)
 
 // Requests that may share a launch: small requests on device buffers whose
 // kernels are the same instantiation.  *key names that group: traces (any
-// lens, any path), table-map queries by mode and dispersion form,
+// lens, any path), table-map queries by mode, node format and dispersion form,
 // polynomial-patch map queries (LT_QUERY_TABLE only) by degree and
 // dispersion form, learned-map queries by precision.
 static bool fusable(const lt_server* s, const lt_request& r, int* key)
@@ -270,7 +270,7 @@ static bool fusable(const lt_server* s, const lt_request& r, int* key)
             if (r.query_mode != LT_QUERY_TABLE) return false;
             *key = 2000 + 2 * r.map->pdev.degree + (r.map->cauchy ? 1 : 0);
         } else {
-            *key = 1000 + 2 * r.query_mode + (r.map->cauchy ? 1 : 0);
+            *key = 1000 + 4 * r.query_mode + 2 * (r.map->node_format == LT_NODE_S16 ? 1 : 0) + (r.map->cauchy ? 1 : 0);
         }
         return true;
     }
@@ -419,7 +419,7 @@ static void launch_fused_queries(lt_server* s, std::vector<Pending>& group)
         if (r0.kind == LT_REQ_MLP) ls = launch_fused_mlp(T, r0.precision, st);
         else if (r0.map->kind == LT_MAP_KIND_POLY)
             ls = launch_fused_poly(T, r0.map->pdev.degree, r0.query_mode, r0.map->cauchy, st);
-        else ls = launch_fused_table(T, r0.query_mode, r0.map->cauchy, st);
+        else ls = launch_fused_table(T, r0.query_mode, r0.map->cauchy, r0.map->node_format == LT_NODE_S16, st);
     }
     finish_launch(s, st, ids, bytes, rays, true, ls);
     group.clear();

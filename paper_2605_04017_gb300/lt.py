@@ -384,7 +384,11 @@ class c_map_opts(ctypes.Structure):
                 ("lo", ctypes.c_double * 5), ("hi", ctypes.c_double * 5),
                 ("max_residual_mm", ctypes.c_double),
                 ("fit_x", _fptr), ("fit_y", _fptr), ("fit_dx", _fptr), ("fit_dy", _fptr),
-                ("fit_dz", _fptr), ("fit_lambda", _fptr), ("n_fit", ctypes.c_size_t)]
+                ("fit_dz", _fptr), ("fit_lambda", _fptr), ("n_fit", ctypes.c_size_t),
+                ("node_format", ctypes.c_int32)]
+
+
+NODE_F32, NODE_S16 = 0, 1
 
 
 class c_map_stats(ctypes.Structure):
@@ -393,7 +397,8 @@ class c_map_stats(ctypes.Structure):
                 ("cells_valid", ctypes.c_uint64), ("cells_boundary", ctypes.c_uint64),
                 ("fit_inside", ctypes.c_uint64), ("fit_valid", ctypes.c_uint64),
                 ("fit_residual_rms_mm", ctypes.c_double), ("fit_residual_max_mm", ctypes.c_double),
-                ("table_bytes", ctypes.c_uint64), ("build_ms", ctypes.c_double)]
+                ("table_bytes", ctypes.c_uint64), ("build_ms", ctypes.c_double),
+                ("node_format", ctypes.c_int32), ("node_step", ctypes.c_float * 6)]
 
 
 class c_poly_opts(ctypes.Structure):
@@ -460,10 +465,11 @@ class Map:
 
     @classmethod
     def build(cls, lens: Lens, path_id: int, res, lo, hi, fit=None, max_residual_mm: float = 0.0,
-              stream=None) -> "Map":
-        """fit: a batch.DeviceRays (or None)."""
+              stream=None, node_format: int = NODE_F32) -> "Map":
+        """fit: a batch.DeviceRays (or None); node_format NODE_F32 or NODE_S16."""
         o = c_map_opts()
         o.path_id = path_id
+        o.node_format = node_format
         for d in range(5):
             o.res[d] = int(res[d])
             o.lo[d] = float(lo[d])
@@ -548,7 +554,8 @@ class Map:
     def stats(self) -> dict:
         s = c_map_stats()
         check(lib().lt_map_stats_get(self.handle, ctypes.byref(s)))
-        return {k: getattr(s, k) for k, _ in c_map_stats._fields_}
+        return {k: (list(getattr(s, k)) if isinstance(getattr(s, k), ctypes.Array) else getattr(s, k))
+                for k, _ in c_map_stats._fields_}
 
     def query(self, inp: Sequence, lam, out: Sequence, n: int, mode: int = QUERY_TABLE,
               stream=None) -> None:
