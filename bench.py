@@ -11,7 +11,7 @@ traced fit rays.  One step = the FP32 map query of the whole batch: mask
 lookup, patch polynomial on VALID cells, the exact tracer on BOUNDARY cells.
 `value` is map-query rays/s; the brute-force FP32 trace of the same rays is
 timed the same way ("trace"), and so is the 32^4 x 8 multilinear table map
-("table_map", which misses the 1e-4 mm bound).
+with its 16-bit node table ("table_map", which misses the 1e-4 mm bound).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -294,7 +294,7 @@ def run_ours(args):
     pbuild_s = time.perf_counter() - t0
     pstats, ppoly = pmap.stats(), pmap.poly_stats()
     t0 = time.perf_counter()
-    gmap = lt.Map.build(lens, 0, RES, lo, hi, fit=fit)
+    gmap = lt.Map.build(lens, 0, RES, lo, hi, fit=fit, node_format=lt.NODE_S16)
     build_s = time.perf_counter() - t0
     mstats = gmap.stats()
     del fit
@@ -367,8 +367,9 @@ def run_ours(args):
     s_bytes = n * 24 + (pstats["n_cells"] + 15) // 16 * 4 + n_fb * 28 + n_interp * 32
     e_bytes = n_interp * 32 + coef_bytes + n * 25
     # the table map's classify-and-gather kernel: 24 B in, 25 B out per answered
-    # ray, 4 B per queued ray, the node table (6 floats per node) and classes once
-    table_bytes = mstats["n_nodes"] * 24 + (mstats["n_cells"] + 15) // 16 * 4
+    # ray, 4 B per queued ray, the 16-bit node table (6 values of 2 B per node)
+    # and classes once
+    table_bytes = mstats["n_nodes"] * 12 + (mstats["n_cells"] + 15) // 16 * 4
     m_bytes = n * 24 + (n - m_fb) * 25 + m_fb * 4 + table_bytes
     kernels = {
         "poly_sort_kernel": kernel_roofline("poly_sort_kernel", pq, peaks, args.steps, units_bytes=s_bytes),
@@ -422,13 +423,15 @@ def run_ours(args):
                 "corner_residual_max_mm": ppoly["corner_residual_max_mm"],
                 "table_bytes": pstats["table_bytes"],
                 "err_vs_fp32_trace": map_error(qout, qflags, tout, tflags, lt)},
-        "table_map": {"res": RES, "rays_per_s": round(table_value, 1),
+        "table_map": {"res": RES, "node_format": "s16", "table_bytes": mstats["table_bytes"],
+                      "rays_per_s": round(table_value, 1),
                       "ms_per_step": round(statistics.mean(t_table), 4),
                       "ms_per_step_profiled": round(statistics.mean(tp_table), 4),
                       "map_over_trace": round(table_value / trace_value, 3), "build_s": round(build_s, 3),
                       "traced": round(m_fb / n, 4),
                       "err_vs_fp32_trace": map_error(mout, mflags, tout, tflags, lt),
-                      "note": "multilinear interpolation of traced nodes; outside the 1e-4 mm bound"},
+                      "note": "multilinear interpolation of traced nodes (16-bit node table); outside the "
+                              "1e-4 mm bound"},
         "roofline": roof,
         "kernels": kernels,
         "e2e": {"value": round(n / e2e_s, 1), "unit": "rays/s",
@@ -848,7 +851,7 @@ def bench_serving(args, peaks, seconds=10.0, warm=1.0, rate=2000.0):
         rho = 1.2 * p.surfaces[0].aperture_r
         lo, hi = map_box(rho)
         fit = batch.DeviceRays(w.entrance_rays(1 << 21, w.SEED_BASE + 5 + 7 * k, rho))
-        maps.append(lt.Map.build(lenses[k], 0, RES, lo, hi, fit=fit))
+        maps.append(lt.Map.build(lenses[k], 0, RES, lo, hi, fit=fit, node_format=lt.NODE_S16))
         del fit
         inputs.append(batch.DeviceRays(w.entrance_rays(NMAX, w.SEED_BASE + 5 + 7 * k + 1, rho)))
     # each resident map's error against the FP32 tracer on the first 65,536
@@ -957,7 +960,8 @@ def bench_serving(args, peaks, seconds=10.0, warm=1.0, rate=2000.0):
     loaded = run(args.serve_high_rate, 0, 1)
     windowed = run(args.serve_high_rate, 200, 2)
     return {"workload": "8 seeded lenses (S 4..22), Poisson arrivals, sizes log-uniform [1024, 4194304], "
-                        "main path via resident 32^4x8 map else a uniform ghost traced; %g s after %g s warm-up "
+                        "main path via resident 32^4x8 16-bit table map else a uniform ghost traced; "
+                        "%g s after %g s warm-up "
                         "per run" % (seconds, warm),
             **base,
             "high_load": loaded,
