@@ -55,17 +55,15 @@ FLOPS_PER_INTERACTION = 89
 # dram__bytes_write.sum of one launch / rays in it) with the hash of the
 # kernel sources it was measured on; stale hashes report traffic = null.
 NCU_TRAFFIC = {
-    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, one launch of the
-    # 4,194,304-ray query of the 11-surface lens: 253,664,512 + 102,752,768 bytes
-    # (taken on sources whose kernels are those hashed here: since then only the
-    # host-side checks of lt_map_load have changed)
-    "map_query_kernel": {"bytes_per_ray": 356417280 / 4194304, "hash": "12bf472bbeff6ce1"},
-    "map_trace_kernel": {"bytes_per_ray": 105388544 / 4194304, "hash": "12bf472bbeff6ce1"},
-    # ncu --set full, one launch of each kernel of the polynomial-patch query of
-    # the same 4,194,304 rays: 102,797,056 + 7,808,512 bytes (sort) and
-    # 38,197,504 + 45,350,912 bytes (evaluation)
-    "poly_sort_kernel": {"bytes_per_ray": 110605568 / 4194304, "hash": "b0506b74d7c77f28"},
-    "poly_eval_kernel": {"bytes_per_ray": 83548416 / 4194304, "hash": "b0506b74d7c77f28"},
+    # ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum,
+    # one launch of each kernel of the polynomial-patch query of the headline's
+    # 4,194,304 rays: 102,804,736 + 7,603,200 bytes (sort) and 38,221,824 +
+    # 41,444,864 bytes (evaluation)
+    "poly_sort_kernel": {"bytes_per_ray": 110407936 / 4194304, "hash": "4ff7bae24b2d3eda"},
+    "poly_eval_kernel": {"bytes_per_ray": 79666688 / 4194304, "hash": "4ff7bae24b2d3eda"},
+    # ncu --set full, one launch of the 16-bit table's classify-and-gather kernel
+    # on the same rays: 134,313,984 + 88,311,808 bytes
+    "map_query_kernel": {"bytes_per_ray": 222625792 / 4194304, "hash": "4ff7bae24b2d3eda"},
 }
 
 KERNEL_SRCS = ["paper_2605_04017_gb300/csrc/trace.cu", "paper_2605_04017_gb300/csrc/tracer.cuh",
@@ -384,9 +382,13 @@ def run_ours(args):
     # the roofline reported is that of the step's longer kernel
     dom = max(("poly_sort_kernel", "poly_eval_kernel", "map_trace_kernel"),
               key=lambda k: kernels[k]["kernel_ms_per_step"])
+    # the ncu DRAM bytes of one launch of each kernel, where a capture of the
+    # current kernel sources exists
+    sh = src_hash()
+    for name, kr in kernels.items():
+        tr = NCU_TRAFFIC.get(name)
+        kr["traffic"] = round(tr["bytes_per_ray"] * n) if tr and tr["hash"] == sh else None
     roof = dict(kernels[dom])
-    tr = NCU_TRAFFIC.get(dom)
-    roof["traffic"] = (tr["bytes_per_ray"] * n if tr and tr["hash"] == src_hash() else None)
 
     # end to end through the host-buffer entry point (pinned host memory)
     h = batch.HostRays(rays)
