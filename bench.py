@@ -977,6 +977,10 @@ SWEEP_POLY = [
     (4, [4, 4, 2, 1], [32, 32, 32, 8], 0.0),
     (4, [4, 4, 2, 1], [16, 16, 16, 4], 1e-4),
     (4, [4, 4, 2, 1], [64, 64, 64, 8], 1e-4),
+    (4, [4, 4, 1, 1], [32, 32, 64, 8], 1e-4),
+    (4, [2, 2, 2, 1], [64, 64, 32, 8], 1e-4),
+    (4, [2, 2, 1, 1], [64, 64, 64, 8], 1e-4),
+    (3, [4, 4, 2, 1], [32, 32, 32, 8], 1e-4),
     (5, [4, 4, 2, 1], [32, 32, 32, 8], 1e-4),
     (3, [8, 8, 4, 2], [16, 16, 16, 4], 1e-4),
     (2, [16, 16, 8, 2], [8, 8, 8, 4], 1e-4),
