@@ -181,7 +181,8 @@ struct TcTile {
 };
 
 // The query of one CTA: CTA `cta` of `ncta` takes tiles (cta * kTcWG + g) *
-// kTcSlots + {0, 1} and every ncta * kTcWG * kTcSlots tiles after them.
+// kTcSlots + {0 .. kTcSlots - 1} and every ncta * kTcWG * kTcSlots tiles
+// after them.
 // `bias` holds the TcBias words (a kernel parameter, or a shared-memory copy
 // in the server's fused launch).
 template <bool BF16>
@@ -277,8 +278,8 @@ __device__ __forceinline__ void tc_query_cta(TcShared& S, const MlpFrame& F, con
         tc_fence_before();
         wg_sync(g);
         if (leader) {
-            issue_layer(0, 0);
-            issue_layer(1, 0);
+#pragma unroll
+            for (int sl = 0; sl < kTcSlots; ++sl) issue_layer(sl, 0);
         }
         float zr[kTcSlots][6];
 #pragma unroll
