@@ -204,6 +204,10 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t z)
 }
 
 constexpr int kTB = 128;   // rays per training block
+// Row stride (floats) of the block's activations and deltas in shared memory:
+// odd, so that the weight-gradient products, whose lanes read one column of
+// different rows, hit 32 different banks.
+constexpr int kTS = kTB + 1;
 
 struct TrainBatch {
     const float* X;          // inputs (n x 4)
@@ -228,8 +232,8 @@ mlp_train_kernel(const float* __restrict__ P, TrainBatch tb, MlpFrame F, float* 
     using N = Net<REG>;
     extern __shared__ float sh[];
     float* W = sh;                                    // N::NP
-    float* act = W + ((N::NP + 3) & ~3);              // L layers x 32 x kTB (layer 0 = inputs)
-    float* dl = act + N::L * 32 * kTB;                // 32 x kTB deltas
+    float* act = W + ((N::NP + 3) & ~3);              // L layers x 32 rows of kTS (layer 0 = inputs)
+    float* dl = act + N::L * 32 * kTS;                // 32 rows of kTS deltas
     __shared__ double lsum[kTB / 32];
     for (int i = threadIdx.x; i < N::NP; i += kTB) W[i] = P[i];
     const int j = threadIdx.x;
@@ -248,10 +252,10 @@ mlp_train_kernel(const float* __restrict__ P, TrainBatch tb, MlpFrame F, float* 
     {
         const float4 x = live ? reinterpret_cast<const float4*>(tb.X)[row] : make_float4(0.f, 0.f, 0.f, 0.f);
         a[0] = x.x; a[1] = x.y; a[2] = x.z; a[3] = x.w;
-        act[0 * kTB + j] = a[0];
-        act[1 * kTB + j] = a[1];
-        act[2 * kTB + j] = a[2];
-        act[3 * kTB + j] = a[3];
+        act[0 * kTS + j] = a[0];
+        act[1 * kTS + j] = a[1];
+        act[2 * kTS + j] = a[2];
+        act[3 * kTS + j] = a[3];
     }
     __syncthreads();
     float z[N::NOUT];
@@ -276,7 +280,7 @@ mlp_train_kernel(const float* __restrict__ P, TrainBatch tb, MlpFrame F, float* 
 #pragma unroll
             for (int o = 0; o < 32; ++o) {
                 a[o] = tanhf(t[o]);
-                act[((l + 1) * 32 + o) * kTB + j] = a[o];
+                act[((l + 1) * 32 + o) * kTS + j] = a[o];
             }
         } else {
 #pragma unroll
@@ -347,24 +351,52 @@ mlp_train_kernel(const float* __restrict__ P, TrainBatch tb, MlpFrame F, float* 
         const float* Wl = W + N::woff(l);
 #pragma unroll
         for (int o = 0; o < 32; ++o)
-            if (o < no) dl[o * kTB + j] = d[o];
+            if (o < no) dl[o * kTS + j] = d[o];
         __syncthreads();
-        // dW[o][k] = sum_j d[o][j] a_l[k][j], db[o] = sum_j d[o][j]
-        const float* al = act + l * 32 * kTB;
-        for (int e = j; e < no * (ni + 1); e += kTB) {
-            const int o = e / (ni + 1), k = e % (ni + 1);
-            const float* dr = dl + o * kTB;
-            float s = 0.0f;
-            if (k < ni) {
-                const float* ar = al + k * kTB;
-#pragma unroll 8
-                for (int q = 0; q < kTB; ++q) s = fmaf(dr[q], ar[q], s);
-                Gb[N::woff(l) + o * ni + k] = s;
-            } else {
-#pragma unroll 8
-                for (int q = 0; q < kTB; ++q) s += dr[q];
-                Gb[N::boff(l) + o] = s;
+        // dW[o][k] = sum_j d[o][j] a_l[k][j], db[o] = sum_j d[o][j]: each
+        // thread takes a tile of kGO x kGK weights, so that a delta and an
+        // activation loaded from shared memory serve kGK and kGO products
+        // (every entry still sums over the block's rays in ray order)
+        const float* al = act + l * 32 * kTS;
+        constexpr int kGO = 2, kGK = 4;
+        const int nto = (no + kGO - 1) / kGO, ntk = (ni + kGK - 1) / kGK;
+        for (int tile = j; tile < nto * ntk; tile += kTB) {
+            const int o0 = (tile / ntk) * kGO, k0 = (tile % ntk) * kGK;
+            const float* dr[kGO];
+            const float* ar[kGK];
+#pragma unroll
+            for (int i = 0; i < kGO; ++i) dr[i] = dl + min(o0 + i, no - 1) * kTS;
+#pragma unroll
+            for (int c = 0; c < kGK; ++c) ar[c] = al + min(k0 + c, ni - 1) * kTS;
+            float sacc[kGO][kGK];
+#pragma unroll
+            for (int i = 0; i < kGO; ++i)
+#pragma unroll
+                for (int c = 0; c < kGK; ++c) sacc[i][c] = 0.0f;
+#pragma unroll 4
+            for (int q = 0; q < kTB; ++q) {
+                float dv[kGO], av[kGK];
+#pragma unroll
+                for (int i = 0; i < kGO; ++i) dv[i] = dr[i][q];
+#pragma unroll
+                for (int c = 0; c < kGK; ++c) av[c] = ar[c][q];
+#pragma unroll
+                for (int i = 0; i < kGO; ++i)
+#pragma unroll
+                    for (int c = 0; c < kGK; ++c) sacc[i][c] = fmaf(dv[i], av[c], sacc[i][c]);
             }
+#pragma unroll
+            for (int i = 0; i < kGO; ++i)
+#pragma unroll
+                for (int c = 0; c < kGK; ++c)
+                    if (o0 + i < no && k0 + c < ni) Gb[N::woff(l) + (o0 + i) * ni + (k0 + c)] = sacc[i][c];
+        }
+        for (int o = j; o < no; o += kTB) {
+            const float* dr = dl + o * kTS;
+            float sb = 0.0f;
+#pragma unroll 8
+            for (int q = 0; q < kTB; ++q) sb += dr[q];
+            Gb[N::boff(l) + o] = sb;
         }
         if (l > 0) {
             float nd[32];
@@ -374,7 +406,7 @@ mlp_train_kernel(const float* __restrict__ P, TrainBatch tb, MlpFrame F, float* 
 #pragma unroll
                 for (int o = 0; o < 32; ++o)
                     if (o < no) s = fmaf(Wl[o * ni + k], d[o], s);
-                const float ak = act[(l * 32 + k) * kTB + j];
+                const float ak = act[(l * 32 + k) * kTS + j];
                 nd[k] = s * (1.0f - ak * ak);
             }
 #pragma unroll
@@ -398,6 +430,9 @@ mlp_adam_kernel(float* __restrict__ P, const float* __restrict__ G, int nblocks,
     const int p = blockIdx.x * 256 + threadIdx.x;
     if (p >= np) return;
     double g = 0.0;
+    // unrolled so that sixteen partials' loads are in flight at once (the
+    // sum keeps its order)
+#pragma unroll 16
     for (int b = 0; b < nblocks; ++b) g += (double)G[(size_t)b * np + p];
     const double m = 0.9 * m1[p] + 0.1 * g;
     const double v = 0.999 * m2[p] + 0.001 * g * g;
@@ -575,7 +610,7 @@ lt_status mlp_serve_blob(const lt_mlp* mc, int precision, std::vector<unsigned c
 template <bool REG>
 static size_t train_smem()
 {
-    return (size_t)(((Net<REG>::NP + 3) & ~3) + Net<REG>::L * 32 * kTB + 32 * kTB) * sizeof(float);
+    return (size_t)(((Net<REG>::NP + 3) & ~3) + Net<REG>::L * 32 * kTS + 32 * kTS) * sizeof(float);
 }
 
 // one training step of net REG on the batch; returns the batch-mean loss when `want_loss`
