@@ -250,3 +250,50 @@ def test_binding_constants_match_the_header():
     assert m and lt.NOALLOC_MAX_RAYS == 1 << int(m.group(1))
     m = re.search(r"#define LT_POLY_MAX_DEGREE (\d+)", src)
     assert m and lt.POLY_MAX_DEGREE == int(m.group(1))
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes mirror of a header struct has the C struct's size, and
+    each field the two share by name sits at the same offset: the header is
+    compiled with the host C compiler and asked for sizeof and offsetof."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no host C compiler")
+    pairs = {}
+    for name in dir(lt):
+        cls = getattr(lt, name)
+        if name.startswith("c_") and isinstance(cls, type) and issubclass(cls, ctypes.Structure):
+            cname = "lt_" + name[2:]
+            pairs[cname] = cls
+    header = open(os.path.join(ROOT, "include", "lt.h")).read()
+    pairs = {k: v for k, v in pairs.items() if re.search(r"\}\s*" + k + r"\s*;", header)}
+    assert len(pairs) >= 15
+    renamed = {"inp": "in"}          # the binding's names for C fields that are Python keywords
+    lines = ['#include "lt.h"', "#include <stdio.h>", "#include <stddef.h>", "int main(void) {"]
+    for cname, cls in pairs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {renamed.get(fname, fname)}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    checked = 0
+    for ln in out:
+        parts = ln.split()
+        if len(parts) != 3:
+            continue
+        cname, what, val = parts[0], parts[1], int(parts[2])
+        cls = pairs[cname]
+        if what == "size":
+            assert ctypes.sizeof(cls) == val, (cname, ctypes.sizeof(cls), val)
+        else:
+            assert getattr(cls, what).offset == val, (cname, what, getattr(cls, what).offset, val)
+        checked += 1
+    assert checked == len(pairs) + sum(len(c._fields_) for c in pairs.values())
