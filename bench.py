@@ -359,11 +359,11 @@ def run_ours(args):
     # the sort kernel reads every ray's 24 B and the class table once, and
     # writes a 28 B queue entry per ray it hands to the tracer and a 32 B
     # record per ray the polynomial answers; the evaluation kernel reads
-    # those records and the coefficient table once, and writes every ray's
-    # 25 B row
+    # those records, the coefficient table once and the queue entries, and
+    # writes every ray's 25 B row
     coef_bytes = ppoly["patches"] * ((ppoly["terms"] + 3) // 4) * 80
     s_bytes = n * 24 + (pstats["n_cells"] + 15) // 16 * 4 + n_fb * 28 + n_interp * 32
-    e_bytes = n_interp * 32 + coef_bytes + n * 25
+    e_bytes = n_interp * 32 + coef_bytes + n * 25 + n_fb * 28
     # the table map's classify-and-gather kernel: 24 B in, 25 B out per answered
     # ray, 4 B per queued ray, the 16-bit node table (6 values of 2 B per node)
     # and classes once
@@ -371,17 +371,17 @@ def run_ours(args):
     m_bytes = n * 24 + (n - m_fb) * 25 + m_fb * 4 + table_bytes
     kernels = {
         "poly_sort_kernel": kernel_roofline("poly_sort_kernel", pq, peaks, args.steps, units_bytes=s_bytes),
+        # the evaluation kernel also traces the step's queued rays (its work
+        # counter counts their interactions)
         "poly_eval_kernel": kernel_roofline("poly_eval_kernel", pq, peaks, args.steps, units_bytes=e_bytes),
-        "map_trace_kernel": kernel_roofline("map_trace_kernel", pq, peaks, args.steps,
-                                            flops_per_work=FLOPS_PER_INTERACTION),
         "trace_kernel": kernel_roofline("trace_kernel", pt, peaks, args.steps,
                                         flops_per_work=FLOPS_PER_INTERACTION),
         "map_query_kernel": kernel_roofline("map_query_kernel", pm, peaks, args.steps, units_bytes=m_bytes),
     }
-    kernels["map_trace_kernel"]["traced_rays_per_step"] = n_fb
+    kernels["poly_eval_kernel"]["traced_rays_per_step"] = n_fb
+    kernels["poly_eval_kernel"]["traced_interactions_per_step"] = int(pq["poly_eval_kernel"][2] / args.steps)
     # the roofline reported is that of the step's longer kernel
-    dom = max(("poly_sort_kernel", "poly_eval_kernel", "map_trace_kernel"),
-              key=lambda k: kernels[k]["kernel_ms_per_step"])
+    dom = max(("poly_sort_kernel", "poly_eval_kernel"), key=lambda k: kernels[k]["kernel_ms_per_step"])
     # the ncu DRAM bytes of one launch of each kernel, where a capture of the
     # current kernel sources exists
     sh = src_hash()

@@ -35,7 +35,7 @@ struct MapDev {
 // appending to segment b % kQSegs, so that the appends' atomics spread over
 // kQSegs counters in separate 128-byte lines instead of one hot address:
 // count[s * kQCountStride] counts segment s, count[kQSegs * kQCountStride]
-// the 128-ray chunks the tracer has taken.
+// the chunks the tracer has taken.
 constexpr int kQSegs = 64;
 constexpr int kQCountStride = 32;
 constexpr size_t kQHeaderBytes = (kQSegs + 1) * kQCountStride * 4 + 128;   // 8,448 bytes
@@ -58,16 +58,18 @@ constexpr size_t query_scratch_bytes(size_t n) { return kQHeaderBytes + 7 * 4 * 
 // 32 bytes) in the tile's region, sorted by patch with every patch's run
 // padded to an even length (so that record pairs share a patch), and the
 // tile's padded count.  A tile's region holds kSortTileRays + P records for
-// a map of P patches.
+// a map of P patches.  Per tile, a bit per ray marks the rays handed to the
+// trace queue (their rows are written by the tracer, not the evaluation).
 constexpr size_t kSortTileRays = 1024;
 constexpr size_t query_tiles(size_t n) { return (n + kSortTileRays - 1) / kSortTileRays; }
 constexpr size_t poly_scratch_bytes(size_t n, size_t patches)
 {
-    return query_scratch_bytes(n) + query_tiles(n) * ((kSortTileRays + patches) * 32 + 4) + 256;
+    return query_scratch_bytes(n) + query_tiles(n) * ((kSortTileRays + patches) * 32 + 4 + kSortTileRays / 8) + 256;
 }
 struct PolyScratch {
     float4* rec;          // query_tiles(n) x (kSortTileRays + patches) x 2 float4
     uint32_t* tile_nv;    // query_tiles(n)
+    uint32_t* traced;     // query_tiles(n) x kSortTileRays / 32 words: the rays queued for the tracer
     uint32_t stride;      // records per tile region
 };
 // the records and counts after the queue of n rays in `scratch` (poly_scratch_bytes(n, patches))

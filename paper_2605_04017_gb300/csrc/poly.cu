@@ -418,8 +418,8 @@ poly_query_kernel(const __grid_constant__ PolyDev P, RaysInDev in, RaysOutDev ou
     if (r < n) poly_store(out, r, c.o, c.ip ? LT_FLAG_VALID : 0u);
 }
 
-// Large batches, maps of at most kSortMaxPatches patches, run as three
-// kernels: classify-and-sort, evaluate, and the queue's tracer.
+// Large batches, maps of at most kSortMaxPatches patches, run as two
+// kernels: classify-and-sort, then evaluate-and-trace.
 //
 // poly_sort_kernel takes a tile of kSortTile rays per block:
 //  A. classifies them (coalesced loads that bypass L1, four rounds of 256
@@ -432,7 +432,7 @@ poly_query_kernel(const __grid_constant__ PolyDev P, RaysInDev in, RaysOutDev ou
 //     (c, s), a word holding its mirror and patch, its index in the tile: 32
 //     bytes, one sector -- to its sorted slot of the tile's region, every
 //     patch's run padded to even length, and the count goes to the tile's
-//     counter.
+//     counter; a bit per queued ray goes to the tile's traced mask.
 // Round j of tile b appends to queue segment (4 b + j) % kQSegs: the same
 // segment a 256-ray block of the same rays would use, so the queue's
 // capacity rule (query_segcap) holds.
@@ -443,8 +443,11 @@ poly_query_kernel(const __grid_constant__ PolyDev P, RaysInDev in, RaysOutDev ou
 // evaluates the tile's records in sorted order (coalesced reads; adjacent
 // records mostly share a patch, so a coefficient load is one or two
 // shared-memory addresses for the whole warp); stages the tile's rows in
-// shared memory (zeros for every other ray: a placeholder the queue's
-// tracer overwrites for a queued ray); and stores the rows coalesced.
+// shared memory (zeros for the INVALID rays); and stores every row but the
+// queued rays'.  A block whose tiles are done takes chunks of the trace
+// queue from a counter and traces them with the block tracer, writing those
+// rows: the queue's tracing overlaps the other blocks' evaluation instead of
+// following it as a third kernel.
 constexpr int kSortThreads = 256;
 constexpr int kSortRounds = 4;
 constexpr int kSortTile = kSortThreads * kSortRounds;
@@ -529,6 +532,8 @@ poly_sort_kernel(const __grid_constant__ PolyDev P, RaysInDev in, uint32_t n, Tr
             else tr = k != LT_CELL_INVALID;
         }
         mq[j] = __ballot_sync(full, tr);
+        // the tile's traced-ray bits: word j * 8 + warp holds rays j * 256 + warp * 32 + lane
+        if (lane == 0) R.traced[(size_t)blockIdx.x * (kSortTile / 32) + j * (kSortThreads / 32) + (t >> 5)] = mq[j];
     }
     uint32_t qb[kSortRounds];
 #pragma unroll
@@ -596,13 +601,26 @@ poly_sort_kernel(const __grid_constant__ PolyDev P, RaysInDev in, uint32_t n, Tr
         }
 }
 
-template <int D>
+// The shared memory of poly_eval_kernel's two phases: a tile's staged rows
+// while it evaluates, the block tracer's states once it traces.
+union EvalSmem {
+    struct {
+        float ob[6][kSortTile];
+        uint8_t of[kSortTile];
+    } e;
+    TraceSmem<kEvalThreads> t;
+};
+
+template <int D, bool CAUCHY>
 __global__ void __launch_bounds__(kEvalThreads)
-poly_eval_kernel(const __grid_constant__ PolyDev P, RaysOutDev out, uint32_t n, PolyScratch R, uint32_t ntiles)
+poly_eval_kernel(const __grid_constant__ PolyDev P, const __grid_constant__ MapDev M, RaysOutDev out, uint32_t n,
+                 PolyScratch R, uint32_t ntiles, TraceQueue Q, unsigned long long* work)
 {
     extern __shared__ float4 smc[];                 // the coefficient table
-    __shared__ float ob[6][kSortTile];              // the tile's rows
-    __shared__ uint8_t of[kSortTile];
+    __shared__ EvalSmem U;
+    __shared__ uint32_t tmask[kSortTile / 32];      // the tile's traced rays
+    __shared__ uint32_t cnt[kQSegs], cum[kQSegs + 1];
+    __shared__ uint32_t chunk, cseg;
     const int t = threadIdx.x;
     const int ntab = P.n_patches * poly_groups(D) * 5;
     for (int i = t; i < ntab; i += kEvalThreads) {
@@ -610,19 +628,21 @@ poly_eval_kernel(const __grid_constant__ PolyDev P, RaysOutDev out, uint32_t n, 
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(P.cg + i));
     }
     asm volatile("cp.async.commit_group;");
-    // the sort kernel's records are read only after it has completed
+    // the sort kernel's records and queue are read only after it has completed
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
+    // phase 1: the tiles of this block
 #pragma unroll 1
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint32_t r0 = tile * kSortTile;
-        const uint32_t cnt = min((uint32_t)kSortTile, n - r0);
+        const uint32_t cnt_t = min((uint32_t)kSortTile, n - r0);
         for (uint32_t l = (uint32_t)t; l < (uint32_t)kSortTile; l += kEvalThreads) {
 #pragma unroll
-            for (int q = 0; q < 6; ++q) ob[q][l] = 0.0f;
-            of[l] = 0;
+            for (int q = 0; q < 6; ++q) U.e.ob[q][l] = 0.0f;
+            U.e.of[l] = 0;
         }
+        if (t < kSortTile / 32) tmask[t] = R.traced[(size_t)tile * (kSortTile / 32) + t];
         __syncthreads();
         const uint32_t nv = R.tile_nv[tile];
         const float4* rec = R.rec + (size_t)tile * R.stride * 2;
@@ -641,29 +661,84 @@ poly_eval_kernel(const __grid_constant__ PolyDev P, RaysOutDev out, uint32_t n, 
             uint32_t l = __float_as_uint(b0.w);
             poly_unreduce(acc[0], b0.x, b0.y, (w0 & 0x80000000u) ? -1.0f : 1.0f, o);
 #pragma unroll
-            for (int q = 0; q < 6; ++q) ob[q][l] = o[q];
-            of[l] = LT_FLAG_VALID;
+            for (int q = 0; q < 6; ++q) U.e.ob[q][l] = o[q];
+            U.e.of[l] = LT_FLAG_VALID;
             l = __float_as_uint(b1.w);
             if (l != kNoRay) {
                 poly_unreduce(acc[1], b1.x, b1.y, (w1 & 0x80000000u) ? -1.0f : 1.0f, o);
 #pragma unroll
-                for (int q = 0; q < 6; ++q) ob[q][l] = o[q];
-                of[l] = LT_FLAG_VALID;
+                for (int q = 0; q < 6; ++q) U.e.ob[q][l] = o[q];
+                U.e.of[l] = LT_FLAG_VALID;
             }
         }
         __syncthreads();
-        for (uint32_t l = (uint32_t)t; l < cnt; l += kEvalThreads) {
+        // every row but the queued rays', which the tracer writes
+        for (uint32_t l = (uint32_t)t; l < cnt_t; l += kEvalThreads) {
+            if ((tmask[l >> 5] >> (l & 31u)) & 1u) continue;
             const uint32_t r = r0 + l;
-            __stcs(out.x + r, ob[0][l]);
-            __stcs(out.y + r, ob[1][l]);
-            __stcs(out.dx + r, ob[2][l]);
-            __stcs(out.dy + r, ob[3][l]);
-            __stcs(out.dz + r, ob[4][l]);
-            __stcs(out.I + r, ob[5][l]);
-            out.flags[r] = of[l];
+            __stcs(out.x + r, U.e.ob[0][l]);
+            __stcs(out.y + r, U.e.ob[1][l]);
+            __stcs(out.dx + r, U.e.ob[2][l]);
+            __stcs(out.dy + r, U.e.ob[3][l]);
+            __stcs(out.dz + r, U.e.ob[4][l]);
+            __stcs(out.I + r, U.e.ob[5][l]);
+            out.flags[r] = U.e.of[l];
         }
         __syncthreads();
     }
+    // phase 2: the trace queue, kEvalThreads-ray chunks of its segments taken
+    // from a counter until none is left (chunk c: segment s with cum[s] <= c <
+    // cum[s + 1]), started by each block when its tiles are done
+    if (t < kQSegs) cnt[t] = Q.count[t * kQCountStride];
+    __syncthreads();
+    if (t == 0) {
+        uint32_t c = 0;
+        for (int sg = 0; sg < kQSegs; ++sg) {
+            cum[sg] = c;
+            c += (cnt[sg] + kEvalThreads - 1) / kEvalThreads;
+        }
+        cum[kQSegs] = c;
+    }
+    __syncthreads();
+    const uint32_t nchunks = cum[kQSegs];
+    TraceSmem<kEvalThreads>& S = U.t;
+    int nint = 0;
+#pragma unroll 1
+    while (true) {
+        if (t == 0) {
+            const uint32_t c = atomicAdd(Q.count + kQSegs * kQCountStride, 1u);
+            int sg = 0;
+            while (sg < kQSegs - 1 && cum[sg + 1] <= c) ++sg;
+            chunk = c;
+            cseg = (uint32_t)sg;
+        }
+        __syncthreads();
+        if (chunk >= nchunks) break;
+        const uint32_t sg = cseg;
+        const uint32_t i = (chunk - cum[sg]) * (uint32_t)kEvalThreads + (uint32_t)t;   // entry within the segment
+        const bool have = i < cnt[sg];
+        const uint32_t k = sg * Q.segcap + i;
+        uint32_t e = 0;
+        RayState st;
+        bool live = false;
+        S.of[t] = 0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) S.ob[q][t] = 0.0f;
+        if (have) {
+            e = Q.tag[k];
+            live = trace_init(Q.x[k], Q.y[k], Q.dx[k], Q.dy[k], Q.dz[k], Q.lam[k], st);
+            if (!live) S.of[t] = (uint8_t)st.flags;
+        }
+        nint += trace_block_states<CAUCHY, kEvalThreads>(M.L, M.pi, M.pj, live, st, S);
+        __syncthreads();
+        if (have) {
+            const uint32_t r = e & ~kOutsideBit;
+            const float o[6] = {S.ob[0][t], S.ob[1][t], S.ob[2][t], S.ob[3][t], S.ob[4][t], S.ob[5][t]};
+            poly_store(out, r, o, S.of[t] | LT_FLAG_TRACED | ((e & kOutsideBit) ? LT_FLAG_OUTSIDE : 0u));
+        }
+        __syncthreads();
+    }
+    warp_add(work, (unsigned)nint);
 }
 
 // Small batches: the whole query in one kernel; each block traces its own
@@ -1091,6 +1166,7 @@ PolyScratch poly_scratch_at(void* scratch, size_t n, size_t patches)
     R.stride = (uint32_t)(kSortTileRays + patches);
     R.rec = reinterpret_cast<float4*>(p);
     R.tile_nv = reinterpret_cast<uint32_t*>(p + query_tiles(n) * R.stride * 32);
+    R.traced = R.tile_nv + query_tiles(n);
     return R;
 }
 
@@ -1193,8 +1269,10 @@ lt_status launch_poly_query(const lt_map* map, const RaysInDev& in, const RaysOu
             attr[0].val.programmaticStreamSerializationAllowed = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
+            unsigned long long* w = prof.work();
+            const bool ca = map->cauchy;
             LT_POLY_DISPATCH(D, {
-                const void* kf = (const void*)poly_eval_kernel<DD>;
+                const void* kf = ca ? (const void*)poly_eval_kernel<DD, true> : (const void*)poly_eval_kernel<DD, false>;
                 e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab);
                 if (e == cudaSuccess) {
                     int per_sm = 0, sms = 0, dev = 0;
@@ -1202,10 +1280,13 @@ lt_status launch_poly_query(const lt_map* map, const RaysInDev& in, const RaysOu
                     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
                     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, kEvalThreads, tab);
                     cfg.gridDim = dim3(std::max(1u, std::min(sb, (unsigned)(std::max(per_sm, 1) * sms))));
-                    e = cudaLaunchKernelEx(&cfg, poly_eval_kernel<DD>, map->pdev, out, n, R, sb);
+                    if (ca) e = cudaLaunchKernelEx(&cfg, poly_eval_kernel<DD, true>, map->pdev, map->dev, out, n, R, sb, Q, w);
+                    else e = cudaLaunchKernelEx(&cfg, poly_eval_kernel<DD, false>, map->pdev, map->dev, out, n, R, sb, Q, w);
                 }
             });
             if (e != cudaSuccess) { s = cuda_fail(e, "lt_query: launch"); break; }
+            // the evaluation kernel also traced the queue
+            break;
         } else {
             ProfScope prof("poly_query_kernel", st);
             LT_POLY_DISPATCH(D, {
