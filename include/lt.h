@@ -387,12 +387,16 @@ enum {
 };
 
 /* Query the map for n rays (device arrays, as lt_trace): the factorised
- * lookup of Sec. 4.2 (Eq. 11).  A first kernel classifies every ray,
- * answers INVALID cells, interpolates VALID cells and queues BOUNDARY cells
- * and rays outside the box; a second traces the queue exactly (those rays
- * carry LT_FLAG_TRACED) and writes their results.  The queue (28 bytes per
- * ray) comes from the library's stream-ordered memory pool, which keeps
- * freed blocks for reuse, so steady-state calls do not reach cudaMalloc.
+ * lookup of Sec. 4.2 (Eq. 11).  A table map: a first kernel classifies every
+ * ray, answers INVALID cells, interpolates VALID cells and queues BOUNDARY
+ * cells and rays outside the box; a second traces the queue exactly (those
+ * rays carry LT_FLAG_TRACED) and writes their results.  A polynomial-patch
+ * map: the first kernel classifies, queues and sorts the answered rays by
+ * patch; the second evaluates their polynomials and then traces the queue.
+ * The queue (28 bytes per ray; with a polynomial-patch map also a 32-byte
+ * record per answered ray) comes from the library's stream-ordered memory
+ * pool, which keeps freed blocks for reuse, so steady-state calls do not
+ * reach cudaMalloc.
  * Batches of at most 2^18 rays run as one kernel whose blocks trace their
  * own queued rays (no queue, no pool); the results are the same either way.
  * Errors as lt_trace; LT_ENOMEM if the queue cannot be had; LT_EINVAL if the
