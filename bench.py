@@ -57,13 +57,14 @@ FLOPS_PER_INTERACTION = 89
 NCU_TRAFFIC = {
     # ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum,
     # one launch of each kernel of the polynomial-patch query of the headline's
-    # 4,194,304 rays: 102,804,736 + 7,603,200 bytes (sort) and 38,221,824 +
-    # 41,444,864 bytes (evaluation)
-    "poly_sort_kernel": {"bytes_per_ray": 110407936 / 4194304, "hash": "4ff7bae24b2d3eda"},
-    "poly_eval_kernel": {"bytes_per_ray": 79666688 / 4194304, "hash": "4ff7bae24b2d3eda"},
+    # 4,194,304 rays: 102,802,176 + 7,534,592 bytes (sort) and 46,543,104 +
+    # 53,741,312 bytes (evaluation and the queue's trace)
+    "poly_sort_kernel": {"bytes_per_ray": 110336768 / 4194304, "hash": "3ec37e83f4b75ef7"},
+    "poly_eval_kernel": {"bytes_per_ray": 100284416 / 4194304, "hash": "3ec37e83f4b75ef7"},
     # ncu --set full, one launch of the 16-bit table's classify-and-gather kernel
-    # on the same rays: 134,313,984 + 88,311,808 bytes
-    "map_query_kernel": {"bytes_per_ray": 222625792 / 4194304, "hash": "4ff7bae24b2d3eda"},
+    # on the same rays: 134,313,984 + 88,311,808 bytes (its source has not
+    # changed since)
+    "map_query_kernel": {"bytes_per_ray": 222625792 / 4194304, "hash": "3ec37e83f4b75ef7"},
 }
 
 KERNEL_SRCS = ["paper_2605_04017_gb300/csrc/trace.cu", "paper_2605_04017_gb300/csrc/tracer.cuh",
