@@ -518,7 +518,12 @@ def bench_singlet(args, stream, flush, peaks):
     d = batch.DeviceRays(rays)
     lo, hi = map_box(w.SINGLET_RHO)
     gmap = lt.Map.build(lens, 0, RES, lo, hi, fit=d)
+    gmap16 = lt.Map.build(lens, 0, RES, lo, hi, fit=d, node_format=lt.NODE_S16)
     oq, ot = batch.DeviceOut(n), batch.DeviceOut(n)
+    q16, pq16 = time_kernel(lambda: gmap16.query(d.inp, d.lam, oq.out, n, lt.QUERY_TABLE, stream), "q16", args,
+                            flush, stream, n, lt)
+    torch.cuda.synchronize()
+    q16o, q16f = oq.numpy()
     q, pq = time_kernel(lambda: gmap.query(d.inp, d.lam, oq.out, n, lt.QUERY_TABLE, stream), "q", args, flush,
                         stream, n, lt)
     t, pt = time_kernel(lambda: lt.trace(lens, d.inp, d.lam, 0, ot.out, n, stream), "t", args, flush, stream, n,
@@ -533,8 +538,14 @@ def bench_singlet(args, stream, flush, peaks):
                                   units_bytes=n * 49 + n_interp * 32 * 24)
     q["kernel"]["note"] = "algorithmic bytes: 49 B per ray + 768 B of corner gathers per interpolated ray"
     t["kernel"] = kernel_roofline("trace_kernel", pt, peaks, args.steps, flops_per_work=FLOPS_PER_INTERACTION)
+    n16 = int((((q16f & lt.FLAG_VALID) != 0) & ((q16f & lt.FLAG_TRACED) == 0)).sum())
+    q16["kernel"] = kernel_roofline("map_query_fused_kernel", pq16, peaks, args.steps,
+                                    units_bytes=n * 49 + n16 * 32 * 12)
+    q16["kernel"]["note"] = "algorithmic bytes: 49 B per ray + 384 B of 16-bit corner gathers per interpolated ray"
+    q16["map_err_vs_fp32_trace"] = pos_err(q16o, q16f, to, tf, lt.FLAG_VALID)
     return {"workload": "2-surface singlet (R +-50 mm, t 5 mm, a 10 mm), 65,536 rays, map 32^4x8 fitted on them",
-            "query": q, "trace": t, "map_err_vs_fp32_trace": pos_err(qo, qf, to, tf, lt.FLAG_VALID)}
+            "query": q, "query_s16": q16, "trace": t,
+            "map_err_vs_fp32_trace": pos_err(qo, qf, to, tf, lt.FLAG_VALID)}
 
 
 def bench_precision(args, stream, flush, peaks):
