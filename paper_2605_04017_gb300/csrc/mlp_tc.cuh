@@ -1,9 +1,12 @@
 // Learned-map query on the 5th-generation tensor cores (tcgen05, TMEM).
 //
-// One CTA of four warpgroups per SM.  A warpgroup works on two 128-ray tiles
-// at once (slots 0 and 1) and alternates between them: while the tensor core
-// runs one slot's layer, the warpgroup's threads finish the other slot's
-// previous layer, so the MMA latency hides behind the epilogue.  Per slot:
+// One CTA of eight warpgroups per SM (1,024 threads), each with one 128-ray
+// tile in flight (a slot): while the tensor core runs one warpgroup's layer,
+// the other warpgroups run their epilogues, so the MMA latency hides behind
+// them.  The epilogues are the critical path, so the CTA takes as many warps
+// as the register file and TMEM allow (64 registers a thread, 8 x 64 TMEM
+// columns); the code also runs with several slots per warpgroup, which
+// alternate within it (4 x 2 and 2 x 4 were measured slower).  Per slot:
 //   TMEM cols 0..63 of the slot: accumulators D (layer 0: regressor 0..31,
 //     classifier 32..63; later layers the same split)
 //   shared memory: the A operand of the regressor's next layer (K = 32,
@@ -25,10 +28,10 @@
 
 namespace lt {
 
-constexpr int kTcWG = 4;                    // warpgroups per CTA
+constexpr int kTcWG = 8;                    // warpgroups per CTA
 constexpr int kTcThreads = 128 * kTcWG;
 constexpr int kTcCols = 512;                // TMEM columns allocated per CTA (64 per slot)
-constexpr int kTcSlots = 2;                 // tiles in flight per warpgroup
+constexpr int kTcSlots = 1;                 // tiles in flight per warpgroup
 constexpr int kAbytes = 8192;               // one A operand: 128 rows x 32 x 16 bits
 constexpr uint32_t kTcWaitPolls = 1u << 17; // bounded mbarrier wait (x up to 1 us each)
 
