@@ -137,7 +137,7 @@ paths_front_kernel(const __grid_constant__ LensDev L, const __grid_constant__ Pa
         }
     }
     emit(valid, p, r, st);
-    queue_push(Q, live, st, r, (uint16_t)p);
+    queue_push<kPathsBlock>(Q, live, st, r, (uint16_t)p);
     warp_add(work, (unsigned)nint);
 }
 

@@ -16,7 +16,7 @@ constexpr int kTraceBlock = 256;
 // running to its longest ray with most lanes idle.
 //  - trace_front_kernel: one thread per ray through the first kFront
 //    interactions; finished rays are written at once (survivors' rows get a
-//    placeholder), survivors' states go to a queue (warp-aggregated appends,
+//    placeholder), survivors' states go to a queue (block-aggregated appends,
 //    structure of arrays).
 //  - trace_rest_kernel: a persistent grid traces the queue to the end with
 //    every lane busy and writes each result at its ray's index.
@@ -88,7 +88,7 @@ trace_front_kernel(const __grid_constant__ LensDev L, int pi, int pj, RaysInDev 
         // sectors, which L2 takes without merging partial lines.
         store_result(out, r, st, live ? STEP_DEAD : res);
     }
-    queue_push(Q, live, st, r, 0);
+    queue_push<kTraceBlock>(Q, live, st, r, 0);
     warp_add(work, (unsigned)nint);
 }
 
