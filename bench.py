@@ -51,28 +51,31 @@ POLY = {"degree": 4, "patches": [4, 4, 2, 1], "cells": [32, 32, 32, 8], "samples
 # FMA as 2; the output plane and stop tests are folded into the same unit.
 FLOPS_PER_INTERACTION = 89
 
+# Sources a kernel's code comes from: the file that holds it and the headers
+# it includes.
+_CSRC = "paper_2605_04017_gb300/csrc/"
+_HDRS = [_CSRC + f for f in ("lt_internal.h", "map_internal.h", "rays.cuh", "tracer.cuh", "profile.h")] + \
+    ["include/lt.h"]
+POLY_SRCS = [_CSRC + "poly.cu"] + _HDRS
+MAP_SRCS = [_CSRC + "map.cu"] + _HDRS
+
 # ncu DRAM traffic per ray of each kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch / rays in it) with the hash of the
-# kernel sources it was measured on; stale hashes report traffic = null.
+# kernel's sources it was measured on; stale hashes report traffic = null.
 NCU_TRAFFIC = {
     # ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum,
     # one launch of each kernel of the polynomial-patch query of the headline's
-    # 4,194,304 rays: 102,802,176 + 7,534,592 bytes (sort) and 46,543,104 +
-    # 53,741,312 bytes (evaluation and the queue's trace)
-    "poly_sort_kernel": {"bytes_per_ray": 110336768 / 4194304, "hash": "3ec37e83f4b75ef7"},
-    "poly_eval_kernel": {"bytes_per_ray": 100284416 / 4194304, "hash": "3ec37e83f4b75ef7"},
-    # ncu --set full, one launch of the 16-bit table's classify-and-gather kernel
-    # on the same rays: 134,313,984 + 88,311,808 bytes (its source has not
-    # changed since)
-    "map_query_kernel": {"bytes_per_ray": 222625792 / 4194304, "hash": "3ec37e83f4b75ef7"},
+    # 4,194,304 rays: 102,819,840 + 7,987,712 bytes (sort) and 46,514,176 +
+    # 53,522,176 bytes (evaluation and the queue's trace)
+    "poly_sort_kernel": {"bytes_per_ray": 110807552 / 4194304, "srcs": POLY_SRCS, "hash": "008163db491015c1"},
+    "poly_eval_kernel": {"bytes_per_ray": 100036352 / 4194304, "srcs": POLY_SRCS, "hash": "008163db491015c1"},
+    # the same metrics, one launch of the 16-bit table's classify-and-gather
+    # kernel on the same rays: 134,233,856 + 88,113,920 bytes
+    "map_query_kernel": {"bytes_per_ray": 222347776 / 4194304, "srcs": MAP_SRCS, "hash": "87578288f784c1e2"},
 }
 
-KERNEL_SRCS = ["paper_2605_04017_gb300/csrc/trace.cu", "paper_2605_04017_gb300/csrc/tracer.cuh",
-               "paper_2605_04017_gb300/csrc/map.cu", "paper_2605_04017_gb300/csrc/lt_internal.h",
-               "paper_2605_04017_gb300/csrc/map_internal.h", "paper_2605_04017_gb300/csrc/poly.cu"]
 
-
-def src_hash(files=KERNEL_SRCS):
+def src_hash(files):
     h = hashlib.sha256()
     for f in files:
         with open(os.path.join(ROOT, f), "rb") as fh:
@@ -385,10 +388,9 @@ def run_ours(args):
     dom = max(("poly_sort_kernel", "poly_eval_kernel"), key=lambda k: kernels[k]["kernel_ms_per_step"])
     # the ncu DRAM bytes of one launch of each kernel, where a capture of the
     # current kernel sources exists
-    sh = src_hash()
     for name, kr in kernels.items():
         tr = NCU_TRAFFIC.get(name)
-        kr["traffic"] = round(tr["bytes_per_ray"] * n) if tr and tr["hash"] == sh else None
+        kr["traffic"] = round(tr["bytes_per_ray"] * n) if tr and tr["hash"] == src_hash(tr["srcs"]) else None
     roof = dict(kernels[dom])
 
     # end to end through the host-buffer entry point (pinned host memory)

@@ -657,6 +657,48 @@ map_query_kernel(const __grid_constant__ MapDev M, RaysInDev in, RaysOutDev out,
     gather_any<S16>(M, out, n, r, c, gq_all[warp], ob_all[warp]);
 }
 
+// The one-kernel query's trace of its block's listed BOUNDARY and outside
+// rays (tlist: the ray's slot in the block | the outside bit), with survivor
+// compaction in S.
+template <bool CAUCHY>
+__device__ __forceinline__ void fused_trace_listed(const MapDev& M, const RaysInDev& in, const RaysOutDev& out,
+                                                   uint32_t r0, uint32_t nt, const uint32_t* tlist,
+                                                   TraceSmem<kQTile>& S, unsigned long long* work)
+{
+    const int t = threadIdx.x;
+    // trace the listed rays, thread k taking entry k
+    RayState st;
+    bool live = false;
+    uint32_t e = 0;
+    S.of[t] = 0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) S.ob[q][t] = 0.0f;
+    if ((uint32_t)t < nt) {
+        e = tlist[t];
+        const uint32_t rr = r0 + (e & ~kOutsideBit);
+        live = trace_init(__ldg(in.x + rr), __ldg(in.y + rr), __ldg(in.dx + rr), __ldg(in.dy + rr),
+                          __ldg(in.dz + rr), __ldg(in.lam + rr), st);
+        if (!live) S.of[t] = (uint8_t)st.flags;
+    }
+    const int nint = trace_block_states<CAUCHY, kQTile>(M.L, M.pi, M.pj, live, st, S);
+    __syncthreads();
+    if ((uint32_t)t < nt) {
+        const uint32_t rr = r0 + (e & ~kOutsideBit);
+        const float o[6] = {S.ob[0][t], S.ob[1][t], S.ob[2][t], S.ob[3][t], S.ob[4][t], S.ob[5][t]};
+        store_out(out, rr, o, S.of[t] | LT_FLAG_TRACED | ((e & kOutsideBit) ? LT_FLAG_OUTSIDE : 0u));
+    }
+    warp_add(work, (unsigned)nint);
+}
+
+// the same, as a call (its own register allocation)
+template <bool CAUCHY>
+__device__ __noinline__ void fused_trace_listed_call(const MapDev& M, const RaysInDev& in, const RaysOutDev& out,
+                                                     uint32_t r0, uint32_t nt, const uint32_t* tlist,
+                                                     TraceSmem<kQTile>& S, unsigned long long* work)
+{
+    fused_trace_listed<CAUCHY>(M, in, out, r0, nt, tlist, S, work);
+}
+
 // The whole query in one kernel, for small batches (fewer blocks than the
 // GPU holds at once, where the second launch and its queue cost more than
 // they save): each block classifies and gathers as map_query_kernel does,
@@ -694,28 +736,13 @@ __device__ __forceinline__ void fused_query_block(const MapDev& M, const RaysInD
     __syncthreads();
     const uint32_t nt = tcount;
     if (nt == 0) return;
-    // trace the listed rays, thread k taking entry k
-    RayState st;
-    bool live = false;
-    uint32_t e = 0;
-    S.of[t] = 0;
-#pragma unroll
-    for (int q = 0; q < 6; ++q) S.ob[q][t] = 0.0f;
-    if ((uint32_t)t < nt) {
-        e = tlist[t];
-        const uint32_t rr = r0 + (e & ~kOutsideBit);
-        live = trace_init(__ldg(in.x + rr), __ldg(in.y + rr), __ldg(in.dx + rr), __ldg(in.dy + rr),
-                          __ldg(in.dz + rr), __ldg(in.lam + rr), st);
-        if (!live) S.of[t] = (uint8_t)st.flags;
-    }
-    const int nint = trace_block_states<CAUCHY, kQTile>(M.L, M.pi, M.pj, live, st, S);
-    __syncthreads();
-    if ((uint32_t)t < nt) {
-        const uint32_t rr = r0 + (e & ~kOutsideBit);
-        const float o[6] = {S.ob[0][t], S.ob[1][t], S.ob[2][t], S.ob[3][t], S.ob[4][t], S.ob[5][t]};
-        store_out(out, rr, o, S.of[t] | LT_FLAG_TRACED | ((e & kOutsideBit) ? LT_FLAG_OUTSIDE : 0u));
-    }
-    warp_add(work, (unsigned)nint);
+    // The FP32-node instantiation calls the tracer out of line: inlined, the
+    // compiler gives the whole kernel 48 registers and the quad gather loses
+    // loads in flight (65,536 singlet rays: 0.041 against 0.034 ms out of
+    // line).  The 16-bit gather is faster with the tracer inlined (0.023
+    // against 0.029 ms).
+    if (S16) fused_trace_listed<CAUCHY>(M, in, out, r0, nt, tlist, S, work);
+    else fused_trace_listed_call<CAUCHY>(M, in, out, r0, nt, tlist, S, work);
 }
 
 template <int MODE, bool CAUCHY, bool S16>
