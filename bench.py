@@ -65,13 +65,13 @@ MAP_SRCS = [_CSRC + "map.cu"] + _HDRS
 NCU_TRAFFIC = {
     # ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum,
     # one launch of each kernel of the polynomial-patch query of the headline's
-    # 4,194,304 rays: 102,819,840 + 7,987,712 bytes (sort) and 46,514,176 +
-    # 53,522,176 bytes (evaluation and the queue's trace)
-    "poly_sort_kernel": {"bytes_per_ray": 110807552 / 4194304, "srcs": POLY_SRCS, "hash": "008163db491015c1"},
-    "poly_eval_kernel": {"bytes_per_ray": 100036352 / 4194304, "srcs": POLY_SRCS, "hash": "008163db491015c1"},
+    # 4,194,304 rays: 102,805,760 + 7,710,464 bytes (sort) and 46,535,680 +
+    # 53,677,824 bytes (evaluation and the queue's trace)
+    "poly_sort_kernel": {"bytes_per_ray": 110516224 / 4194304, "srcs": POLY_SRCS, "hash": "a98669c5dc0a7af3"},
+    "poly_eval_kernel": {"bytes_per_ray": 100213504 / 4194304, "srcs": POLY_SRCS, "hash": "a98669c5dc0a7af3"},
     # the same metrics, one launch of the 16-bit table's classify-and-gather
-    # kernel on the same rays: 134,233,856 + 88,113,920 bytes
-    "map_query_kernel": {"bytes_per_ray": 222347776 / 4194304, "srcs": MAP_SRCS, "hash": "87578288f784c1e2"},
+    # kernel on the same rays: 134,202,368 + 88,067,584 bytes
+    "map_query_kernel": {"bytes_per_ray": 222269952 / 4194304, "srcs": MAP_SRCS, "hash": "27a803adcc21d91c"},
 }
 
 

@@ -201,6 +201,22 @@ lt_status lt_trace(const lt_lens* lens, const lt_rays_in* in, const float* lambd
 lt_status lt_trace_host(const lt_lens* lens, const lt_rays_in* in, const float* lambda_nm,
                         int32_t path_id, const lt_rays_out* out, size_t n);
 
+/* The tracer's own FP32 reciprocal and square root, element by element, so
+ * that their accuracy can be checked against correctly rounded results.
+ * Every interaction of lt_trace (Sec. 3, Eq. 2-7) divides by the hit root's
+ * denominator, by the index n2 of the medium entered and by the product of
+ * the two Fresnel denominators, and takes two square roots; the tracer forms
+ * each reciprocal as the hardware approximation plus one Newton-Raphson step
+ * r' = r + r (1 - x r), and each square root from the hardware reciprocal
+ * square root plus one Newton step.  Outputs: rcp[i] = 1 / x[i] (within about
+ * 1 ulp for finite nonzero x[i] whose reciprocal is a normal number) and
+ * sqrt_out[i] = sqrt(x[i]) (about 1 ulp for x[i] > 0; 0 for x[i] <= 0).
+ * x, rcp, sqrt_out: DEVICE arrays of n floats owned by the caller; the
+ * outputs must not overlap x.  Asynchronous on `stream`.  Errors: LT_EINVAL
+ * for a NULL array with n > 0 or n above 2^38; LT_ECUDA if the launch fails.
+ * n = 0 is a no-op. */
+lt_status lt_tracer_math(const float* x, float* rcp, float* sqrt_out, size_t n, lt_stream stream);
+
 /* Compacted output of lt_trace_paths: path p owns the segment
  * [p * capacity, (p + 1) * capacity) of every array.  Only rays that reach
  * the image plane are written, in no particular order within a segment. */

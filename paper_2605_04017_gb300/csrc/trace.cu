@@ -114,6 +114,17 @@ trace_rest_kernel(const __grid_constant__ LensDev L, int pi, int pj, RayQueue Q,
     warp_add(work, (unsigned)nint);
 }
 
+// The tracer's reciprocal and square root, element by element (lt_tracer_math).
+__global__ void __launch_bounds__(256)
+tracer_math_kernel(const float* __restrict__ x, float* __restrict__ rcp, float* __restrict__ sq, size_t n)
+{
+    const size_t i = (size_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= n) return;
+    const float v = x[i];
+    rcp[i] = rcp_nr(v);
+    sq[i] = fast_sqrt(v);
+}
+
 // Grid of a persistent kernel: resident blocks per SM x SMs, but no more warps
 // than there are chunks of work.
 unsigned persistent_blocks(const void* kernel, int block, size_t items, size_t per_warp)
@@ -259,6 +270,18 @@ lt_status lt_trace_host(const lt_lens* L, const lt_rays_in* in, const float* lam
     return run_host_pipelined(in, lam, out, n,
                               [&](const RaysInDev& a, const RaysOutDev& b, size_t m,
                                   cudaStream_t st) { return launch_trace(L, pi, pj, a, b, m, st); });
+}
+
+lt_status lt_tracer_math(const float* x, float* rcp, float* sqrt_out, size_t n, lt_stream stream)
+{
+    clear_error();
+    if (n == 0) return LT_OK;
+    if (!x || !rcp || !sqrt_out) return fail(LT_EINVAL, "lt_tracer_math: NULL array with n = %zu", n);
+    if (n > ((size_t)1 << 38)) return fail(LT_EINVAL, "lt_tracer_math: n = %zu is too large", n);
+    const size_t blocks = (n + 255) / 256;
+    tracer_math_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(x, rcp, sqrt_out, n);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LT_OK : cuda_fail(e, "lt_tracer_math: launch");
 }
 
 }  // extern "C"

@@ -121,6 +121,8 @@ def _declare(L: ctypes.CDLL) -> None:
     L.lt_trace_host.restype = st
     L.lt_trace_host.argtypes = [vp, ctypes.POINTER(c_rays_in), vp, ctypes.c_int32,
                                 ctypes.POINTER(c_rays_out), ctypes.c_size_t]
+    L.lt_tracer_math.restype = st
+    L.lt_tracer_math.argtypes = [vp, vp, vp, ctypes.c_size_t, vp]
 
 
 def check(code: int) -> None:
@@ -247,6 +249,12 @@ def trace(lens: Lens, inp: Sequence, lam, path_id: int, out: Sequence, n: int, s
     ro = rays_out(*out)
     check(lib().lt_trace(lens.handle, ctypes.byref(ri), _ptr(lam), path_id, ctypes.byref(ro), n,
                          _stream_handle(stream)))
+
+
+def tracer_math(x, rcp, sqrt_out, n: int, stream=None):
+    """lt_tracer_math on device float tensors: the tracer's reciprocal and
+    square root of each x[i]."""
+    check(lib().lt_tracer_math(_ptr(x), _ptr(rcp), _ptr(sqrt_out), n, _stream_handle(stream)))
 
 
 def trace_host(lens: Lens, inp: Sequence, lam, path_id: int, out: Sequence, n: int):
